@@ -1,0 +1,659 @@
+/* snap_oracle.c -- plain FP64 CPU reference of one SNAP finite-volume step.
+ *
+ * TEST INFRASTRUCTURE: called only by the tests, the smoke check and the CPU-baseline leg
+ * of the benchmark. Nothing in the product library links, loads or calls it, and it
+ * shares no code with the CUDA path. Whole-array loops in the order the paper states the
+ * method; no blocking, fusion or reordering.
+ *
+ * Paper: C. Li and X. Chen, ApJS 2019 (arXiv 1901.02955). Each function names the
+ * passage it follows; readings of passages the paper leaves open are marked READING.
+ */
+#include "snap_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ---------------------------------------------------------------------------------------
+ * layout helpers
+ * ------------------------------------------------------------------------------------- */
+static int nmom_of(const orc_grid *g) { return g->ny > 1 ? 3 : 2; }
+static int im0_of(const orc_grid *g) { return 1 + g->nvap + g->nvap * g->ncond; }
+int orc_nvar(const orc_grid *g) { return im0_of(g) + nmom_of(g) + 1; }
+static int icond(const orc_grid *g, int i, int j) { return 1 + g->nvap + i * g->ncond + j; }
+/* momentum slot of spatial direction d (0 x, 1 y, 2 z) */
+static int mom_slot(const orc_grid *g, int d) {
+  if (g->ny > 1) return im0_of(g) + d;
+  return im0_of(g) + (d == 2 ? 1 : 0);
+}
+
+/* Thermodynamic constants per unit mass (Sec. 2 and App. A):
+ *   c_vd = R_d/(gamma_d-1), R_i = R_d/eps_i, c_vi = sigma_vi c_vd, c_pi = c_vi + R_i,
+ *   c_ij = sigma_ij c_vd, dc_ij = c_ij - c_pi (Eq. latent),
+ *   mu_ij = mu_i - (L^r_ij + dc_ij T^r) with mu_i = 0 (Eq. muij). */
+static double c_vd(const orc_grid *g) { return g->Rd / (g->gamma_d - 1.0); }
+static double R_vap(const orc_grid *g, int i) { return g->Rd / g->eps[i]; }
+static double c_pv(const orc_grid *g, int i) { return g->sig_v[i] * c_vd(g) + R_vap(g, i); }
+static double dc_of(const orc_grid *g, int i, int j) {
+  return g->sig_c[i][j] * c_vd(g) - c_pv(g, i);
+}
+static double mu_of(const orc_grid *g, int i, int j) {
+  return -(g->Lref[i][j] + dc_of(g, i, j) * g->Tref[i]);
+}
+
+/* ---------------------------------------------------------------------------------------
+ * Sec. 4.2, Eq. weno5: fifth-order WENO interpolant to the face i-1/2 from the left,
+ * q = (Q_{i-3}, Q_{i-2}, Q_{i-1}, Q_i, Q_{i+1}).
+ * READING: the nonlinear weights are those of Jiang & Shu (1996), which the paper cites
+ * without printing: smoothness indicators beta_k of the three 3-cell stencils,
+ * alpha_k = d_k / (eps + beta_k)^2 with d = (0.1, 0.6, 0.3), normalised to sum 1.
+ * ------------------------------------------------------------------------------------- */
+static void weno5_betas(const double q[5], double b[3]) {
+  double t;
+  t = q[0] - 2.0 * q[1] + q[2];
+  b[0] = 13.0 / 12.0 * t * t;
+  t = q[0] - 4.0 * q[1] + 3.0 * q[2];
+  b[0] += 0.25 * t * t;
+  t = q[1] - 2.0 * q[2] + q[3];
+  b[1] = 13.0 / 12.0 * t * t;
+  t = q[1] - q[3];
+  b[1] += 0.25 * t * t;
+  t = q[2] - 2.0 * q[3] + q[4];
+  b[2] = 13.0 / 12.0 * t * t;
+  t = 3.0 * q[2] - 4.0 * q[3] + q[4];
+  b[2] += 0.25 * t * t;
+}
+
+void orc_weno5_weights(const double q[5], double eps, double w[3]) {
+  static const double d[3] = {0.1, 0.6, 0.3};
+  double b[3], a[3], s = 0.0;
+  weno5_betas(q, b);
+  for (int k = 0; k < 3; ++k) {
+    a[k] = d[k] / ((eps + b[k]) * (eps + b[k]));
+    s += a[k];
+  }
+  for (int k = 0; k < 3; ++k) w[k] = a[k] / s;
+}
+
+double orc_weno5(const double q[5], double eps) {
+  double w[3];
+  orc_weno5_weights(q, eps, w);
+  /* the three third-order candidate interpolants of Eq. weno5 */
+  double v0 = q[0] / 3.0 - 7.0 / 6.0 * q[1] + 11.0 / 6.0 * q[2];
+  double v1 = -q[1] / 6.0 + 5.0 / 6.0 * q[2] + q[3] / 3.0;
+  double v2 = q[2] / 3.0 + 5.0 / 6.0 * q[3] - q[4] / 6.0;
+  return w[0] * v0 + w[1] * v1 + w[2] * v2;
+}
+
+/* Sec. 4.2: the fifth-order polynomial interpolant I_poly. */
+double orc_weno5_poly(const double q[5]) {
+  return q[0] / 30.0 - 13.0 / 60.0 * q[1] + 47.0 / 60.0 * q[2] + 9.0 / 20.0 * q[3] -
+         q[4] / 20.0;
+}
+
+/* ---------------------------------------------------------------------------------------
+ * App. B: conserved Y -> primitive X = (rho, q_i, q_ij, u, [v], w, p), plus T (Eq. eos)
+ * and the effective adiabatic index gamma.
+ * ------------------------------------------------------------------------------------- */
+static void mix_factors(const orc_grid *g, const double *X, double *num, double *den) {
+  /* num = 1 + sum q_i (sigma_vi - 1) + sum q_ij (sigma_ij - 1)
+   * den = 1 + sum q_i (1/eps_i - 1) - sum q_ij                       (App. B, Eq. p2) */
+  double n = 1.0, d = 1.0;
+  for (int i = 0; i < g->nvap; ++i) {
+    n += X[1 + i] * (g->sig_v[i] - 1.0);
+    d += X[1 + i] * (1.0 / g->eps[i] - 1.0);
+    for (int j = 0; j < g->ncond; ++j) {
+      double qij = X[icond(g, i, j)];
+      n += qij * (g->sig_c[i][j] - 1.0);
+      d -= qij;
+    }
+  }
+  *num = n;
+  *den = d;
+}
+
+void orc_cons_to_prim(const orc_grid *g, const double *Y, double *X, double *T, double *gamma) {
+  const int im0 = im0_of(g), nm = nmom_of(g), nv = orc_nvar(g);
+  double rho = 0.0;
+  for (int s = 0; s < im0; ++s) rho += Y[s];
+  X[0] = rho;
+  for (int s = 1; s < im0; ++s) X[s] = Y[s] / rho;
+  double K = 0.0;
+  for (int m = 0; m < nm; ++m) {
+    X[im0 + m] = Y[im0 + m] / rho;
+    K += 0.5 * rho * X[im0 + m] * X[im0 + m];
+  }
+  double A = 0.0;
+  for (int i = 0; i < g->nvap; ++i)
+    for (int j = 0; j < g->ncond; ++j) A += mu_of(g, i, j) * Y[icond(g, i, j)];
+  double U = Y[nv - 1] - K - A;
+  double num, den;
+  mix_factors(g, X, &num, &den);
+  double p = (g->gamma_d - 1.0) * den / num * U;
+  X[nv - 1] = p;
+  if (T) *T = p / (rho * g->Rd * den);
+  if (gamma) *gamma = 1.0 + (g->gamma_d - 1.0) * den / num;
+}
+
+void orc_prim_to_cons(const orc_grid *g, const double *X, double *Y) {
+  const int im0 = im0_of(g), nm = nmom_of(g), nv = orc_nvar(g);
+  double rho = X[0], rd = rho;
+  for (int s = 1; s < im0; ++s) {
+    Y[s] = rho * X[s];
+    rd -= Y[s];
+  }
+  Y[0] = rd;
+  double K = 0.0;
+  for (int m = 0; m < nm; ++m) {
+    Y[im0 + m] = rho * X[im0 + m];
+    K += 0.5 * rho * X[im0 + m] * X[im0 + m];
+  }
+  double A = 0.0;
+  for (int i = 0; i < g->nvap; ++i)
+    for (int j = 0; j < g->ncond; ++j) A += mu_of(g, i, j) * Y[icond(g, i, j)];
+  double num, den;
+  mix_factors(g, X, &num, &den);
+  Y[nv - 1] = num / den * X[nv - 1] / (g->gamma_d - 1.0) + K + A;
+}
+
+/* App. D: integrated Clausius-Clapeyron relation over condensate (i,1):
+ * p* = p^r exp[beta (1 - 1/t) - delta ln t], t = T/T^r, beta = (L^r + dc T^r)/(R_i T^r),
+ * delta = dc/R_i. */
+double orc_sat_pressure(const orc_grid *g, int i, double T) {
+  double Ri = R_vap(g, i), dc = dc_of(g, i, 0);
+  double beta = (g->Lref[i][0] + dc * g->Tref[i]) / (Ri * g->Tref[i]);
+  double delta = dc / Ri;
+  double t = T / g->Tref[i];
+  return g->pref[i] * exp(beta * (1.0 - 1.0 / t) - delta * log(t));
+}
+
+/* ---------------------------------------------------------------------------------------
+ * Sec. 4.1, Eqs. rp and ru: LMARS.
+ * READINGS (the paper defers details to Chen et al. 2013):
+ *  - rho c = (rho_L + rho_R)/2 * (c_L + c_R)/2 with c^2 = gamma p / rho (gamma of App. B).
+ *  - Eqs. rp/ru use the pressure perturbation p' = p - pref ("perturbation pressure in the
+ *    vertical"); a constant pref cancels from both, so the same form serves every face.
+ *  - Flux = u* Phi_S + p'* n, with S the upwind side (left if u* > 0, else right) and
+ *    Phi = (rho_d, rho_i, rho_ij, rho u, [rho v], rho w, rho e + p) built from the
+ *    reconstructed primitives of side S; p in rho e + p is the total pressure pref + p'_S.
+ *    The reference pressure's own momentum flux is accounted for in the gravity source.
+ * ------------------------------------------------------------------------------------- */
+void orc_lmars(const orc_grid *g, const double *XL, const double *XR, int dir, double pref,
+               double *F, double *ustar, double *pstar) {
+  const int im0 = im0_of(g), nm = nmom_of(g), nv = orc_nvar(g);
+  const int mn = mom_slot(g, dir);
+  double numL, denL, numR, denR;
+  mix_factors(g, XL, &numL, &denL);
+  mix_factors(g, XR, &numR, &denR);
+  double pL = pref + XL[nv - 1], pR = pref + XR[nv - 1];
+  double gamL = 1.0 + (g->gamma_d - 1.0) * denL / numL;
+  double gamR = 1.0 + (g->gamma_d - 1.0) * denR / numR;
+  double cL = sqrt(gamL * pL / XL[0]), cR = sqrt(gamR * pR / XR[0]);
+  double rhoc = 0.5 * (XL[0] + XR[0]) * 0.5 * (cL + cR);
+  double uL = XL[mn], uR = XR[mn];
+  double ps = 0.5 * (XL[nv - 1] + XR[nv - 1]) - 0.5 * rhoc * (uR - uL); /* Eq. rp */
+  double us = 0.5 * (uL + uR) - (XR[nv - 1] - XL[nv - 1]) / (2.0 * rhoc); /* Eq. ru */
+  const double *XS = us > 0.0 ? XL : XR;
+  double numS = us > 0.0 ? numL : numR, denS = us > 0.0 ? denL : denR;
+  double pS = us > 0.0 ? pL : pR;
+  double rhoS = XS[0];
+  double mflux = us * rhoS;
+  double qsum = 0.0;
+  for (int s = 1; s < im0; ++s) {
+    F[s] = mflux * XS[s];
+    qsum += XS[s];
+  }
+  F[0] = mflux * (1.0 - qsum);
+  double K = 0.0;
+  for (int m = 0; m < nm; ++m) {
+    F[im0 + m] = mflux * XS[im0 + m];
+    K += 0.5 * rhoS * XS[im0 + m] * XS[im0 + m];
+  }
+  F[mn] += ps;
+  double A = 0.0;
+  for (int i = 0; i < g->nvap; ++i)
+    for (int j = 0; j < g->ncond; ++j) A += mu_of(g, i, j) * rhoS * XS[icond(g, i, j)];
+  double rhoe = numS / denS * pS / (g->gamma_d - 1.0) + K + A; /* App. B */
+  F[nv - 1] = us * (rhoe + pS);
+  if (ustar) *ustar = us;
+  if (pstar) *pstar = ps;
+}
+
+/* ---------------------------------------------------------------------------------------
+ * App. D: isochoric saturation adjustment of one cell.
+ * READINGS:
+ *  - Each vapour i exchanges mass only with its first condensate (cloud, j = 1); further
+ *    condensates (precipitation) are left unchanged.
+ *  - One sweep visits the vapours in table order; each computes the projected molar
+ *    transfer dq of Eq. dxf with the isochoric alpha (App. D, second form, which carries
+ *    the 1/T the first form omits), limits it to [-q_cloud, q_vapour], and moves the mass.
+ *    Temperature and pressure are then recomputed exactly from the conserved total energy
+ *    (Eq. energy) and the equation of state (Eq. eos); rho_d, rho e and the momenta never
+ *    change. If p* >= p (s >= 1, boiling) the cloud evaporates entirely.
+ *  - Stop when every |dq| <= tol (q_vapour + q_cloud) in a sweep, or report -1 after
+ *    max_iter sweeps.
+ * Molar fractions count condensates among the moles (App. D): with
+ * N = rho_d + sum_k (rho_k + sum_j rho_kj)/eps_k, q^_i = rho_i/(eps_i N).
+ * ------------------------------------------------------------------------------------- */
+int orc_satadj_cell(const orc_grid *g, double *Y, int max_iter, double tol) {
+  const int nv = orc_nvar(g);
+  double X[64], T;
+  if (g->nvap == 0 || g->ncond == 0) return 0;
+  for (int sweep = 1; sweep <= max_iter; ++sweep) {
+    int converged = 1;
+    for (int i = 0; i < g->nvap; ++i) {
+      orc_cons_to_prim(g, Y, X, &T, NULL);
+      double p = X[nv - 1];
+      double N = Y[0], gas = Y[0], heat = 0.0;
+      for (int k = 0; k < g->nvap; ++k) {
+        double tot = Y[1 + k];
+        for (int j = 0; j < g->ncond; ++j) tot += Y[icond(g, k, j)];
+        N += tot / g->eps[k];
+        gas += Y[1 + k] / g->eps[k];
+      }
+      for (int k = 0; k < g->nvap; ++k) {
+        double tot = Y[1 + k];
+        for (int j = 0; j < g->ncond; ++j) tot += Y[icond(g, k, j)];
+        /* (q^_k + sum_j q^_kj)(sigma^_vk - 1), sigma^_vk = c^_vk / c^_vd = sigma_vk eps_k */
+        heat += tot / (g->eps[k] * N) * (g->sig_v[k] * g->eps[k] - 1.0);
+      }
+      double qv = Y[1 + i] / (g->eps[i] * N);
+      double qc = Y[icond(g, i, 0)] / (g->eps[i] * N);
+      double gsum = gas / N - qv; /* other gases */
+      double s = orc_sat_pressure(g, i, T) / p;
+      double dq;
+      if (s >= 1.0) {
+        dq = -qc;
+      } else {
+        double Ri = R_vap(g, i), dc = dc_of(g, i, 0);
+        double beta = (g->Lref[i][0] + dc * g->Tref[i]) / (Ri * g->Tref[i]);
+        double delta = dc / Ri;
+        double t = T / g->Tref[i];
+        double alpha = (g->gamma_d - 1.0) * (beta / t - delta - 1.0) / (1.0 + heat);
+        double r = s / (1.0 - s);
+        dq = (qv - r * gsum) /
+             (1.0 + s / ((1.0 - s) * (1.0 - s)) * (beta / t - delta) * alpha * gsum);
+      }
+      /* positivity limit; at a limit the whole phase moves, exactly */
+      double drho;
+      if (dq >= qv) {
+        dq = qv;
+        drho = Y[1 + i];
+      } else if (dq <= -qc) {
+        dq = -qc;
+        drho = -Y[icond(g, i, 0)];
+      } else {
+        drho = dq * g->eps[i] * N;
+      }
+      Y[1 + i] -= drho;
+      Y[icond(g, i, 0)] += drho;
+      if (fabs(dq) > tol * (qv + qc)) converged = 0;
+    }
+    if (converged) return sweep;
+  }
+  return -1;
+}
+
+/* Exact equilibrium of the same cell (test pin): the internal energy U = rho e - K is fixed;
+ * at trial temperature T each vapour holds min(total_i, p*_i(T)/(R_i T)) and its cloud the
+ * rest; F(T) = C_v(T) T + A(T) - U is strictly increasing, so bisection finds the root. */
+static double satadj_residual(const orc_grid *g, const double *Y0, double U, double T,
+                              double *Yout) {
+  const int nv = orc_nvar(g);
+  memcpy(Yout, Y0, sizeof(double) * (size_t)nv);
+  for (int i = 0; i < g->nvap; ++i) {
+    double tot = Y0[1 + i] + Y0[icond(g, i, 0)];
+    double v = orc_sat_pressure(g, i, T) / (R_vap(g, i) * T);
+    if (v > tot) v = tot;
+    Yout[1 + i] = v;
+    Yout[icond(g, i, 0)] = tot - v;
+  }
+  double Cv = Yout[0];
+  double A = 0.0;
+  for (int i = 0; i < g->nvap; ++i) {
+    Cv += g->sig_v[i] * Yout[1 + i];
+    for (int j = 0; j < g->ncond; ++j) {
+      Cv += g->sig_c[i][j] * Yout[icond(g, i, j)];
+      A += mu_of(g, i, j) * Yout[icond(g, i, j)];
+    }
+  }
+  Cv *= c_vd(g);
+  return Cv * T + A - U;
+}
+
+int orc_satadj_bisect(const orc_grid *g, double *Y) {
+  const int im0 = im0_of(g), nm = nmom_of(g), nv = orc_nvar(g);
+  double rho = 0.0, K = 0.0, Yt[64];
+  for (int s = 0; s < im0; ++s) rho += Y[s];
+  for (int m = 0; m < nm; ++m) K += 0.5 * Y[im0 + m] * Y[im0 + m] / rho;
+  double U = Y[nv - 1] - K;
+  double lo = 10.0, hi = 5000.0;
+  if (satadj_residual(g, Y, U, lo, Yt) > 0.0 || satadj_residual(g, Y, U, hi, Yt) < 0.0)
+    return -1;
+  for (int it = 0; it < 400 && hi - lo > 1e-15 * hi; ++it) {
+    double mid = 0.5 * (lo + hi);
+    if (satadj_residual(g, Y, U, mid, Yt) > 0.0)
+      hi = mid;
+    else
+      lo = mid;
+  }
+  satadj_residual(g, Y, U, 0.5 * (lo + hi), Yt);
+  memcpy(Y, Yt, sizeof(double) * (size_t)nv);
+  return 0;
+}
+
+/* ---------------------------------------------------------------------------------------
+ * Whole-grid right-hand side L(Y) of Eq. forward.
+ * Primitive cell values are held with three ghost cells per side in each active direction.
+ * READINGS:
+ *  - Boundaries: a reflecting side mirrors every primitive and negates the normal velocity;
+ *    a periodic side wraps. The vertical direction must be reflecting.
+ *  - The pressure carried in the primitive vector is the perturbation p' = p - pbar_k about
+ *    the fixed reference state (cell value pbar_k = (pbar_{k-1/2} + pbar_{k+1/2})/2), in all
+ *    directions; ghosts mirror p'. Faces of level k use pbar_k as reference in x and y and
+ *    pbar_{k-1/2} on the lower z face.
+ *  - Vertical momentum source: -(rho_k - rho_bar_k) g, the gravity term of Eq. mom3 once
+ *    the reference profile's discrete hydrostatic balance
+ *    (pbar_{k+1/2} - pbar_{k-1/2})/dz = -g rho_bar_k is taken out of the pressure flux.
+ *  - Energy source -rho g w (Sec. 2) is discretised as -g (F_rho,k-1/2 + F_rho,k+1/2)/2 from
+ *    the vertical total-mass fluxes, so the sum of rho e + rho g z is conserved in a closed
+ *    box; the pointwise -g (rho w)_k form is available as an option.
+ *  - Constant viscosity (used by the density-current workload; Sec. 5.1 applies it to
+ *    momentum and to the thermodynamic equation): at each face, from the two adjacent cell
+ *    values, the momentum flux -rho_f nu du/dn and the energy flux
+ *    -rho_f nu u_f . du/dn - rho_f c_pd nu Pi_f dtheta/dn, where theta = T / Pi and
+ *    Pi = (p / 1e5 Pa)^(R_d/c_pd) (App. C, Eq. theta, dry); the subscript f is the mean of
+ *    the two cells. Ghost cells mirror theta, so no heat crosses a reflecting wall.
+ * ------------------------------------------------------------------------------------- */
+typedef struct {
+  int nxe, nye, nze, ox, oy, oz;
+} ext_dims;
+
+static long ext_index(const ext_dims *e, int k, int j, int i) {
+  return ((long)(k + e->oz) * e->nye + (j + e->oy)) * e->nxe + (i + e->ox);
+}
+
+static int wrap_or_mirror(int idx, int n, int bc_lo, int bc_hi, int *flip) {
+  *flip = 0;
+  if (idx < 0) {
+    if (bc_lo == ORC_PERIODIC) return ((idx % n) + n) % n;
+    *flip = 1;
+    return -1 - idx;
+  }
+  if (idx >= n) {
+    if (bc_hi == ORC_PERIODIC) return idx % n;
+    *flip = 1;
+    return 2 * n - 1 - idx;
+  }
+  return idx;
+}
+
+static double pbar_cell(const orc_grid *g, int k) {
+  return 0.5 * (g->p_bar_face[k] + g->p_bar_face[k + 1]);
+}
+
+int orc_rhs(const orc_grid *g, const double *Y, double *dYdt) {
+  const int nx = g->nx, ny = g->ny, nz = g->nz, nv = orc_nvar(g), im0 = im0_of(g);
+  const int three_d = ny > 1;
+  if (nx < 1 || ny < 1 || nz < 3) return -1;
+  if (g->bc[4] != ORC_REFLECT || g->bc[5] != ORC_REFLECT) return -1;
+  if ((g->bc[0] == ORC_REFLECT || g->bc[1] == ORC_REFLECT) && nx < 3) return -1;
+  if (three_d && (g->bc[2] == ORC_REFLECT || g->bc[3] == ORC_REFLECT) && ny < 3) return -1;
+  ext_dims e = {nx + 6, three_d ? ny + 6 : 1, nz + 6, 3, three_d ? 3 : 0, 3};
+  const long next = (long)e.nxe * e.nye * e.nze;
+  const long ncell = (long)nx * ny * nz;
+  double *X = calloc((size_t)(nv * next), sizeof(double));
+  double *Tx = calloc((size_t)next, sizeof(double));  /* theta */
+  double *Px = calloc((size_t)next, sizeof(double));  /* Pi */
+  double *F = malloc(sizeof(double) * (size_t)nv * (size_t)(nx + 1) * (ny + 1) * (nz + 1));
+  double *Frho_z = malloc(sizeof(double) * (size_t)nx * ny * (nz + 1));
+  if (!X || !Tx || !Px || !F || !Frho_z) {
+    free(X); free(Tx); free(Px); free(F); free(Frho_z);
+    return -2;
+  }
+  double Yc[64], Xc[64];
+  const double cpd = g->gamma_d * c_vd(g);
+
+  /* 1. primitives of interior cells (App. B), pressure stored as p' = p - pbar_k */
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        long c = ((long)k * ny + j) * nx + i;
+        for (int v = 0; v < nv; ++v) Yc[v] = Y[v * ncell + c];
+        double T;
+        orc_cons_to_prim(g, Yc, Xc, &T, NULL);
+        double Pi = pow(Xc[nv - 1] / 1e5, (g->gamma_d - 1.0) / g->gamma_d);
+        Xc[nv - 1] -= pbar_cell(g, k);
+        long x = ext_index(&e, k, j, i);
+        for (int v = 0; v < nv; ++v) X[v * next + x] = Xc[v];
+        Tx[x] = T / Pi;
+        Px[x] = Pi;
+      }
+
+  /* 2. ghost cells */
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j < ny; ++j)
+      for (int gi = -3; gi < nx + 3; ++gi) {
+        if (gi >= 0 && gi < nx) continue;
+        int flip, si = wrap_or_mirror(gi, nx, g->bc[0], g->bc[1], &flip);
+        long dst = ext_index(&e, k, j, gi), src = ext_index(&e, k, j, si);
+        for (int v = 0; v < nv; ++v) X[v * next + dst] = X[v * next + src];
+        Tx[dst] = Tx[src];
+        Px[dst] = Px[src];
+        if (flip) X[(long)mom_slot(g, 0) * next + dst] *= -1.0;
+      }
+  if (three_d)
+    for (int k = 0; k < nz; ++k)
+      for (int gj = -3; gj < ny + 3; ++gj)
+        for (int i = 0; i < nx; ++i) {
+          if (gj >= 0 && gj < ny) continue;
+          int flip, sj = wrap_or_mirror(gj, ny, g->bc[2], g->bc[3], &flip);
+          long dst = ext_index(&e, k, gj, i), src = ext_index(&e, k, sj, i);
+          for (int v = 0; v < nv; ++v) X[v * next + dst] = X[v * next + src];
+          Tx[dst] = Tx[src];
+          Px[dst] = Px[src];
+          if (flip) X[(long)mom_slot(g, 1) * next + dst] *= -1.0;
+        }
+  for (int gk = -3; gk < nz + 3; ++gk)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        if (gk >= 0 && gk < nz) continue;
+        int flip, sk = wrap_or_mirror(gk, nz, g->bc[4], g->bc[5], &flip);
+        long dst = ext_index(&e, gk, j, i), src = ext_index(&e, sk, j, i);
+        for (int v = 0; v < nv; ++v) X[v * next + dst] = X[v * next + src];
+        Tx[dst] = Tx[src];
+        Px[dst] = Px[src];
+        if (flip) X[(long)mom_slot(g, 2) * next + dst] *= -1.0;
+      }
+
+  for (long v = 0; v < nv * ncell; ++v) dYdt[v] = 0.0;
+
+  /* 3. per direction: reconstruct both face states (Eq. q+ with m = 3), Riemann flux
+   *    (Eq. riemann via LMARS), then the flux difference of Eq. forward. */
+  for (int d = 0; d < 3; ++d) {
+    if (d == 1 && !three_d) continue;
+    const int fx = (d == 0), fy = (d == 1), fz = (d == 2);
+    const int nfx = nx + fx, nfy = ny + fy, nfz = nz + fz;
+    const double h = d == 0 ? g->dx : (d == 1 ? g->dy : g->dz);
+    for (int k = 0; k < nfz; ++k)
+      for (int j = 0; j < nfy; ++j)
+        for (int i = 0; i < nfx; ++i) {
+          double XL[64], XR[64], Ff[64], st[5];
+          /* stencil cell s (s = -3..+2) lies s cells along d from the face's right cell */
+          for (int v = 0; v < nv; ++v) {
+            double col[6];
+            for (int s = -3; s <= 2; ++s)
+              col[s + 3] = X[v * next + ext_index(&e, k + s * fz, j + s * fy, i + s * fx)];
+            for (int s = 0; s < 5; ++s) st[s] = col[s]; /* Q_{i-3} .. Q_{i+1} */
+            XL[v] = orc_weno5(st, g->weno_eps);
+            for (int s = 0; s < 5; ++s) st[s] = col[5 - s]; /* Q_{i+2} .. Q_{i-2} */
+            XR[v] = orc_weno5(st, g->weno_eps);
+          }
+          double pref = fz ? g->p_bar_face[k] : pbar_cell(g, k);
+          orc_lmars(g, XL, XR, d, pref, Ff, NULL, NULL);
+          if (g->nu > 0.0) {
+            long cl = ext_index(&e, k - fz, j - fy, i - fx), cr = ext_index(&e, k, j, i);
+            double rl = X[cl], rr = X[cr];
+            double rf = 0.5 * (rl + rr), work = 0.0;
+            for (int m = 0; m < nmom_of(g); ++m) {
+              double ul = X[(long)(im0 + m) * next + cl], ur = X[(long)(im0 + m) * next + cr];
+              double grad = (ur - ul) / h;
+              Ff[im0 + m] -= rf * g->nu * grad;
+              work += 0.5 * (ul + ur) * grad;
+            }
+            double heat = 0.5 * (Px[cl] + Px[cr]) * (Tx[cr] - Tx[cl]) / h;
+            Ff[nv - 1] -= rf * g->nu * work + rf * cpd * g->nu * heat;
+          }
+          long fidx = ((long)k * nfy + j) * nfx + i;
+          long nf = (long)nfx * nfy * nfz;
+          for (int v = 0; v < nv; ++v) F[v * nf + fidx] = Ff[v];
+          if (fz) {
+            double m = 0.0;
+            for (int s = 0; s < im0; ++s) m += Ff[s];
+            Frho_z[((long)k * ny + j) * nx + i] = m;
+          }
+        }
+    long nf = (long)nfx * nfy * nfz;
+    for (int k = 0; k < nz; ++k)
+      for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+          long c = ((long)k * ny + j) * nx + i;
+          long f0 = ((long)k * nfy + j) * nfx + i;
+          long f1 = ((long)(k + fz) * nfy + (j + fy)) * nfx + (i + fx);
+          for (int v = 0; v < nv; ++v) dYdt[v * ncell + c] -= (F[v * nf + f1] - F[v * nf + f0]) / h;
+        }
+  }
+
+  /* 4. gravity sources (Eq. mom3 and the energy equation of Sec. 2) */
+  const int mw = mom_slot(g, 2);
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        long c = ((long)k * ny + j) * nx + i;
+        double rho = X[ext_index(&e, k, j, i)];
+        dYdt[(long)mw * ncell + c] -= (rho - g->rho_bar[k]) * g->grav;
+        if (g->gravity_energy_pointwise) {
+          dYdt[(long)(nv - 1) * ncell + c] -= g->grav * Y[(long)mw * ncell + c];
+        } else {
+          double fb = Frho_z[((long)k * ny + j) * nx + i];
+          double ft = Frho_z[((long)(k + 1) * ny + j) * nx + i];
+          dYdt[(long)(nv - 1) * ncell + c] -= g->grav * 0.5 * (fb + ft);
+        }
+      }
+  free(X);
+  free(Tx);
+  free(Px);
+  free(F);
+  free(Frho_z);
+  return 0;
+}
+
+/* Sec. 4.3: third-order TVD (SSP) Runge-Kutta of Shu & Osher:
+ *   stage 0: Y1 = Yn + dt L(Yn)
+ *   stage 1: Y2 = 3/4 Yn + 1/4 (Y1 + dt L(Y1))
+ *   stage 2: Yn+1 = 1/3 Yn + 2/3 (Y2 + dt L(Y2)) */
+void orc_rk3_combine(int stage, long n, const double *Yn, const double *Ys, const double *L,
+                     double dt, double *Yout) {
+  for (long c = 0; c < n; ++c) {
+    double ys = Ys[c] + dt * L[c];
+    if (stage == 0)
+      Yout[c] = ys;
+    else if (stage == 1)
+      Yout[c] = 0.75 * Yn[c] + 0.25 * ys;
+    else
+      Yout[c] = Yn[c] / 3.0 + 2.0 / 3.0 * ys;
+  }
+}
+
+int orc_stage(const orc_grid *g, int stage, const double *Yn, const double *Ys, double dt,
+              double *Yout) {
+  const int nv = orc_nvar(g);
+  const long ncell = (long)g->nx * g->ny * g->nz;
+  double *L = malloc(sizeof(double) * (size_t)(nv * ncell));
+  if (!L) return -2;
+  int rc = orc_rhs(g, Ys, L);
+  if (rc) {
+    free(L);
+    return rc;
+  }
+  orc_rk3_combine(stage, nv * ncell, Yn, Ys, L, dt, Yout);
+  free(L);
+  int worst = 0;
+  if (g->satadj && g->nvap > 0 && g->ncond > 0) {
+    double Yc[64];
+    for (long c = 0; c < ncell; ++c) {
+      for (int v = 0; v < nv; ++v) Yc[v] = Yout[v * ncell + c];
+      int it = orc_satadj_cell(g, Yc, g->satadj_max_iter, g->satadj_tol);
+      if (it < 0) worst = -1;
+      else if (worst >= 0 && it > worst) worst = it;
+      for (int v = 0; v < nv; ++v) Yout[v * ncell + c] = Yc[v];
+    }
+  }
+  return worst;
+}
+
+/* READING: the paper gives no time-step rule. For the unsplit update of Eq. forward,
+ * dt = cfl / max over cells of sum_d (|u_d| + c) / dx_d, from the state at the start of the
+ * step, held for all three stages. */
+double orc_dt_cfl(const orc_grid *g, const double *Y, double cfl) {
+  const int nv = orc_nvar(g);
+  const long ncell = (long)g->nx * g->ny * g->nz;
+  double Yc[64], Xc[64], rate = 0.0;
+  for (long c = 0; c < ncell; ++c) {
+    for (int v = 0; v < nv; ++v) Yc[v] = Y[v * ncell + c];
+    double gam;
+    orc_cons_to_prim(g, Yc, Xc, NULL, &gam);
+    double cs = sqrt(gam * Xc[nv - 1] / Xc[0]);
+    double r = 0.0;
+    for (int d = 0; d < 3; ++d) {
+      if (d == 1 && g->ny == 1) continue;
+      double h = d == 0 ? g->dx : (d == 1 ? g->dy : g->dz);
+      r += (fabs(Xc[mom_slot(g, d)]) + cs) / h;
+    }
+    if (r > rate) rate = r;
+  }
+  return cfl / rate;
+}
+
+int orc_step(const orc_grid *g, double *Y, int nsteps, double dt, double cfl, double *dt_last) {
+  const int nv = orc_nvar(g);
+  const long n = (long)nv * g->nx * g->ny * g->nz;
+  double *Y1 = malloc(sizeof(double) * (size_t)n), *Y2 = malloc(sizeof(double) * (size_t)n);
+  if (!Y1 || !Y2) {
+    free(Y1); free(Y2);
+    return -2;
+  }
+  int worst = 0;
+  for (int s = 0; s < nsteps; ++s) {
+    double h = dt > 0.0 ? dt : orc_dt_cfl(g, Y, cfl);
+    if (dt_last) *dt_last = h;
+    int r0 = orc_stage(g, 0, Y, Y, h, Y1);
+    int r1 = orc_stage(g, 1, Y, Y1, h, Y2);
+    int r2 = orc_stage(g, 2, Y, Y2, h, Y1);
+    if (r0 < -1 || r1 < -1 || r2 < -1) {
+      free(Y1); free(Y2);
+      return -2;
+    }
+    if (r0 < 0 || r1 < 0 || r2 < 0) worst = -1;
+    memcpy(Y, Y1, sizeof(double) * (size_t)n);
+  }
+  free(Y1);
+  free(Y2);
+  return worst;
+}
+
+void orc_budget(const orc_grid *g, const double *Y, double *out) {
+  const int nv = orc_nvar(g), im0 = im0_of(g);
+  const long ncell = (long)g->nx * g->ny * g->nz;
+  const double vol = g->dx * (g->ny > 1 ? g->dy : 1.0) * g->dz;
+  for (int v = 0; v <= nv; ++v) out[v] = 0.0;
+  for (int k = 0; k < g->nz; ++k) {
+    double z = (k + 0.5) * g->dz;
+    for (long c = (long)k * g->nx * g->ny; c < (long)(k + 1) * g->nx * g->ny; ++c) {
+      double rho = 0.0;
+      for (int v = 0; v < nv; ++v) out[v] += Y[v * ncell + c] * vol;
+      for (int s = 0; s < im0; ++s) rho += Y[s * ncell + c];
+      out[nv] += (Y[(long)(nv - 1) * ncell + c] + rho * g->grav * z) * vol;
+    }
+  }
+}

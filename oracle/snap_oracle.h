@@ -1,0 +1,102 @@
+/* snap_oracle.h -- plain FP64 CPU reference of one SNAP finite-volume step.
+ *
+ * TEST INFRASTRUCTURE. Only the tests, the smoke check and the CPU-baseline leg of the
+ * benchmark may call this code. The product library never links or loads it, and this
+ * oracle shares no code, header, table or helper with the CUDA path.
+ *
+ * Sources (Li & Chen 2019, "Simulating Non-hydrostatic atmospheres on Planets"):
+ *   conserved / primitive vectors and their conversion ............ App. B
+ *   equation of state, total energy, latent heat, chem. potential . Sec. 2
+ *   finite-volume update, Riemann problem, reconstruction ........ Sec. 4, Eqs. forward, riemann, q+
+ *   LMARS face pressure and velocity ............................. Sec. 4.1, Eqs. rp, ru
+ *   fifth-order WENO and the linear interpolant ................... Sec. 4.2, Eq. weno5
+ *   SSP (TVD) Runge-Kutta 3 ........................................ Sec. 4.3
+ *   saturation adjustment (isochoric) .............................. App. D, Eqs. dx, dxf, u
+ * Readings of passages the paper leaves open are stated at each function in snap_oracle.c.
+ *
+ * Every array is FP64, structure-of-arrays Y[field][k][j][i] with i fastest, interior cells
+ * only. Field order (App. B): rho_d, rho_i (nvap), rho_ij (nvap x ncond grouped by vapour),
+ * rho u, [rho v when ny > 1], rho w, rho e.
+ */
+#ifndef SNAP_ORACLE_H
+#define SNAP_ORACLE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ORC_MAXV 4
+#define ORC_MAXC 2
+
+enum { ORC_REFLECT = 0, ORC_PERIODIC = 1 };
+
+typedef struct {
+  int nx, ny, nz;               /* ny == 1: x-z plane with no y direction */
+  double dx, dy, dz;
+  int bc[6];                    /* x-, x+, y-, y+, z-, z+ */
+  double grav, gamma_d, Rd;
+  int nvap, ncond;              /* vapours; condensates per vapour */
+  double eps[ORC_MAXV];         /* m_i / m_d */
+  double sig_v[ORC_MAXV];       /* c_v,i / c_vd */
+  double Tref[ORC_MAXV];        /* reference temperature of vapour i */
+  double pref[ORC_MAXV];        /* saturation pressure over condensate (i,1) at Tref */
+  double sig_c[ORC_MAXV][ORC_MAXC]; /* c_ij / c_vd */
+  double Lref[ORC_MAXV][ORC_MAXC];  /* latent heat of condensate (i,j) at Tref */
+  const double *rho_bar;        /* [nz] reference density */
+  const double *p_bar_face;     /* [nz+1] reference pressure at level faces */
+  double nu;                    /* constant kinematic viscosity (0: inviscid) */
+  int satadj;                   /* apply saturation adjustment after each stage */
+  int satadj_max_iter;
+  double satadj_tol;
+  double weno_eps;
+  int gravity_energy_pointwise; /* 0: -g (F_rho,k-1/2 + F_rho,k+1/2)/2 ; 1: -g (rho w)_k */
+} orc_grid;
+
+int orc_nvar(const orc_grid *g);
+
+/* ---- pointwise pieces (exposed for the pins) ---- */
+double orc_weno5(const double q[5], double eps);          /* I_weno(q_{i-3..i+1}) */
+double orc_weno5_poly(const double q[5]);                 /* I_poly */
+void orc_weno5_weights(const double q[5], double eps, double w[3]);
+
+/* App. B: X = (rho, q_i, q_ij, u, [v], w, p) with the TOTAL pressure p. Also returns T and
+ * the effective adiabatic index gamma (may be NULL). */
+void orc_cons_to_prim(const orc_grid *g, const double *Y, double *X, double *T, double *gamma);
+void orc_prim_to_cons(const orc_grid *g, const double *X, double *Y);
+double orc_sat_pressure(const orc_grid *g, int i, double T);
+
+/* LMARS flux through a face with unit normal along momentum component `dir` (0 x, 1 y, 2 z
+ * in the 3-D numbering; in the x-z plane use 0 for x and 2 for z). XL/XR are primitive
+ * states whose last entry is the pressure perturbation p' = p - pref; pref is the reference
+ * pressure at this face. F receives nvar fluxes; ustar / pstar (may be NULL) receive the
+ * face velocity u* and the face pressure perturbation p'*. */
+void orc_lmars(const orc_grid *g, const double *XL, const double *XR, int dir, double pref,
+               double *F, double *ustar, double *pstar);
+
+/* App. D saturation adjustment of one cell, in place; returns the number of sweeps used or
+ * -1 when it did not converge within max_iter. */
+int orc_satadj_cell(const orc_grid *g, double *Ycell, int max_iter, double tol);
+/* Exact equilibrium by bisection on temperature (test pin for orc_satadj_cell). */
+int orc_satadj_bisect(const orc_grid *g, double *Ycell);
+
+/* ---- whole-grid pieces ---- */
+/* dYdt = L(Y): minus the flux divergence plus the gravity source (and viscous fluxes). */
+int orc_rhs(const orc_grid *g, const double *Y, double *dYdt);
+/* One SSP-RK3 stage combine (Sec. 4.3) on n values: stage 0, 1, 2. */
+void orc_rk3_combine(int stage, long n, const double *Yn, const double *Ys, const double *L,
+                     double dt, double *Yout);
+/* One Runge-Kutta stage: Yout = combine(Yn, Ys + dt L(Ys)), then saturation adjustment.
+ * Returns the largest sweep count, or -1 if a cell did not converge. */
+int orc_stage(const orc_grid *g, int stage, const double *Yn, const double *Ys, double dt,
+              double *Yout);
+/* nsteps full steps in place; dt <= 0 means recompute dt = cfl * min dx/(|u|+c) per step. */
+int orc_step(const orc_grid *g, double *Y, int nsteps, double dt, double cfl, double *dt_last);
+double orc_dt_cfl(const orc_grid *g, const double *Y, double cfl);
+/* out[f] = sum of field f times the cell volume (nvar values), out[nvar] = sum of
+ * (rho e + rho g z) times the cell volume. */
+void orc_budget(const orc_grid *g, const double *Y, double *out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
