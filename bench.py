@@ -1,0 +1,341 @@
+"""Benchmark of the fused SNAP finite-volume step on GB300.
+
+Workload: the 2-D dry density current (25.6 km x 6.4 km, 1024 x 256 cells, theta = 300 K,
+-15 K cosine bubble, nu = 75 m^2/s, reflecting walls), seeded and synthetic. A step is one
+SSP-RK3 step (three fused stages). Metric: cell-updates per second per RK stage,
+cells x 3 x steps / time, FP32 (the headline) with the FP64 step measured beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+One JSON line on rank 0. Under torchrun (N > 1) each rank advances an independent replica
+(weak scaling, no collective on the data path); time is the max over ranks.
+"""
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell-updates/s per RK stage (WENO5+LMARS), FP32 vs FP64, % of HBM roofline"
+UNIT = "cell-updates/s"
+WORKLOAD = "density_current_1024x256"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=40)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="cuda", choices=["cuda", "reference"])
+    p.add_argument("--cpu-seconds", type=float, default=10.0)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def dist_info():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload(dtype):
+    import workloads as W
+    return W.density_current(dtype=dtype)
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            d = json.load(open(path))
+            for k in ("hbm_gbs", "hbm_GBs", "hbm"):
+                if k in d:
+                    return float(d[k]), "measured"
+        except Exception:
+            pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_sources_md5():
+    h = hashlib.md5()
+    csrc = os.path.join(ROOT, "paper_1901_02955_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()
+
+
+def ncu_traffic():
+    """DRAM bytes per launch of the stage kernel from the committed ncu summary, if it was
+    taken on the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "stage_kernel_density_current_traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        d = json.load(open(path))
+        if d.get("sources_md5") == kernel_sources_md5():
+            return float(d["dram_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    def __init__(self, index):
+        self.proc = None
+        self.path = None
+        self.index = index
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.proc or not self.path:
+            return None
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append((float(f[1]), float(f[2]), f[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i in range(4) if r[i] == "Active"})
+        return {"sm_mhz": float(np.median([r[0] for r in rows])),
+                "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons,
+                "samples": len(rows)}
+
+
+def cpu_baseline(seconds):
+    """The FP64 oracle as it stands on the host: whole steps of the full workload."""
+    import oracle
+    oracle.build()
+    w = workload("f64")
+    o = oracle.Oracle(w)
+    dt = o.dt_cfl(w.Y)
+    t0 = time.perf_counter()
+    Y, _, _ = o.step(w.Y, 1, dt=dt)
+    t1 = time.perf_counter() - t0
+    n = max(1, int(seconds / max(t1, 1e-6)) - 1)
+    t0 = time.perf_counter()
+    o.step(Y, n, dt=dt)
+    t = time.perf_counter() - t0
+    steps = n
+    return {"value": w.ncells * 3 * steps / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{steps} full SSP-RK3 steps of {WORKLOAD} in FP64 on one host core "
+                      f"({t:.1f} s)"}
+
+
+def reference_arm(args, rank):
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    w = workload("f64")
+    o = oracle.Oracle(w)
+    dt = o.dt_cfl(w.Y)
+    Y = w.Y
+    for _ in range(args.warmup):
+        Y, _, _ = o.step(Y, 1, dt=dt)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        Y, _, _ = o.step(Y, 1, dt=dt)
+    t = time.perf_counter() - t0
+    v = w.ncells * 3 * args.steps / t
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "cells": w.ncells, "nfields": w.nv,
+                       "parallelism": "single host core"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} full steps of {WORKLOAD}, FP64, one core"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_info()
+    if args.impl == "reference":
+        reference_arm(args, rank)
+        return
+    import torch
+    if not torch.cuda.is_available():
+        print(json.dumps({"metric": METRIC, "error": "no CUDA device"}))
+        sys.exit(1)
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1901_02955_gb300 import Context
+
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")  # > 129 MB L2
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x):
+        if not dist:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def device_steps(ctx, steps, warmup):
+        """Per-step device time (ms) with the L2 flushed before each step."""
+        for _ in range(warmup):
+            flush.fill_(1)
+            ctx.step_async(1)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        barrier()
+        for s, e in ev:
+            flush.fill_(1)
+            s.record(stream)
+            ctx.step_async(1)
+            e.record(stream)
+        barrier()
+        rc, flags = ctx.check()
+        assert rc == 0, f"device check failed: flags {flags}"
+        return [s.elapsed_time(e) for s, e in ev]
+
+    # ---- FP32 fused step (headline) --------------------------------------------------------
+    w32 = workload("f32")
+    ctx = Context(w32, dtype="f32")
+    ctx.set_stream(stream)
+    ctx.set_state(w32.Y)
+    with Clocks(local) as clk:
+        times = device_steps(ctx, args.steps, args.warmup)
+    ms32 = max_over_ranks(float(np.sum(times)) / args.steps)
+    cells = w32.ncells
+    value = world * cells * 3 / (ms32 * 1e-3)
+    launches = 3 * args.steps
+
+    # ---- dominant kernel: the stage kernel, timed per launch --------------------------------
+    ctx.set_state(w32.Y)
+    dt = ctx.compute_dt()
+    nst = max(10, args.steps // 2)
+    evs = []
+    for i in range(nst + 3):
+        flush.fill_(1)
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        e[0].record(stream)
+        for st in range(3):
+            ctx.stage(st, dt)
+            e[st + 1].record(stream)
+        if i >= 3:
+            evs.append(e)
+    torch.cuda.synchronize()
+    per_stage = [[e[s].elapsed_time(e[s + 1]) for s in range(3)] for e in evs]
+    stage_ms = float(np.mean(per_stage))
+    word = 4
+    alg_bytes = (8.0 / 3.0) * w32.nv * word * cells  # per launch, averaged over the 3 stages
+    peak, peak_src = measured_peaks()
+    achieved = alg_bytes / (stage_ms * 1e-3) / 1e9
+    traffic = ncu_traffic()
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic,
+                "peak_source": f"{peak_src} HBM copy bandwidth",
+                "kernel": "snap::stage_kernel<float, dry x-z, viscous>",
+                "stage_ms": [float(np.mean([p[s] for p in per_stage])) for s in range(3)],
+                "algorithmic_bytes_per_launch": alg_bytes}
+
+    # ---- end to end through the C ABI with pinned host buffers --------------------------------
+    host_in = torch.from_numpy(w32.Y.astype(np.float32)).pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    for _ in range(max(2, args.warmup)):
+        ctx.set_state(host_in)
+        ctx.step_async(1)
+        ctx.get_state(out=host_out)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        flush.fill_(1)
+        ctx.set_state(host_in)
+        ctx.step_async(1)
+        ctx.get_state(out=host_out)  # synchronises: the step's result is on the host
+    barrier()
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / args.steps)
+    nbytes = host_in.numel() * 4
+    e2e = {"value": world * cells * 3 / e2e_s, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+           "d2h_bytes_per_step": nbytes, "note": "wall clock per step incl. one L2 flush"}
+    ctx.close()
+
+    # ---- FP64 fused step beside it ---------------------------------------------------------
+    w64 = workload("f64")
+    c64 = Context(w64, dtype="f64")
+    c64.set_stream(stream)
+    c64.set_state(w64.Y)
+    k64 = max(5, args.steps // 4)
+    t64 = device_steps(c64, k64, 2)
+    ms64 = max_over_ranks(float(np.sum(t64)) / k64)
+    v64 = world * cells * 3 / (ms64 * 1e-3)
+    c64.close()
+
+    if rank == 0:
+        cpu = None if args.no_cpu_baseline else cpu_baseline(args.cpu_seconds)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms32,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "cells": cells, "nfields": w32.nv,
+                       "grid": [w32.nx, w32.nz], "viscosity": w32.nu,
+                       "l2": "flushed (512 MB write) before every timed step",
+                       "fp64_value": v64, "fp64_ms_per_step": ms64, "fp32_over_fp64": value / v64,
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,184 @@
+/* snap.h -- C ABI of the GB300 (sm_103a) library for one explicit finite-volume step of the
+ * compressible Euler equations with total energy and moist tracers, after
+ * C. Li and X. Chen, "Simulating Non-hydrostatic atmospheres on Planets (SNAP)",
+ * ApJS 2019 (arXiv 1901.02955).
+ *
+ * Conventions shared by every entry point
+ *  - Return value: SNAP_OK (0) or a negative snap_status. No C++ exception crosses the ABI.
+ *    snap_last_error() gives a one-line description of the last failure on a context.
+ *  - A context is not thread-safe; use one host thread per context at a time.
+ *  - Work is ordered on the context's CUDA stream (snap_set_stream; default: a stream the
+ *    library creates). Calls that return host data synchronise that stream.
+ *  - State layout (App. B conserved vector): structure of arrays Y[field][k][j][i], i fastest,
+ *    interior cells only, fields in the order
+ *      rho_d, rho_i (n_vapor), rho_ij (n_vapor x n_cond, grouped by vapour: i=0 j=0.., i=1 ..),
+ *      rho u, [rho v when ny > 1], rho w, rho e.
+ *    ny == 1 selects the x-z plane (no rho v). Units SI.
+ *  - The library copies every input it is given; the caller keeps ownership of its buffers.
+ */
+#ifndef SNAP_H
+#define SNAP_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SNAP_MAX_VAPOR 4
+#define SNAP_MAX_COND 2
+#define SNAP_MAX_FIELDS 24
+
+typedef enum snap_status {
+  SNAP_OK = 0,
+  SNAP_EINVAL = -1,     /* invalid argument or descriptor */
+  SNAP_ENOMEM = -2,     /* device or host allocation failed */
+  SNAP_ECUDA = -3,      /* a CUDA call failed (snap_last_error has the CUDA message) */
+  SNAP_ENONFINITE = -4, /* a step produced a non-finite value or a non-positive density */
+  SNAP_ENOCONV = -5,    /* saturation adjustment hit its sweep limit in some cell */
+  SNAP_ETIMEOUT = -6,   /* a bounded device-side wait gave up */
+  SNAP_ENOTSUP = -7     /* combination of options not built into this library */
+} snap_status;
+
+enum { SNAP_REFLECT = 0, SNAP_PERIODIC = 1 };
+enum { SNAP_F64 = 0, SNAP_F32 = 1 };
+
+/* One condensable vapour i and its condensates (i,j); j = 0 is the cloud that exchanges mass
+ * with the vapour in the saturation adjustment (App. D), j = 1 (precipitation) is carried. */
+typedef struct snap_species {
+  double eps;                   /* m_i / m_d (App. A) */
+  double sigma_v;               /* c_v,i / c_v,d */
+  double T_ref;                 /* reference temperature T^r of Eq. latent, K */
+  double p_ref;                 /* saturation vapour pressure over condensate (i,0) at T_ref, Pa */
+  double sigma_c[SNAP_MAX_COND];/* c_ij / c_v,d */
+  double L_ref[SNAP_MAX_COND];  /* latent heat L^r_ij at T_ref, J/kg */
+} snap_species;
+
+/* Grid and physics of one domain (Sec. 2 equations, Sec. 4 scheme). */
+typedef struct snap_grid_desc {
+  int nx, ny, nz;          /* cells; ny == 1: x-z plane. Each active extent >= 3 */
+  double dx, dy, dz;       /* cell sizes, m (dy ignored when ny == 1) */
+  int bc[6];               /* x-, x+, y-, y+, z-, z+ : SNAP_REFLECT or SNAP_PERIODIC; z must
+                              reflect; a periodic side needs its opposite side periodic */
+  double grav;             /* gravitational acceleration, m/s^2 (along -z) */
+  double gamma_d;          /* c_p,d / c_v,d of the dry gas */
+  double R_d;              /* dry-gas constant, J/(kg K) */
+  int n_vapor;             /* 0 .. SNAP_MAX_VAPOR (library builds: 0, 1, 2) */
+  int n_cond;              /* condensates per vapour: 0 or 2 */
+  snap_species species[SNAP_MAX_VAPOR];
+  const double *rho_bar;   /* host [nz]: reference density of each level */
+  const double *p_bar_face;/* host [nz+1]: reference pressure at level faces, discretely
+                              hydrostatic: p_face[k+1] = p_face[k] - grav rho_bar[k] dz
+                              (checked to 1e-9 relative) */
+  int dtype;               /* SNAP_F64 or SNAP_F32: storage and arithmetic of the step */
+  double cfl;              /* dt = cfl / max_cells sum_d (|u_d| + c)/dx_d when no fixed dt */
+  double nu;               /* constant kinematic viscosity, m^2/s (0: none; dry only) */
+  int satadj;              /* 1: saturation adjustment after every stage (needs n_cond > 0) */
+  int satadj_max_iter;     /* sweep limit of the adjustment (e.g. 20) */
+  double satadj_tol;       /* relative stop tolerance on the molar transfer; raised to
+                              4 machine epsilons of dtype when smaller */
+  double weno_eps;         /* epsilon of the WENO5 weights (e.g. 1e-6) */
+} snap_grid_desc;
+
+/* Domain totals: field sums times the cell volume, and sum of (rho e + rho g z) dV. */
+typedef struct snap_budget {
+  int nfields;
+  double total[SNAP_MAX_FIELDS];
+  double energy_with_potential;
+  double dt_last;          /* time step used by the last step, s */
+  unsigned int flags;      /* bit 0: non-finite/non-positive density seen; bit 1: no conv. */
+  int satadj_max_sweeps;   /* largest sweep count of the adjustment since the last reset */
+} snap_budget;
+
+typedef struct snap_ctx snap_ctx;
+
+/* Create a context with n_domains >= 1 domains described by d[0..n_domains-1] (Sec. 2
+ * equations on each). Domains of one context share dtype, n_vapor, n_cond, species table,
+ * gamma_d, R_d, dimensionality and viscosity switch; sizes, spacings, boundaries, grav,
+ * reference profiles and cfl may differ. n_domains > 1 advances all domains in the same
+ * launches (an ensemble). Device memory: 3 state copies per domain plus small tables.
+ * On success *out owns the context; release it with snap_free. */
+int snap_init_grid(snap_ctx **out, const snap_grid_desc *d, int n_domains);
+
+/* Copy the conserved state of one domain in. Y has the layout above with element type
+ * dtype (SNAP_F64 or SNAP_F32, converted to the context's dtype); on_device != 0 means Y is a
+ * device pointer (e.g. a torch CUDA tensor), else host memory (pinned memory is copied
+ * asynchronously). stream: a cudaStream_t to order the copy on, or NULL for the context's.
+ * The CFL rate of the new state is recomputed. */
+int snap_set_state(snap_ctx *ctx, int domain, const void *Y, int dtype, int on_device,
+                   void *stream);
+
+/* Copy the current conserved state of one domain out (same layout and conventions). Host
+ * destinations are written when the call returns. */
+int snap_get_state(snap_ctx *ctx, int domain, void *Y_out, int dtype, int on_device,
+                   void *stream);
+
+/* Advance every domain by nsteps steps of SSP-RK3 (Sec. 4.3); each stage is the fused
+ * WENO5 reconstruction (Sec. 4.2), LMARS flux (Sec. 4.1), flux divergence and gravity source
+ * (Eq. forward), stage combine and saturation adjustment (App. D). dt_fixed > 0 uses that
+ * time step for every domain; otherwise each domain uses its CFL rule from the state at the
+ * start of each step. dt_used (may be NULL) receives domain 0's last time step; out_budget
+ * (may be NULL) receives domain 0's budget after the last step. Returns SNAP_ENONFINITE or
+ * SNAP_ENOCONV when a device check tripped during these steps (the state is still advanced). */
+int snap_step(snap_ctx *ctx, int nsteps, double dt_fixed, double *dt_used,
+              snap_budget *out_budget);
+
+/* Enqueue nsteps steps on the context's stream and return at once: no host synchronisation,
+ * no status read-back (use snap_check). Same dt_fixed meaning as snap_step. */
+int snap_step_async(snap_ctx *ctx, int nsteps, double dt_fixed);
+
+/* Enqueue one Runge-Kutta stage (0, 1 or 2 of Sec. 4.3) for every domain. Stage 0 reads the
+ * state and writes the first intermediate, stage 1 the second, stage 2 writes the new state in
+ * place; a step is the three in order. For timing and tests of single stages. */
+int snap_stage(snap_ctx *ctx, int stage, double dt_fixed);
+
+/* Synchronise the context's stream and report the device checks since the last reset:
+ * SNAP_ENONFINITE, SNAP_ENOCONV or SNAP_OK; flags (may be NULL) receives the raw bits. */
+int snap_check(snap_ctx *ctx, unsigned int *flags);
+
+/* Clear the device check bits and the sweep-count maximum (stream-ordered). */
+int snap_reset_flags(snap_ctx *ctx);
+
+/* Budget of one domain's current state (FP64 sums, deterministic order). */
+int snap_budget_compute(snap_ctx *ctx, int domain, snap_budget *out);
+
+/* CFL time step of one domain's current state (what snap_step would use next). */
+int snap_compute_dt(snap_ctx *ctx, int domain, double *dt);
+
+/* Apply the App. D saturation adjustment to every cell of one domain's current state. */
+int snap_saturation_adjust(snap_ctx *ctx, int domain);
+
+/* Discrete adjoint of snap_step (reverse of the stages with recomputation from checkpoints).
+ * Not built in this library version: returns SNAP_ENOTSUP. */
+int snap_step_adjoint(snap_ctx *ctx, int nsteps, const void *lambda_final, void *lambda_init,
+                      int dtype, void *stream);
+
+/* Order all following work on this cudaStream_t (NULL: the context's own stream). */
+int snap_set_stream(snap_ctx *ctx, void *stream);
+
+/* 1 (default): snap_step replays one captured CUDA graph per step; 0: plain launches. */
+int snap_use_graph(snap_ctx *ctx, int enable);
+
+/* Sizes the context was built with. */
+typedef struct snap_info {
+  int n_domains;
+  int nfields;
+  long long ncells_total;
+  long long state_bytes;      /* bytes of one state copy over all domains */
+  int tile[3];                /* cells per tile in x, y, z */
+  int tiles_total;            /* tiles over all domains */
+  int kernel_launches_per_step;
+} snap_info;
+int snap_get_info(const snap_ctx *ctx, snap_info *info);
+
+/* Device pointer of one of a domain's three state buffers: slot 0 the current state, slot 1
+ * the result of stage 0, slot 2 the result of stage 1 (layout and dtype of the context).
+ * Valid until snap_free; the library writes them during stages. */
+int snap_buffer_pointer(snap_ctx *ctx, int domain, int slot, void **ptr);
+
+void snap_free(snap_ctx *ctx);
+const char *snap_last_error(const snap_ctx *ctx);
+const char *snap_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,272 @@
+"""ctypes binding of the C ABI in include/snap.h (argument marshalling only).
+
+Every step of the numerical method runs in the CUDA library libsnap_gb300.so; this module
+only fills descriptors and passes pointers. Importing it without the built library raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libsnap_gb300.so")
+
+MAX_VAPOR = 4
+MAX_COND = 2
+MAX_FIELDS = 24
+
+OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, ENOCONV, ETIMEOUT, ENOTSUP = 0, -1, -2, -3, -4, -5, -6, -7
+REFLECT, PERIODIC = 0, 1
+F64, F32 = 0, 1
+
+# every function declared in include/snap.h
+EXPORTS = ["snap_init_grid", "snap_set_state", "snap_get_state", "snap_step", "snap_step_async",
+           "snap_stage", "snap_check", "snap_reset_flags", "snap_budget_compute",
+           "snap_compute_dt", "snap_saturation_adjust", "snap_step_adjoint", "snap_set_stream",
+           "snap_use_graph", "snap_get_info", "snap_buffer_pointer", "snap_free",
+           "snap_last_error", "snap_status_string"]
+
+
+class Species(C.Structure):
+    _fields_ = [("eps", C.c_double), ("sigma_v", C.c_double), ("T_ref", C.c_double),
+                ("p_ref", C.c_double), ("sigma_c", C.c_double * MAX_COND),
+                ("L_ref", C.c_double * MAX_COND)]
+
+
+class GridDesc(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+                ("dx", C.c_double), ("dy", C.c_double), ("dz", C.c_double),
+                ("bc", C.c_int * 6), ("grav", C.c_double), ("gamma_d", C.c_double),
+                ("R_d", C.c_double), ("n_vapor", C.c_int), ("n_cond", C.c_int),
+                ("species", Species * MAX_VAPOR),
+                ("rho_bar", C.POINTER(C.c_double)), ("p_bar_face", C.POINTER(C.c_double)),
+                ("dtype", C.c_int), ("cfl", C.c_double), ("nu", C.c_double),
+                ("satadj", C.c_int), ("satadj_max_iter", C.c_int), ("satadj_tol", C.c_double),
+                ("weno_eps", C.c_double)]
+
+
+class Budget(C.Structure):
+    _fields_ = [("nfields", C.c_int), ("total", C.c_double * MAX_FIELDS),
+                ("energy_with_potential", C.c_double), ("dt_last", C.c_double),
+                ("flags", C.c_uint), ("satadj_max_sweeps", C.c_int)]
+
+
+class Info(C.Structure):
+    _fields_ = [("n_domains", C.c_int), ("nfields", C.c_int), ("ncells_total", C.c_longlong),
+                ("state_bytes", C.c_longlong), ("tile", C.c_int * 3), ("tiles_total", C.c_int),
+                ("kernel_launches_per_step", C.c_int)]
+
+
+class SnapError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{msg} (status {code})")
+        self.code = code
+
+
+_LIB = None
+
+
+def load(path: Optional[str] = None) -> C.CDLL:
+    """Load the CUDA library; raises if it has not been built."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise ImportError(f"CUDA library not built: {path} (run __graft_entry__.build())")
+    lib = C.CDLL(path)
+    P = C.c_void_p
+    lib.snap_init_grid.argtypes = [C.POINTER(P), C.POINTER(GridDesc), C.c_int]
+    lib.snap_set_state.argtypes = [P, C.c_int, P, C.c_int, C.c_int, P]
+    lib.snap_get_state.argtypes = [P, C.c_int, P, C.c_int, C.c_int, P]
+    lib.snap_step.argtypes = [P, C.c_int, C.c_double, C.POINTER(C.c_double), C.POINTER(Budget)]
+    lib.snap_step_async.argtypes = [P, C.c_int, C.c_double]
+    lib.snap_stage.argtypes = [P, C.c_int, C.c_double]
+    lib.snap_check.argtypes = [P, C.POINTER(C.c_uint)]
+    lib.snap_reset_flags.argtypes = [P]
+    lib.snap_budget_compute.argtypes = [P, C.c_int, C.POINTER(Budget)]
+    lib.snap_compute_dt.argtypes = [P, C.c_int, C.POINTER(C.c_double)]
+    lib.snap_saturation_adjust.argtypes = [P, C.c_int]
+    lib.snap_step_adjoint.argtypes = [P, C.c_int, P, P, C.c_int, P]
+    lib.snap_set_stream.argtypes = [P, P]
+    lib.snap_use_graph.argtypes = [P, C.c_int]
+    lib.snap_get_info.argtypes = [P, C.POINTER(Info)]
+    lib.snap_buffer_pointer.argtypes = [P, C.c_int, C.c_int, C.POINTER(P)]
+    lib.snap_free.argtypes = [P]
+    lib.snap_free.restype = None
+    lib.snap_last_error.argtypes = [P]
+    lib.snap_last_error.restype = C.c_char_p
+    lib.snap_status_string.argtypes = [C.c_int]
+    lib.snap_status_string.restype = C.c_char_p
+    _LIB = lib
+    return lib
+
+
+def desc_from_workload(w, dtype: Optional[str] = None, satadj: Optional[bool] = None):
+    """GridDesc of a workloads.Workload (the arrays it points to are returned to keep alive)."""
+    d = GridDesc()
+    d.nx, d.ny, d.nz = w.nx, w.ny, w.nz
+    d.dx, d.dy, d.dz = w.dx, w.dy, w.dz
+    for s in range(6):
+        d.bc[s] = int(w.bc[s])
+    d.grav, d.gamma_d, d.R_d = w.grav, w.gamma_d, w.R_d
+    d.n_vapor, d.n_cond = len(w.vapors), w.ncond
+    for i, v in enumerate(w.vapors):
+        sp = d.species[i]
+        sp.eps, sp.sigma_v, sp.T_ref, sp.p_ref = v.eps, v.sigma_v, v.T_ref, v.p_ref
+        for j in range(w.ncond):
+            sp.sigma_c[j] = v.cond[j].sigma_v
+            sp.L_ref[j] = v.cond[j].L_ref
+    keep = (np.ascontiguousarray(w.rho_bar, dtype=np.float64),
+            np.ascontiguousarray(w.p_bar_face, dtype=np.float64))
+    d.rho_bar = keep[0].ctypes.data_as(C.POINTER(C.c_double))
+    d.p_bar_face = keep[1].ctypes.data_as(C.POINTER(C.c_double))
+    dt = w.dtype if dtype is None else dtype
+    d.dtype = F32 if dt == "f32" else F64
+    d.cfl, d.nu = w.cfl, w.nu
+    d.satadj = int((len(w.vapors) > 0 and w.ncond > 0) if satadj is None else satadj)
+    d.satadj_max_iter, d.satadj_tol = w.satadj_max_iter, w.satadj_tol
+    d.weno_eps = w.weno_eps
+    return d, keep
+
+
+class Context:
+    """One library context (snap_ctx) over one or more domains."""
+
+    def __init__(self, workloads: Sequence, dtype: Optional[str] = None,
+                 satadj: Optional[bool] = None):
+        self.lib = load()
+        ws = list(workloads) if isinstance(workloads, (list, tuple)) else [workloads]
+        self.workloads = ws
+        descs, self._keep = [], []
+        for w in ws:
+            d, k = desc_from_workload(w, dtype, satadj)
+            descs.append(d)
+            self._keep.append(k)
+        arr = (GridDesc * len(descs))(*descs)
+        self._ptr = C.c_void_p()
+        rc = self.lib.snap_init_grid(C.byref(self._ptr), arr, len(descs))
+        if rc:
+            raise SnapError(rc, self.lib.snap_last_error(None).decode())
+        self.f32 = descs[0].dtype == F32
+        self.np_dtype = np.float32 if self.f32 else np.float64
+
+    def _check(self, rc):
+        if rc:
+            raise SnapError(rc, self.lib.snap_last_error(self._ptr).decode())
+        return rc
+
+    def close(self):
+        if self._ptr:
+            self.lib.snap_free(self._ptr)
+            self._ptr = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- state --------------------------------------------------------------------------
+    def set_state(self, Y, domain=0, stream=None):
+        """Y: numpy array (host) or torch tensor (CUDA or CPU), float32 or float64."""
+        ptr, dt, dev = _buffer(Y)
+        return self._check(self.lib.snap_set_state(self._ptr, domain, ptr, dt, dev, stream))
+
+    def get_state(self, domain=0, out=None, dtype=np.float64, stream=None):
+        w = self.workloads[domain]
+        if out is None:
+            out = np.empty((w.nv, w.nz, w.ny, w.nx), dtype=dtype)
+        ptr, dt, dev = _buffer(out)
+        self._check(self.lib.snap_get_state(self._ptr, domain, ptr, dt, dev, stream))
+        return out
+
+    # -- stepping -----------------------------------------------------------------------
+    def step(self, nsteps=1, dt_fixed=0.0):
+        dt = C.c_double(0.0)
+        self._check(self.lib.snap_step(self._ptr, nsteps, dt_fixed, C.byref(dt), None))
+        return dt.value
+
+    def step_async(self, nsteps=1, dt_fixed=0.0):
+        return self._check(self.lib.snap_step_async(self._ptr, nsteps, dt_fixed))
+
+    def stage(self, stage, dt_fixed=0.0):
+        return self._check(self.lib.snap_stage(self._ptr, stage, dt_fixed))
+
+    def check(self):
+        f = C.c_uint(0)
+        rc = self.lib.snap_check(self._ptr, C.byref(f))
+        return rc, f.value
+
+    def reset_flags(self):
+        return self._check(self.lib.snap_reset_flags(self._ptr))
+
+    def budget(self, domain=0):
+        b = Budget()
+        self._check(self.lib.snap_budget_compute(self._ptr, domain, C.byref(b)))
+        n = b.nfields
+        return {"total": np.array(b.total[:n]), "energy_with_potential": b.energy_with_potential,
+                "dt_last": b.dt_last, "flags": b.flags, "satadj_max_sweeps": b.satadj_max_sweeps}
+
+    def compute_dt(self, domain=0):
+        dt = C.c_double(0.0)
+        self._check(self.lib.snap_compute_dt(self._ptr, domain, C.byref(dt)))
+        return dt.value
+
+    def saturation_adjust(self, domain=0):
+        return self._check(self.lib.snap_saturation_adjust(self._ptr, domain))
+
+    def set_stream(self, stream):
+        """stream: a torch.cuda.Stream, a raw cudaStream_t integer, or None."""
+        h = getattr(stream, "cuda_stream", stream)
+        return self._check(self.lib.snap_set_stream(self._ptr, h))
+
+    def use_graph(self, enable=True):
+        return self._check(self.lib.snap_use_graph(self._ptr, int(enable)))
+
+    def info(self):
+        i = Info()
+        self._check(self.lib.snap_get_info(self._ptr, C.byref(i)))
+        return {"n_domains": i.n_domains, "nfields": i.nfields, "ncells_total": i.ncells_total,
+                "state_bytes": i.state_bytes, "tile": tuple(i.tile), "tiles_total": i.tiles_total,
+                "kernel_launches_per_step": i.kernel_launches_per_step}
+
+    def buffer_pointer(self, domain=0, slot=0):
+        p = C.c_void_p()
+        self._check(self.lib.snap_buffer_pointer(self._ptr, domain, slot, C.byref(p)))
+        return p.value
+
+    def buffer_view(self, domain=0, slot=0):
+        """Zero-copy torch view of a device state buffer (see snap_buffer_pointer)."""
+        import torch
+        w = self.workloads[domain]
+
+        class _Dev:
+            __cuda_array_interface__ = {
+                "shape": (w.nv, w.nz, w.ny, w.nx),
+                "typestr": "<f4" if self.f32 else "<f8",
+                "data": (self.buffer_pointer(domain, slot), False),
+                "version": 2,
+            }
+
+        return torch.as_tensor(_Dev(), device="cuda")
+
+
+def _buffer(Y):
+    """(pointer, dtype code, on_device) of a numpy array or torch tensor."""
+    if isinstance(Y, np.ndarray):
+        if not Y.flags["C_CONTIGUOUS"]:
+            raise ValueError("state array must be C-contiguous")
+        if Y.dtype == np.float64:
+            return C.c_void_p(Y.ctypes.data), F64, 0
+        if Y.dtype == np.float32:
+            return C.c_void_p(Y.ctypes.data), F32, 0
+        raise TypeError("state must be float32 or float64")
+    import torch  # torch tensors: plumbing only (memory and streams)
+    if not Y.is_contiguous():
+        raise ValueError("state tensor must be contiguous")
+    code = {torch.float64: F64, torch.float32: F32}[Y.dtype]
+    return C.c_void_p(Y.data_ptr()), code, int(Y.is_cuda)

@@ -1,0 +1,631 @@
+// capi.cu -- host side of the C ABI declared in include/snap.h: validation, device memory,
+// launch sequencing of the Runge-Kutta stages (Sec. 4.3), CUDA-graph replay, budgets and
+// status reporting.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/snap.h"
+#include "snap_internal.h"
+
+namespace snap {
+bool find_kernels_dry2d(int f32, int visc, KernelSet *out);
+bool find_kernels_dry3d(int f32, int visc, KernelSet *out);
+bool find_kernels_moist2d(int f32, int visc, KernelSet *out);
+bool find_kernels_moist3d(int f32, int visc, KernelSet *out);
+
+bool find_kernels(int f32, int nvap, int ncond, int three_d, int visc, KernelSet *out) {
+  if (nvap == 0 && ncond == 0) return three_d ? find_kernels_dry3d(f32, visc, out)
+                                              : find_kernels_dry2d(f32, visc, out);
+  if (nvap == 1 && ncond == 2 && !three_d) return find_kernels_moist2d(f32, visc, out);
+  if (nvap == 2 && ncond == 2 && three_d) return find_kernels_moist3d(f32, visc, out);
+  return false;
+}
+
+int budget_blocks(long long ncell) {
+  long long b = (ncell + 255) / 256;
+  return int(b < 1 ? 1 : (b > 1024 ? 1024 : b));
+}
+
+template <class S, class D>
+__global__ void convert_kernel(const S *src, D *dst, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    dst[i] = D(src[i]);
+}
+
+cudaError_t launch_convert(const void *src, int src_f32, void *dst, int dst_f32, long long n,
+                           cudaStream_t s) {
+  const int grid = 1216, block = 256;
+  if (src_f32 && !dst_f32)
+    convert_kernel<float, double><<<grid, block, 0, s>>>((const float *)src, (double *)dst, n);
+  else if (!src_f32 && dst_f32)
+    convert_kernel<double, float><<<grid, block, 0, s>>>((const double *)src, (float *)dst, n);
+  else if (src_f32)
+    convert_kernel<float, float><<<grid, block, 0, s>>>((const float *)src, (float *)dst, n);
+  else
+    convert_kernel<double, double><<<grid, block, 0, s>>>((const double *)src, (double *)dst, n);
+  return cudaGetLastError();
+}
+}  // namespace snap
+
+using namespace snap;
+
+struct snap_ctx {
+  int ndom = 0;
+  int f32 = 0, nvap = 0, ncond = 0, three_d = 0, visc = 0, nv = 0;
+  size_t word = 8;
+  KernelSet ks{};
+  Phys ph{};
+  std::vector<snap_grid_desc> desc;
+  std::vector<DomDev> dom;   // host mirror of doms_dev
+  std::vector<int> prefix;   // tile prefix per domain
+  int ntiles = 0, grid = 0;
+  // device memory
+  void *arena = nullptr;
+  DomDev *doms_dev = nullptr;
+  int *prefix_dev = nullptr;
+  double *prof_dev = nullptr;
+  unsigned long long *rate_dev = nullptr;
+  double *dt_dev = nullptr;
+  unsigned int *flags_dev = nullptr;
+  int *sweeps_dev = nullptr;
+  double *budget_partials = nullptr;
+  double *budget_out = nullptr;
+  void *staging = nullptr;
+  size_t staging_bytes = 0;
+  long long state_bytes = 0, ncells = 0;
+  // execution
+  cudaStream_t own_stream = nullptr, stream = nullptr;
+  int use_graph = 1;
+  cudaGraphExec_t graph = nullptr;
+  double graph_dt = -1.0;
+  std::string err;
+};
+
+static thread_local std::string g_init_error;
+
+static int fail(snap_ctx *c, int code, const std::string &msg) {
+  if (c)
+    c->err = msg;
+  else
+    g_init_error = msg;
+  return code;
+}
+
+static int cuda_fail(snap_ctx *c, cudaError_t e, const char *where) {
+  std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+  if (e == cudaErrorMemoryAllocation) return fail(c, SNAP_ENOMEM, m);
+  return fail(c, SNAP_ECUDA, m);
+}
+
+#define CK(call)                                              \
+  do {                                                        \
+    cudaError_t e_ = (call);                                  \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call);  \
+  } while (0)
+
+static void release(snap_ctx *ctx) {
+  if (!ctx) return;
+  if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
+  cudaFree(ctx->arena);
+  cudaFree(ctx->doms_dev);
+  cudaFree(ctx->prefix_dev);
+  cudaFree(ctx->prof_dev);
+  cudaFree(ctx->rate_dev);
+  cudaFree(ctx->dt_dev);
+  cudaFree(ctx->flags_dev);
+  cudaFree(ctx->sweeps_dev);
+  cudaFree(ctx->budget_partials);
+  cudaFree(ctx->budget_out);
+  cudaFree(ctx->staging);
+  if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
+}
+
+static int validate(const snap_grid_desc &d, const snap_grid_desc &d0, int idx, std::string &m) {
+  char b[256];
+  auto bad = [&](const char *what) {
+    snprintf(b, sizeof b, "domain %d: %s", idx, what);
+    m = b;
+    return SNAP_EINVAL;
+  };
+  if (d.nx < 3 || d.nz < 3 || d.ny < 1 || d.ny == 2) return bad("need nx >= 3, nz >= 3, ny == 1 or ny >= 3");
+  if (!(d.dx > 0) || !(d.dz > 0) || (d.ny > 1 && !(d.dy > 0))) return bad("cell sizes must be positive");
+  for (int s = 0; s < 6; ++s)
+    if (d.bc[s] != SNAP_REFLECT && d.bc[s] != SNAP_PERIODIC) return bad("bc must be REFLECT or PERIODIC");
+  if (d.bc[4] != SNAP_REFLECT || d.bc[5] != SNAP_REFLECT) return bad("the z boundaries must reflect");
+  if ((d.bc[0] == SNAP_PERIODIC) != (d.bc[1] == SNAP_PERIODIC)) return bad("periodic x needs both x sides periodic");
+  if ((d.bc[2] == SNAP_PERIODIC) != (d.bc[3] == SNAP_PERIODIC)) return bad("periodic y needs both y sides periodic");
+  if (!(d.gamma_d > 1.0) || !(d.R_d > 0.0)) return bad("gamma_d > 1 and R_d > 0 required");
+  if (!(d.grav >= 0.0)) return bad("grav must be >= 0");
+  if (!(d.cfl > 0.0)) return bad("cfl must be > 0");
+  if (!(d.weno_eps > 0.0)) return bad("weno_eps must be > 0");
+  if (d.n_vapor < 0 || d.n_vapor > SNAP_MAX_VAPOR) return bad("n_vapor out of range");
+  if (d.n_cond < 0 || d.n_cond > SNAP_MAX_COND) return bad("n_cond out of range");
+  if (d.dtype != SNAP_F64 && d.dtype != SNAP_F32) return bad("dtype must be SNAP_F64 or SNAP_F32");
+  if (d.satadj && (d.n_vapor == 0 || d.n_cond == 0)) return bad("satadj needs vapours with condensates");
+  if (d.satadj && d.satadj_max_iter < 1) return bad("satadj_max_iter must be >= 1");
+  if (!(d.nu >= 0.0)) return bad("nu must be >= 0");
+  if (!d.rho_bar || !d.p_bar_face) return bad("reference profile pointers are NULL");
+  for (int k = 0; k < d.nz; ++k) {
+    if (!(d.rho_bar[k] > 0) || !(d.p_bar_face[k] > 0) || !(d.p_bar_face[k + 1] > 0))
+      return bad("reference profile must be positive");
+    double want = d.p_bar_face[k] - d.grav * d.rho_bar[k] * d.dz;
+    if (fabs(d.p_bar_face[k + 1] - want) > 1e-9 * d.p_bar_face[k])
+      return bad("reference profile is not discretely hydrostatic");
+  }
+  if (d.dtype != d0.dtype || d.n_vapor != d0.n_vapor || d.n_cond != d0.n_cond ||
+      (d.ny > 1) != (d0.ny > 1) || d.gamma_d != d0.gamma_d || d.R_d != d0.R_d ||
+      (d.nu > 0) != (d0.nu > 0) || d.nu != d0.nu || d.satadj != d0.satadj ||
+      d.weno_eps != d0.weno_eps)
+    return bad("domains of one context must share dtype, species, gases, dimensionality, "
+               "viscosity and scheme options");
+  for (int i = 0; i < d.n_vapor; ++i) {
+    const snap_species &s = d.species[i], &s0 = d0.species[i];
+    if (!(s.eps > 0) || !(s.sigma_v > 0) || !(s.T_ref > 0) || !(s.p_ref > 0))
+      return bad("species constants must be positive");
+    if (memcmp(&s, &s0, sizeof s) != 0) return bad("domains must share the species table");
+  }
+  return SNAP_OK;
+}
+
+static void derive_phys(const snap_grid_desc &d, Phys &ph) {
+  memset(&ph, 0, sizeof ph);
+  ph.gamma_d = d.gamma_d;
+  ph.R_d = d.R_d;
+  ph.c_vd = d.R_d / (d.gamma_d - 1.0);
+  ph.c_pd = d.gamma_d * ph.c_vd;
+  ph.kappa = d.R_d / ph.c_pd;
+  ph.nvap = d.n_vapor;
+  ph.ncond = d.n_cond;
+  for (int i = 0; i < d.n_vapor; ++i) {
+    const snap_species &s = d.species[i];
+    ph.eps[i] = s.eps;
+    ph.inv_eps[i] = 1.0 / s.eps;
+    ph.sig_v[i] = s.sigma_v;
+    ph.R_v[i] = d.R_d / s.eps;
+    ph.sig_hat[i] = s.sigma_v * s.eps;
+    ph.Tref[i] = s.T_ref;
+    ph.pref[i] = s.p_ref;
+    const double c_pv = s.sigma_v * ph.c_vd + ph.R_v[i];
+    for (int j = 0; j < d.n_cond; ++j) {
+      ph.sig_c[i][j] = s.sigma_c[j];
+      const double dc = s.sigma_c[j] * ph.c_vd - c_pv;   // Eq. latent
+      ph.mu[i][j] = -(s.L_ref[j] + dc * s.T_ref);         // Eq. muij with mu_i = 0
+    }
+    if (d.n_cond > 0) {
+      const double dc = s.sigma_c[0] * ph.c_vd - c_pv;
+      ph.beta[i] = (s.L_ref[0] + dc * s.T_ref) / (ph.R_v[i] * s.T_ref);  // App. D
+      ph.delta[i] = dc / ph.R_v[i];
+    }
+  }
+  ph.weno_eps = d.weno_eps;
+  ph.nu = d.nu;
+  ph.satadj = d.satadj;
+  ph.satadj_max_iter = d.satadj_max_iter;
+  ph.satadj_tol = d.satadj_tol;
+}
+
+static StageArgs args_of(snap_ctx *ctx, int stage) {
+  StageArgs a;
+  a.doms = ctx->doms_dev;
+  a.tile_domain = ctx->prefix_dev;
+  a.ndom = ctx->ndom;
+  a.ntiles = ctx->ntiles;
+  a.stage = stage;
+  a.flags = ctx->flags_dev;
+  a.max_sweeps = ctx->sweeps_dev;
+  a.ph = ctx->ph;
+  return a;
+}
+
+static int refresh_rate(snap_ctx *ctx, int dm, cudaStream_t s) {
+  CK(cudaMemsetAsync(ctx->rate_dev + dm, 0, sizeof(unsigned long long), s));
+  StageArgs a = args_of(ctx, 0);
+  CK(ctx->ks.rate(a, dm, 0, s));
+  return SNAP_OK;
+}
+
+extern "C" int snap_init_grid(snap_ctx **out, const snap_grid_desc *d, int n_domains) {
+  snap_ctx *ctx = nullptr;
+  if (!out || !d || n_domains < 1) return fail(nullptr, SNAP_EINVAL, "snap_init_grid: bad arguments");
+  *out = nullptr;
+  std::string m;
+  for (int i = 0; i < n_domains; ++i) {
+    int rc = validate(d[i], d[0], i, m);
+    if (rc) return fail(nullptr, rc, m);
+  }
+  ctx = new (std::nothrow) snap_ctx();
+  if (!ctx) return fail(nullptr, SNAP_ENOMEM, "snap_init_grid: host allocation failed");
+  ctx->ndom = n_domains;
+  ctx->f32 = d[0].dtype == SNAP_F32;
+  ctx->nvap = d[0].n_vapor;
+  ctx->ncond = d[0].n_cond;
+  ctx->three_d = d[0].ny > 1;
+  ctx->visc = d[0].nu > 0.0;
+  ctx->nv = 1 + ctx->nvap + ctx->nvap * ctx->ncond + (ctx->three_d ? 3 : 2) + 1;
+  ctx->word = ctx->f32 ? 4 : 8;
+  if (!find_kernels(ctx->f32, ctx->nvap, ctx->ncond, ctx->three_d, ctx->visc, &ctx->ks)) {
+    delete ctx;
+    return fail(nullptr, SNAP_ENOTSUP,
+                "snap_init_grid: this library builds dry (any dimension, optional viscosity), "
+                "one vapour with two condensates (x-z plane) and two vapours with two "
+                "condensates (3-D) without viscosity");
+  }
+  derive_phys(d[0], ctx->ph);
+  ctx->desc.assign(d, d + n_domains);
+  cudaError_t e = ctx->ks.prepare();
+  if (e != cudaSuccess) {
+    int rc = cuda_fail(nullptr, e, "snap_init_grid: kernel attributes");
+    delete ctx;
+    return rc;
+  }
+  // layout of the state arena and tile table
+  std::vector<size_t> off(n_domains);
+  size_t total = 0, maxcell = 0;
+  size_t nprof = 0;
+  ctx->prefix.assign(n_domains + 1, 0);
+  ctx->dom.resize(n_domains);
+  for (int i = 0; i < n_domains; ++i) {
+    const snap_grid_desc &g = d[i];
+    size_t nc = (size_t)g.nx * g.ny * g.nz;
+    size_t bytes = ((nc * ctx->nv * ctx->word) + 255) / 256 * 256;
+    off[i] = total;
+    total += 3 * bytes;
+    maxcell = nc > maxcell ? nc : maxcell;
+    ctx->ncells += (long long)nc;
+    ctx->state_bytes += (long long)(nc * ctx->nv * ctx->word);
+    nprof += 3 * (size_t)g.nz + 1;
+    DomDev &D = ctx->dom[i];
+    D.nx = g.nx;
+    D.ny = g.ny;
+    D.nz = g.nz;
+    D.tx = (g.nx + ctx->ks.tile[0] - 1) / ctx->ks.tile[0];
+    D.ty = (g.ny + ctx->ks.tile[1] - 1) / ctx->ks.tile[1];
+    D.tz = (g.nz + ctx->ks.tile[2] - 1) / ctx->ks.tile[2];
+    D.tile_begin = ctx->prefix[i];
+    ctx->prefix[i + 1] = ctx->prefix[i] + D.tx * D.ty * D.tz;
+    for (int s = 0; s < 6; ++s) D.bc[s] = g.bc[s];
+    D.dx = g.dx;
+    D.dy = g.ny > 1 ? g.dy : g.dx;
+    D.dz = g.dz;
+    D.grav = g.grav;
+    D.cfl = g.cfl;
+    D.dt_fixed = -1.0;
+    D.ncell = (long long)nc;
+    (void)bytes;
+  }
+  ctx->ntiles = ctx->prefix[n_domains];
+  int ret = SNAP_OK;
+  do {
+    ctx->grid = ctx->ntiles;
+    if ((e = cudaStreamCreateWithFlags(&ctx->own_stream, cudaStreamNonBlocking)) != cudaSuccess) break;
+    ctx->stream = ctx->own_stream;
+    if ((e = cudaMalloc(&ctx->arena, total)) != cudaSuccess) break;
+    if ((e = cudaMemset(ctx->arena, 0, total)) != cudaSuccess) break;
+    if ((e = cudaMalloc(&ctx->doms_dev, sizeof(DomDev) * n_domains)) != cudaSuccess) break;
+    if ((e = cudaMalloc(&ctx->prefix_dev, sizeof(int) * (n_domains + 1))) != cudaSuccess) break;
+    if ((e = cudaMalloc(&ctx->prof_dev, sizeof(double) * nprof)) != cudaSuccess) break;
+    if ((e = cudaMalloc(&ctx->rate_dev, sizeof(unsigned long long) * n_domains)) != cudaSuccess) break;
+    if ((e = cudaMalloc(&ctx->dt_dev, sizeof(double) * n_domains)) != cudaSuccess) break;
+    if ((e = cudaMalloc(&ctx->flags_dev, sizeof(unsigned int))) != cudaSuccess) break;
+    if ((e = cudaMalloc(&ctx->sweeps_dev, sizeof(int))) != cudaSuccess) break;
+    if ((e = cudaMalloc(&ctx->budget_partials, sizeof(double) * 1024 * (ctx->nv + 1))) != cudaSuccess) break;
+    if ((e = cudaMalloc(&ctx->budget_out, sizeof(double) * (ctx->nv + 1))) != cudaSuccess) break;
+    ctx->staging_bytes = maxcell * ctx->nv * 8;
+    if ((e = cudaMalloc(&ctx->staging, ctx->staging_bytes)) != cudaSuccess) break;
+    if ((e = cudaMemset(ctx->rate_dev, 0, sizeof(unsigned long long) * n_domains)) != cudaSuccess) break;
+    if ((e = cudaMemset(ctx->dt_dev, 0, sizeof(double) * n_domains)) != cudaSuccess) break;
+    if ((e = cudaMemset(ctx->flags_dev, 0, sizeof(unsigned int))) != cudaSuccess) break;
+    if ((e = cudaMemset(ctx->sweeps_dev, 0, sizeof(int))) != cudaSuccess) break;
+    std::vector<double> prof(nprof);
+    size_t po = 0;
+    for (int i = 0; i < n_domains; ++i) {
+      const snap_grid_desc &g = d[i];
+      DomDev &D = ctx->dom[i];
+      size_t nc = (size_t)g.nx * g.ny * g.nz;
+      size_t bytes = ((nc * ctx->nv * ctx->word) + 255) / 256 * 256;
+      for (int b = 0; b < 3; ++b) D.buf[b] = (char *)ctx->arena + off[i] + b * bytes;
+      double *rb = ctx->prof_dev + po, *pf = rb + g.nz, *pc = pf + g.nz + 1;
+      for (int k = 0; k < g.nz; ++k) {
+        prof[po + k] = g.rho_bar[k];
+        prof[po + g.nz + 1 + g.nz + k] = 0.5 * (g.p_bar_face[k] + g.p_bar_face[k + 1]);
+      }
+      for (int k = 0; k <= g.nz; ++k) prof[po + g.nz + k] = g.p_bar_face[k];
+      D.rho_bar = rb;
+      D.p_face = pf;
+      D.p_cell = pc;
+      D.rate = ctx->rate_dev + i;
+      D.dt_step = ctx->dt_dev + i;
+      po += 3 * (size_t)g.nz + 1;
+    }
+    if ((e = cudaMemcpy(ctx->prof_dev, prof.data(), sizeof(double) * nprof, cudaMemcpyHostToDevice)) != cudaSuccess) break;
+    if ((e = cudaMemcpy(ctx->doms_dev, ctx->dom.data(), sizeof(DomDev) * n_domains, cudaMemcpyHostToDevice)) != cudaSuccess) break;
+    if ((e = cudaMemcpy(ctx->prefix_dev, ctx->prefix.data(), sizeof(int) * (n_domains + 1), cudaMemcpyHostToDevice)) != cudaSuccess) break;
+  } while (0);
+  if (e != cudaSuccess) {
+    ret = cuda_fail(nullptr, e, "snap_init_grid");
+    release(ctx);
+    delete ctx;
+    return ret;
+  }
+  *out = ctx;
+  return SNAP_OK;
+}
+
+static cudaStream_t pick(snap_ctx *ctx, void *stream) {
+  return stream ? (cudaStream_t)stream : ctx->stream;
+}
+
+extern "C" int snap_set_state(snap_ctx *ctx, int domain, const void *Y, int dtype, int on_device,
+                              void *stream) {
+  if (!ctx) return fail(nullptr, SNAP_EINVAL, "snap_set_state: NULL context");
+  if (domain < 0 || domain >= ctx->ndom || !Y || (dtype != SNAP_F64 && dtype != SNAP_F32))
+    return fail(ctx, SNAP_EINVAL, "snap_set_state: bad domain, pointer or dtype");
+  cudaStream_t s = pick(ctx, stream);
+  const DomDev &D = ctx->dom[domain];
+  const long long n = D.ncell * ctx->nv;
+  const int src_f32 = dtype == SNAP_F32;
+  const size_t sw = src_f32 ? 4 : 8;
+  if (src_f32 == ctx->f32) {
+    CK(cudaMemcpyAsync(D.buf[0], Y, n * sw, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+  } else if (on_device) {
+    CK(launch_convert(Y, src_f32, D.buf[0], ctx->f32, n, s));
+  } else {
+    CK(cudaMemcpyAsync(ctx->staging, Y, n * sw, cudaMemcpyHostToDevice, s));
+    CK(launch_convert(ctx->staging, src_f32, D.buf[0], ctx->f32, n, s));
+  }
+  return refresh_rate(ctx, domain, s);
+}
+
+extern "C" int snap_get_state(snap_ctx *ctx, int domain, void *Y_out, int dtype, int on_device,
+                              void *stream) {
+  if (!ctx) return fail(nullptr, SNAP_EINVAL, "snap_get_state: NULL context");
+  if (domain < 0 || domain >= ctx->ndom || !Y_out || (dtype != SNAP_F64 && dtype != SNAP_F32))
+    return fail(ctx, SNAP_EINVAL, "snap_get_state: bad domain, pointer or dtype");
+  cudaStream_t s = pick(ctx, stream);
+  const DomDev &D = ctx->dom[domain];
+  const long long n = D.ncell * ctx->nv;
+  const int dst_f32 = dtype == SNAP_F32;
+  const size_t dw = dst_f32 ? 4 : 8;
+  if (dst_f32 == ctx->f32) {
+    CK(cudaMemcpyAsync(Y_out, D.buf[0], n * dw, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+  } else if (on_device) {
+    CK(launch_convert(D.buf[0], ctx->f32, Y_out, dst_f32, n, s));
+  } else {
+    CK(launch_convert(D.buf[0], ctx->f32, ctx->staging, dst_f32, n, s));
+    CK(cudaMemcpyAsync(Y_out, ctx->staging, n * dw, cudaMemcpyDeviceToHost, s));
+  }
+  if (!on_device) CK(cudaStreamSynchronize(s));
+  return SNAP_OK;
+}
+
+static int set_dt_fixed(snap_ctx *ctx, double dt_fixed) {
+  bool changed = false;
+  for (int i = 0; i < ctx->ndom; ++i) {
+    double want = dt_fixed > 0.0 ? dt_fixed : -1.0;
+    if (ctx->dom[i].dt_fixed != want) {
+      ctx->dom[i].dt_fixed = want;
+      changed = true;
+    }
+  }
+  if (changed)
+    CK(cudaMemcpyAsync(ctx->doms_dev, ctx->dom.data(), sizeof(DomDev) * ctx->ndom,
+                       cudaMemcpyHostToDevice, ctx->stream));
+  return SNAP_OK;
+}
+
+static int enqueue_stages(snap_ctx *ctx, cudaStream_t s) {
+  for (int st = 0; st < 3; ++st) {
+    StageArgs a = args_of(ctx, st);
+    CK(ctx->ks.stage(a, ctx->grid, s));
+  }
+  return SNAP_OK;
+}
+
+extern "C" int snap_stage(snap_ctx *ctx, int stage, double dt_fixed) {
+  if (!ctx) return fail(nullptr, SNAP_EINVAL, "snap_stage: NULL context");
+  if (stage < 0 || stage > 2) return fail(ctx, SNAP_EINVAL, "snap_stage: stage must be 0, 1 or 2");
+  int rc = set_dt_fixed(ctx, dt_fixed);
+  if (rc) return rc;
+  StageArgs a = args_of(ctx, stage);
+  CK(ctx->ks.stage(a, ctx->grid, ctx->stream));
+  return SNAP_OK;
+}
+
+extern "C" int snap_step_async(snap_ctx *ctx, int nsteps, double dt_fixed) {
+  if (!ctx) return fail(nullptr, SNAP_EINVAL, "snap_step_async: NULL context");
+  if (nsteps < 0) return fail(ctx, SNAP_EINVAL, "snap_step_async: nsteps < 0");
+  if (nsteps == 0) return SNAP_OK;
+  int rc = set_dt_fixed(ctx, dt_fixed);
+  if (rc) return rc;
+  if (!ctx->use_graph) {
+    for (int n = 0; n < nsteps; ++n) {
+      rc = enqueue_stages(ctx, ctx->stream);
+      if (rc) return rc;
+    }
+    return SNAP_OK;
+  }
+  if (!ctx->graph) {
+    cudaGraph_t g = nullptr;
+    cudaStream_t cap = nullptr;
+    CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      rc = enqueue_stages(ctx, cap);
+      cudaError_t e2 = cudaStreamEndCapture(cap, &g);
+      if (rc == SNAP_OK && e2 != cudaSuccess) e = e2;
+    }
+    if (e == cudaSuccess && rc == SNAP_OK) e = cudaGraphInstantiate(&ctx->graph, g, 0);
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cap);
+    if (rc) return rc;
+    if (e != cudaSuccess) {
+      ctx->graph = nullptr;
+      return cuda_fail(ctx, e, "snap_step_async: graph capture");
+    }
+  }
+  for (int n = 0; n < nsteps; ++n) CK(cudaGraphLaunch(ctx->graph, ctx->stream));
+  return SNAP_OK;
+}
+
+static int read_status(snap_ctx *ctx, unsigned int *flags_out, int *sweeps_out) {
+  unsigned int flags = 0;
+  int sweeps = 0;
+  CK(cudaMemcpyAsync(&flags, ctx->flags_dev, sizeof flags, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(&sweeps, ctx->sweeps_dev, sizeof sweeps, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (flags_out) *flags_out = flags;
+  if (sweeps_out) *sweeps_out = sweeps;
+  return SNAP_OK;
+}
+
+extern "C" int snap_budget_compute(snap_ctx *ctx, int domain, snap_budget *out) {
+  if (!ctx) return fail(nullptr, SNAP_EINVAL, "snap_budget_compute: NULL context");
+  if (domain < 0 || domain >= ctx->ndom || !out) return fail(ctx, SNAP_EINVAL, "snap_budget_compute: bad arguments");
+  StageArgs a = args_of(ctx, 0);
+  const int nb = budget_blocks(ctx->dom[domain].ncell);
+  CK(ctx->ks.budget(a, domain, 0, ctx->budget_partials, nb, ctx->budget_out, ctx->stream));
+  double host[SNAP_MAX_FIELDS + 1];
+  CK(cudaMemcpyAsync(host, ctx->budget_out, sizeof(double) * (ctx->nv + 1), cudaMemcpyDeviceToHost, ctx->stream));
+  double dt = 0.0;
+  CK(cudaMemcpyAsync(&dt, ctx->dt_dev + domain, sizeof dt, cudaMemcpyDeviceToHost, ctx->stream));
+  unsigned int flags = 0;
+  int sweeps = 0;
+  int rc = read_status(ctx, &flags, &sweeps);
+  if (rc) return rc;
+  memset(out, 0, sizeof *out);
+  out->nfields = ctx->nv;
+  for (int v = 0; v < ctx->nv; ++v) out->total[v] = host[v];
+  out->energy_with_potential = host[ctx->nv];
+  out->dt_last = dt;
+  out->flags = flags;
+  out->satadj_max_sweeps = sweeps;
+  return SNAP_OK;
+}
+
+extern "C" int snap_check(snap_ctx *ctx, unsigned int *flags) {
+  if (!ctx) return fail(nullptr, SNAP_EINVAL, "snap_check: NULL context");
+  unsigned int f = 0;
+  int rc = read_status(ctx, &f, nullptr);
+  if (rc) return rc;
+  if (flags) *flags = f;
+  if (f & kFlagNonFinite) return fail(ctx, SNAP_ENONFINITE, "a step produced a non-finite value or non-positive density");
+  if (f & kFlagNoConv) return fail(ctx, SNAP_ENOCONV, "saturation adjustment did not converge in some cell");
+  return SNAP_OK;
+}
+
+extern "C" int snap_step(snap_ctx *ctx, int nsteps, double dt_fixed, double *dt_used,
+                         snap_budget *out_budget) {
+  if (!ctx) return fail(nullptr, SNAP_EINVAL, "snap_step: NULL context");
+  CK(cudaMemsetAsync(ctx->flags_dev, 0, sizeof(unsigned int), ctx->stream));
+  int rc = snap_step_async(ctx, nsteps, dt_fixed);
+  if (rc) return rc;
+  if (dt_used) {
+    CK(cudaMemcpyAsync(dt_used, ctx->dt_dev, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  }
+  if (out_budget) {
+    rc = snap_budget_compute(ctx, 0, out_budget);
+    if (rc) return rc;
+  }
+  return snap_check(ctx, nullptr);
+}
+
+extern "C" int snap_reset_flags(snap_ctx *ctx) {
+  if (!ctx) return fail(nullptr, SNAP_EINVAL, "snap_reset_flags: NULL context");
+  CK(cudaMemsetAsync(ctx->flags_dev, 0, sizeof(unsigned int), ctx->stream));
+  CK(cudaMemsetAsync(ctx->sweeps_dev, 0, sizeof(int), ctx->stream));
+  return SNAP_OK;
+}
+
+extern "C" int snap_compute_dt(snap_ctx *ctx, int domain, double *dt) {
+  if (!ctx) return fail(nullptr, SNAP_EINVAL, "snap_compute_dt: NULL context");
+  if (domain < 0 || domain >= ctx->ndom || !dt) return fail(ctx, SNAP_EINVAL, "snap_compute_dt: bad arguments");
+  int rc = refresh_rate(ctx, domain, ctx->stream);
+  if (rc) return rc;
+  unsigned long long bits = 0;
+  CK(cudaMemcpyAsync(&bits, ctx->rate_dev + domain, sizeof bits, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  double r;
+  memcpy(&r, &bits, sizeof r);
+  *dt = ctx->dom[domain].cfl / r;
+  return SNAP_OK;
+}
+
+extern "C" int snap_saturation_adjust(snap_ctx *ctx, int domain) {
+  if (!ctx) return fail(nullptr, SNAP_EINVAL, "snap_saturation_adjust: NULL context");
+  if (domain < 0 || domain >= ctx->ndom) return fail(ctx, SNAP_EINVAL, "snap_saturation_adjust: bad domain");
+  if (ctx->nvap == 0 || ctx->ncond == 0) return fail(ctx, SNAP_EINVAL, "snap_saturation_adjust: dry context");
+  StageArgs a = args_of(ctx, 0);
+  CK(ctx->ks.satadj(a, domain, 0, ctx->stream));
+  int rc = refresh_rate(ctx, domain, ctx->stream);
+  if (rc) return rc;
+  return snap_check(ctx, nullptr);
+}
+
+extern "C" int snap_step_adjoint(snap_ctx *ctx, int nsteps, const void *lambda_final,
+                                 void *lambda_init, int dtype, void *stream) {
+  (void)nsteps; (void)lambda_final; (void)lambda_init; (void)dtype; (void)stream;
+  return fail(ctx, SNAP_ENOTSUP, "snap_step_adjoint: the discrete adjoint is not built into this library version");
+}
+
+extern "C" int snap_set_stream(snap_ctx *ctx, void *stream) {
+  if (!ctx) return fail(nullptr, SNAP_EINVAL, "snap_set_stream: NULL context");
+  ctx->stream = stream ? (cudaStream_t)stream : ctx->own_stream;
+  return SNAP_OK;
+}
+
+extern "C" int snap_use_graph(snap_ctx *ctx, int enable) {
+  if (!ctx) return fail(nullptr, SNAP_EINVAL, "snap_use_graph: NULL context");
+  ctx->use_graph = enable ? 1 : 0;
+  return SNAP_OK;
+}
+
+extern "C" int snap_get_info(const snap_ctx *ctx, snap_info *info) {
+  if (!ctx || !info) return SNAP_EINVAL;
+  info->n_domains = ctx->ndom;
+  info->nfields = ctx->nv;
+  info->ncells_total = ctx->ncells;
+  info->state_bytes = ctx->state_bytes;
+  for (int i = 0; i < 3; ++i) info->tile[i] = ctx->ks.tile[i];
+  info->tiles_total = ctx->ntiles;
+  info->kernel_launches_per_step = 3;
+  return SNAP_OK;
+}
+
+extern "C" int snap_buffer_pointer(snap_ctx *ctx, int domain, int slot, void **ptr) {
+  if (!ctx || !ptr || domain < 0 || domain >= ctx->ndom || slot < 0 || slot > 2)
+    return SNAP_EINVAL;
+  *ptr = ctx->dom[domain].buf[slot];
+  return SNAP_OK;
+}
+
+extern "C" void snap_free(snap_ctx *ctx) {
+  if (!ctx) return;
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  release(ctx);
+  delete ctx;
+}
+
+extern "C" const char *snap_last_error(const snap_ctx *ctx) {
+  return ctx ? ctx->err.c_str() : g_init_error.c_str();
+}
+
+extern "C" const char *snap_status_string(int status) {
+  switch (status) {
+    case SNAP_OK: return "ok";
+    case SNAP_EINVAL: return "invalid argument";
+    case SNAP_ENOMEM: return "out of memory";
+    case SNAP_ECUDA: return "CUDA error";
+    case SNAP_ENONFINITE: return "non-finite value or non-positive density";
+    case SNAP_ENOCONV: return "saturation adjustment did not converge";
+    case SNAP_ETIMEOUT: return "device wait timed out";
+    case SNAP_ENOTSUP: return "not supported by this build";
+    default: return "unknown status";
+  }
+}

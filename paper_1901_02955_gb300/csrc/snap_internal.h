@@ -1,0 +1,83 @@
+// snap_internal.h -- structures shared by the host library (capi.cu) and the kernel
+// translation units. Not part of the public ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace snap {
+
+constexpr int kMaxVap = 4;
+constexpr int kMaxCond = 2;
+
+// Physical constants of a context, derived on the host from snap_grid_desc (Sec. 2, App. A).
+struct Phys {
+  double gamma_d, R_d, c_vd, c_pd, kappa;  // kappa = R_d / c_pd
+  int nvap, ncond;
+  double eps[kMaxVap], inv_eps[kMaxVap];
+  double sig_v[kMaxVap];                   // c_v,i / c_vd
+  double sig_c[kMaxVap][kMaxCond];         // c_ij / c_vd
+  double mu[kMaxVap][kMaxCond];            // chemical potential of condensate ij, mu_i = 0
+  double Tref[kMaxVap], pref[kMaxVap];     // saturation curve over condensate (i,0)
+  double beta[kMaxVap], delta[kMaxVap];    // Clausius-Clapeyron constants (App. D)
+  double R_v[kMaxVap];                     // R_d / eps_i
+  double sig_hat[kMaxVap];                 // molar c_v,i / c_vd = sigma_v,i * eps_i
+  double weno_eps;
+  double nu;
+  int satadj, satadj_max_iter;
+  double satadj_tol;
+};
+
+// One domain as the kernels see it (device memory).
+struct DomDev {
+  int nx, ny, nz;
+  int tx, ty, tz;            // tiles per direction
+  int tile_begin;            // first tile index of this domain in the launch
+  int bc[6];
+  double dx, dy, dz;
+  double grav, cfl, dt_fixed;
+  long long ncell;
+  void *buf[3];              // B0 = state, B1 = stage 1 result, B2 = stage 2 result
+  const double *rho_bar;     // [nz]
+  const double *p_face;      // [nz+1]
+  const double *p_cell;      // [nz]
+  unsigned long long *rate;  // CFL rate max as double bits (non-negative doubles order as
+                             // unsigned integers)
+  double *dt_step;           // time step of the current step
+};
+
+struct StageArgs {
+  const DomDev *doms;        // device array
+  const int *tile_domain;    // device array [ndom+1]: prefix of tiles per domain
+  int ndom;
+  int ntiles;
+  int stage;                 // 0, 1, 2
+  unsigned int *flags;       // bit 0 non-finite, bit 1 no convergence
+  int *max_sweeps;
+  Phys ph;
+};
+
+enum Flag : unsigned int { kFlagNonFinite = 1u, kFlagNoConv = 2u };
+
+// Kernel family entry points (one per instantiated configuration).
+struct KernelSet {
+  int tile[3];
+  int threads;
+  size_t smem_stage;
+  cudaError_t (*stage)(const StageArgs &, int grid, cudaStream_t);
+  cudaError_t (*rate)(const StageArgs &, int dom, int buf, cudaStream_t);
+  cudaError_t (*budget)(const StageArgs &, int dom, int buf, double *partials, int nblocks,
+                        double *out, cudaStream_t);
+  cudaError_t (*satadj)(const StageArgs &, int dom, int buf, cudaStream_t);
+  cudaError_t (*prepare)();  // one-time attribute setup (dynamic shared memory)
+};
+
+// Returns false when the configuration is not built into this library.
+bool find_kernels(int f32, int nvap, int ncond, int three_d, int visc, KernelSet *out);
+
+// Number of partial rows the budget kernel writes for a domain of ncell cells.
+int budget_blocks(long long ncell);
+
+cudaError_t launch_convert(const void *src, int src_f32, void *dst, int dst_f32, long long n,
+                           cudaStream_t s);
+
+}  // namespace snap

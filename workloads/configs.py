@@ -296,6 +296,32 @@ def isothermal_rest(nx=16, nz=32, T0=250.0, L=1000.0, p0=1e5, R_d=287.0, gamma_d
                     rho_bar=rho_bar, p_bar_face=pf, Y=Y, nsteps=nsteps, dtype=dtype)
 
 
+def dry_bubble_3d(nx=32, ny=24, nz=20, L=1000.0, A=0.5, R=250.0, nsteps=10, dtype="f64",
+                  theta0=300.0, p0=1e5, R_d=287.0, gamma_d=1.4, g=9.81):
+    """3-D dry warm bubble: isentropic theta0 background, spherical cosine bubble at the
+    centre of the lower half, periodic x and y, walls in z."""
+    dx = dy = dz = L / nx
+    kappa = (gamma_d - 1.0) / gamma_d
+
+    def rho_of(k, p):
+        return p / (R_d * theta0 * (p / p0) ** kappa)
+
+    rho_bar, pf = _hydrostatic_column(nz, dz, g, p0, False, rho_of)
+    pk = 0.5 * (pf[:-1] + pf[1:])
+    x = _cell_centres(nx, dx)[None, None, :]
+    y = _cell_centres(ny, dy)[None, :, None]
+    z = _cell_centres(nz, dz)[:, None, None]
+    r = np.sqrt((x - nx * dx / 2) ** 2 + (y - ny * dy / 2) ** 2 + (z - nz * dz / 3) ** 2) / R
+    theta = theta0 + np.where(r <= 1.0, A * np.cos(0.5 * np.pi * np.minimum(r, 1.0)) ** 2, 0.0)
+    T = theta * (pk[:, None, None] / p0) ** kappa
+    rho = pk[:, None, None] / (R_d * T)
+    Y = _assemble(nx, ny, nz, rho, [], T, R_d, gamma_d, [], 0)
+    return Workload(name=f"dry_bubble_{nx}x{ny}x{nz}", nx=nx, ny=ny, nz=nz, dx=dx, dy=dy, dz=dz,
+                    bc=(PERIODIC, PERIODIC, PERIODIC, PERIODIC, REFLECT, REFLECT), grav=g,
+                    gamma_d=gamma_d, R_d=R_d, vapors=[], ncond=0, rho_bar=rho_bar, p_bar_face=pf,
+                    Y=Y, nsteps=nsteps, dtype=dtype)
+
+
 def jovian(nx=256, ny=256, nz=128, Lx=100e3, Ly=100e3, Lz=150e3, nsteps=500, dtype="f32",
            seed=BASE_SEED + 3, noise_K=0.1, q_deep=(0.040, 0.0027)):
     """3-D moist Jovian-like column (Sec. 6): H2/He gas with mu = 2.3 g/mol, c_p = 3.5 R;
