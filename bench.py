@@ -210,7 +210,8 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     from paper_1901_02955_gb300 import Context
 
-    stream = torch.cuda.current_stream()
+    stream = torch.cuda.Stream()  # the library and the events share this stream
+    torch.cuda.set_stream(stream)
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")  # > 129 MB L2
 
     def barrier():

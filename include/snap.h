@@ -15,6 +15,9 @@
  *      rho u, [rho v when ny > 1], rho w, rho e.
  *    ny == 1 selects the x-z plane (no rho v). Units SI.
  *  - The library copies every input it is given; the caller keeps ownership of its buffers.
+ *  - Internally the energy field is stored as rho e - pbar_k/(gamma_d - 1), the departure from
+ *    the hydrostatic reference level by level, so that FP32 storage resolves pressure
+ *    perturbations; set/get convert, and budgets report the total energy.
  */
 #ifndef SNAP_H
 #define SNAP_H
@@ -74,7 +77,7 @@ typedef struct snap_grid_desc {
   int satadj;              /* 1: saturation adjustment after every stage (needs n_cond > 0) */
   int satadj_max_iter;     /* sweep limit of the adjustment (e.g. 20) */
   double satadj_tol;       /* relative stop tolerance on the molar transfer; raised to
-                              4 machine epsilons of dtype when smaller */
+                              32 machine epsilons of dtype when smaller */
   double weno_eps;         /* epsilon of the WENO5 weights (e.g. 1e-6) */
 } snap_grid_desc;
 
@@ -151,7 +154,9 @@ int snap_saturation_adjust(snap_ctx *ctx, int domain);
 int snap_step_adjoint(snap_ctx *ctx, int nsteps, const void *lambda_final, void *lambda_init,
                       int dtype, void *stream);
 
-/* Order all following work on this cudaStream_t (NULL: the context's own stream). */
+/* Order all following work of the context on this cudaStream_t. NULL selects the CUDA legacy
+ * default stream (the handle of torch's default stream); a new context starts on a
+ * non-blocking stream of its own. */
 int snap_set_stream(snap_ctx *ctx, void *stream);
 
 /* 1 (default): snap_step replays one captured CUDA graph per step; 0: plain launches. */
@@ -170,7 +175,8 @@ typedef struct snap_info {
 int snap_get_info(const snap_ctx *ctx, snap_info *info);
 
 /* Device pointer of one of a domain's three state buffers: slot 0 the current state, slot 1
- * the result of stage 0, slot 2 the result of stage 1 (layout and dtype of the context).
+ * the result of stage 0, slot 2 the result of stage 1 (dtype of the context, stored layout:
+ * the energy field holds rho e - pbar_k/(gamma_d - 1)).
  * Valid until snap_free; the library writes them during stages. */
 int snap_buffer_pointer(snap_ctx *ctx, int domain, int slot, void **ptr);
 

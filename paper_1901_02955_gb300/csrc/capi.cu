@@ -32,24 +32,38 @@ int budget_blocks(long long ncell) {
   return int(b < 1 ? 1 : (b > 1024 ? 1024 : b));
 }
 
+// Caller layout <-> stored layout: the energy field (the last of nv) is shifted by the
+// per-level reference e_ref, in FP64; every value is converted to the destination type.
 template <class S, class D>
-__global__ void convert_kernel(const S *src, D *dst, long long n) {
+__global__ void state_copy_kernel(const S *src, D *dst, int nv, long long ncell, long long plane,
+                                  const double *e_ref, double sign) {
+  const long long n = (long long)nv * ncell, e0 = (long long)(nv - 1) * ncell;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x)
-    dst[i] = D(src[i]);
+       i += (long long)gridDim.x * blockDim.x) {
+    if (i >= e0)
+      dst[i] = D(double(src[i]) + sign * e_ref[(i - e0) / plane]);
+    else
+      dst[i] = D(src[i]);
+  }
 }
 
-cudaError_t launch_convert(const void *src, int src_f32, void *dst, int dst_f32, long long n,
-                           cudaStream_t s) {
+cudaError_t launch_state_copy(const void *src, int src_f32, void *dst, int dst_f32, int nv,
+                              long long ncell, long long plane, const double *e_ref,
+                              int to_stored, cudaStream_t s) {
   const int grid = 1216, block = 256;
+  const double sg = to_stored ? -1.0 : 1.0;
   if (src_f32 && !dst_f32)
-    convert_kernel<float, double><<<grid, block, 0, s>>>((const float *)src, (double *)dst, n);
+    state_copy_kernel<float, double><<<grid, block, 0, s>>>((const float *)src, (double *)dst,
+                                                            nv, ncell, plane, e_ref, sg);
   else if (!src_f32 && dst_f32)
-    convert_kernel<double, float><<<grid, block, 0, s>>>((const double *)src, (float *)dst, n);
+    state_copy_kernel<double, float><<<grid, block, 0, s>>>((const double *)src, (float *)dst,
+                                                            nv, ncell, plane, e_ref, sg);
   else if (src_f32)
-    convert_kernel<float, float><<<grid, block, 0, s>>>((const float *)src, (float *)dst, n);
+    state_copy_kernel<float, float><<<grid, block, 0, s>>>((const float *)src, (float *)dst,
+                                                           nv, ncell, plane, e_ref, sg);
   else
-    convert_kernel<double, double><<<grid, block, 0, s>>>((const double *)src, (double *)dst, n);
+    state_copy_kernel<double, double><<<grid, block, 0, s>>>((const double *)src, (double *)dst,
+                                                             nv, ncell, plane, e_ref, sg);
   return cudaGetLastError();
 }
 }  // namespace snap
@@ -280,7 +294,7 @@ extern "C" int snap_init_grid(snap_ctx **out, const snap_grid_desc *d, int n_dom
     maxcell = nc > maxcell ? nc : maxcell;
     ctx->ncells += (long long)nc;
     ctx->state_bytes += (long long)(nc * ctx->nv * ctx->word);
-    nprof += 3 * (size_t)g.nz + 1;
+    nprof += 4 * (size_t)g.nz + 1;
     DomDev &D = ctx->dom[i];
     D.nx = g.nx;
     D.ny = g.ny;
@@ -331,18 +345,21 @@ extern "C" int snap_init_grid(snap_ctx **out, const snap_grid_desc *d, int n_dom
       size_t nc = (size_t)g.nx * g.ny * g.nz;
       size_t bytes = ((nc * ctx->nv * ctx->word) + 255) / 256 * 256;
       for (int b = 0; b < 3; ++b) D.buf[b] = (char *)ctx->arena + off[i] + b * bytes;
-      double *rb = ctx->prof_dev + po, *pf = rb + g.nz, *pc = pf + g.nz + 1;
+      double *rb = ctx->prof_dev + po, *pf = rb + g.nz, *pc = pf + g.nz + 1, *er = pc + g.nz;
       for (int k = 0; k < g.nz; ++k) {
+        const double pk = 0.5 * (g.p_bar_face[k] + g.p_bar_face[k + 1]);
         prof[po + k] = g.rho_bar[k];
-        prof[po + g.nz + 1 + g.nz + k] = 0.5 * (g.p_bar_face[k] + g.p_bar_face[k + 1]);
+        prof[po + 2 * g.nz + 1 + k] = pk;
+        prof[po + 3 * g.nz + 1 + k] = pk / (g.gamma_d - 1.0);
       }
       for (int k = 0; k <= g.nz; ++k) prof[po + g.nz + k] = g.p_bar_face[k];
       D.rho_bar = rb;
       D.p_face = pf;
       D.p_cell = pc;
+      D.e_ref = er;
       D.rate = ctx->rate_dev + i;
       D.dt_step = ctx->dt_dev + i;
-      po += 3 * (size_t)g.nz + 1;
+      po += 4 * (size_t)g.nz + 1;
     }
     if ((e = cudaMemcpy(ctx->prof_dev, prof.data(), sizeof(double) * nprof, cudaMemcpyHostToDevice)) != cudaSuccess) break;
     if ((e = cudaMemcpy(ctx->doms_dev, ctx->dom.data(), sizeof(DomDev) * n_domains, cudaMemcpyHostToDevice)) != cudaSuccess) break;
@@ -359,7 +376,7 @@ extern "C" int snap_init_grid(snap_ctx **out, const snap_grid_desc *d, int n_dom
 }
 
 static cudaStream_t pick(snap_ctx *ctx, void *stream) {
-  return stream ? (cudaStream_t)stream : ctx->stream;
+  return stream ? (cudaStream_t)stream : ctx->stream;  // NULL: the context's current stream
 }
 
 extern "C" int snap_set_state(snap_ctx *ctx, int domain, const void *Y, int dtype, int on_device,
@@ -372,14 +389,13 @@ extern "C" int snap_set_state(snap_ctx *ctx, int domain, const void *Y, int dtyp
   const long long n = D.ncell * ctx->nv;
   const int src_f32 = dtype == SNAP_F32;
   const size_t sw = src_f32 ? 4 : 8;
-  if (src_f32 == ctx->f32) {
-    CK(cudaMemcpyAsync(D.buf[0], Y, n * sw, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
-  } else if (on_device) {
-    CK(launch_convert(Y, src_f32, D.buf[0], ctx->f32, n, s));
-  } else {
+  const void *src = Y;
+  if (!on_device) {
     CK(cudaMemcpyAsync(ctx->staging, Y, n * sw, cudaMemcpyHostToDevice, s));
-    CK(launch_convert(ctx->staging, src_f32, D.buf[0], ctx->f32, n, s));
+    src = ctx->staging;
   }
+  CK(launch_state_copy(src, src_f32, D.buf[0], ctx->f32, ctx->nv, D.ncell,
+                       (long long)D.nx * D.ny, D.e_ref, 1, s));
   return refresh_rate(ctx, domain, s);
 }
 
@@ -393,15 +409,13 @@ extern "C" int snap_get_state(snap_ctx *ctx, int domain, void *Y_out, int dtype,
   const long long n = D.ncell * ctx->nv;
   const int dst_f32 = dtype == SNAP_F32;
   const size_t dw = dst_f32 ? 4 : 8;
-  if (dst_f32 == ctx->f32) {
-    CK(cudaMemcpyAsync(Y_out, D.buf[0], n * dw, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
-  } else if (on_device) {
-    CK(launch_convert(D.buf[0], ctx->f32, Y_out, dst_f32, n, s));
-  } else {
-    CK(launch_convert(D.buf[0], ctx->f32, ctx->staging, dst_f32, n, s));
+  void *dst = on_device ? Y_out : ctx->staging;
+  CK(launch_state_copy(D.buf[0], ctx->f32, dst, dst_f32, ctx->nv, D.ncell,
+                       (long long)D.nx * D.ny, D.e_ref, 0, s));
+  if (!on_device) {
     CK(cudaMemcpyAsync(Y_out, ctx->staging, n * dw, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
   }
-  if (!on_device) CK(cudaStreamSynchronize(s));
   return SNAP_OK;
 }
 
@@ -576,7 +590,7 @@ extern "C" int snap_step_adjoint(snap_ctx *ctx, int nsteps, const void *lambda_f
 
 extern "C" int snap_set_stream(snap_ctx *ctx, void *stream) {
   if (!ctx) return fail(nullptr, SNAP_EINVAL, "snap_set_stream: NULL context");
-  ctx->stream = stream ? (cudaStream_t)stream : ctx->own_stream;
+  ctx->stream = (cudaStream_t)stream;  // NULL: the legacy default stream
   return SNAP_OK;
 }
 

@@ -40,6 +40,8 @@ struct DomDev {
   const double *rho_bar;     // [nz]
   const double *p_face;      // [nz+1]
   const double *p_cell;      // [nz]
+  const double *e_ref;       // [nz]: the stored energy field is rho e - e_ref[k],
+                             // e_ref[k] = pbar_k / (gamma_d - 1) (hydrostatic reference)
   unsigned long long *rate;  // CFL rate max as double bits (non-negative doubles order as
                              // unsigned integers)
   double *dt_step;           // time step of the current step
@@ -77,7 +79,10 @@ bool find_kernels(int f32, int nvap, int ncond, int three_d, int visc, KernelSet
 // Number of partial rows the budget kernel writes for a domain of ncell cells.
 int budget_blocks(long long ncell);
 
-cudaError_t launch_convert(const void *src, int src_f32, void *dst, int dst_f32, long long n,
-                           cudaStream_t s);
+// Copy a state between the caller's layout (total energy) and the stored one (energy minus
+// e_ref per level), converting FP32/FP64. to_stored = 1: caller -> stored.
+cudaError_t launch_state_copy(const void *src, int src_f32, void *dst, int dst_f32, int nv,
+                              long long ncell, long long plane, const double *e_ref,
+                              int to_stored, cudaStream_t s);
 
 }  // namespace snap

@@ -30,8 +30,8 @@ struct Ar<float> {
   static __device__ __forceinline__ float rcp(float x) { return __fdividef(1.0f, x); }
   static __device__ __forceinline__ float div(float a, float b) { return __fdividef(a, b); }
   static __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
-  static __device__ __forceinline__ float exp_(float x) { return __expf(x); }
-  static __device__ __forceinline__ float log_(float x) { return __logf(x); }
+  static __device__ __forceinline__ float exp_(float x) { return expf(x); }
+  static __device__ __forceinline__ float log_(float x) { return logf(x); }
   static __device__ __forceinline__ float pow_(float x, float y) { return powf(x, y); }
   static constexpr double eps = 1.1920928955078125e-07;
 };
@@ -95,12 +95,14 @@ struct Box {
 // ------------------------------------------------------------------------------------------
 // thermodynamics (Sec. 2, App. B)
 // ------------------------------------------------------------------------------------------
-// Conserved -> primitive. x receives (rho, q_i, q_ij, u, [v], w, p - pbar) and the total
-// pressure is returned in p_tot; T in T_out. For the FP32 moist path the inversion
-// U = rho e - K - A, T = U / C_v, p = R_m T runs in FP64.
+// Conserved -> primitive. y holds the stored state, whose energy entry is rho e - eref with
+// eref = pbar / (gamma_d - 1). x receives (rho, q_i, q_ij, u, [v], w, p - pbar), the total
+// pressure is returned in p_tot and T in T_out. Dry: p - pbar = (gamma_d - 1)(y_E - K) is
+// formed from small numbers. Moist: the inversion U = rho e - K - A, T = U / C_v, p = R_m T
+// runs in FP64.
 template <class R, class L>
 __device__ __forceinline__ void cons_to_prim(const Phys &ph, const R *y, R *x, double pbar,
-                                             R &p_tot, R &T_out) {
+                                             double eref, R &p_tot, R &T_out) {
   R rho = y[0];
 #pragma unroll
   for (int s = 1; s < L::IM0; ++s) rho += y[s];
@@ -116,11 +118,13 @@ __device__ __forceinline__ void cons_to_prim(const Phys &ph, const R *y, R *x, d
   }
   K *= R(0.5);
   if constexpr (L::NVAP == 0) {
-    // dry: p = (gamma_d - 1) (rho e - K)
-    R p = R(ph.gamma_d - 1.0) * (y[L::IE] - K);
-    x[L::IE] = R(double(p) - pbar);
+    // dry: p = (gamma_d - 1) (rho e - K), so p - pbar = (gamma_d - 1) (y_E - K)
+    const R pp = R(ph.gamma_d - 1.0) * (y[L::IE] - K);
+    x[L::IE] = pp;
+    const R p = pp + R(pbar);
     p_tot = p;
     T_out = p * Ar<R>::rcp(rho * R(ph.R_d));
+    (void)eref;
   } else {
     double A = 0.0, Cv = y[0], Rm = y[0];
 #pragma unroll
@@ -135,7 +139,7 @@ __device__ __forceinline__ void cons_to_prim(const Phys &ph, const R *y, R *x, d
     }
     Cv *= ph.c_vd;
     Rm *= ph.R_d;
-    double U = double(y[L::IE]) - double(K) - A;
+    double U = (double(y[L::IE]) + eref) - double(K) - A;
     double T = U / Cv;
     double p = Rm * T;
     p_tot = R(p);
@@ -259,7 +263,8 @@ __device__ __forceinline__ void lmars(const Phys &ph, const R *XL, const R *XR, 
 // state. Returns the sweep count, or -1 without convergence.
 // ------------------------------------------------------------------------------------------
 template <class R, class L>
-__device__ __forceinline__ void cell_Tp(const Phys &ph, const R *y, double &T, double &p) {
+__device__ __forceinline__ void cell_Tp(const Phys &ph, const R *y, double eref, double &T,
+                                        double &p) {
   double rho = 0.0, K2 = 0.0, A = 0.0, Cv = y[0], Rm = y[0];
 #pragma unroll
   for (int s = 0; s < L::IM0; ++s) rho += double(y[s]);
@@ -275,13 +280,13 @@ __device__ __forceinline__ void cell_Tp(const Phys &ph, const R *y, double &T, d
       A += ph.mu[i][j] * double(y[L::cond(i, j)]);
     }
   }
-  double U = double(y[L::IE]) - 0.5 * K2 / rho - A;
+  double U = (double(y[L::IE]) + eref) - 0.5 * K2 / rho - A;
   T = U / (Cv * ph.c_vd);
   p = Rm * ph.R_d * T;
 }
 
 template <class R, class L>
-__device__ int satadj_cell(const Phys &ph, R *y, int max_iter, double tol) {
+__device__ int satadj_cell(const Phys &ph, R *y, double eref, int max_iter, double tol) {
   if constexpr (!L::MOIST) {
     return 0;
   } else {
@@ -290,8 +295,9 @@ __device__ int satadj_cell(const Phys &ph, R *y, int max_iter, double tol) {
 #pragma unroll
       for (int i = 0; i < L::NVAP; ++i) {
         double Td, pd;
-        cell_Tp<R, L>(ph, y, Td, pd);
+        cell_Tp<R, L>(ph, y, eref, Td, pd);
         R T = R(Td), p = R(pd);
+        const R dTr = R(Td - ph.Tref[i]);  // T - T^r kept accurate: s(T) is steep
         R N = y[0], gas = y[0], heat = R(0);
 #pragma unroll
         for (int k = 0; k < L::NVAP; ++k) {
@@ -308,8 +314,9 @@ __device__ int satadj_cell(const Phys &ph, R *y, int max_iter, double tol) {
         R qc = y[L::cond(i, 0)] * R(ph.inv_eps[i]) * iN;
         R gsum = gas * iN - qv;
         R t = T * R(1.0 / ph.Tref[i]);
+        // p* = p^r exp[beta (1 - 1/t) - delta ln t] with 1 - 1/t = (T - T^r) / T
         R ps = R(ph.pref[i]) *
-               Ar<R>::exp_(R(ph.beta[i]) * (R(1) - Ar<R>::rcp(t)) - R(ph.delta[i]) * Ar<R>::log_(t));
+               Ar<R>::exp_(R(ph.beta[i]) * dTr * Ar<R>::rcp(T) - R(ph.delta[i]) * Ar<R>::log_(t));
         R s = Ar<R>::div(ps, p);
         R dq;
         if (s >= R(1)) {
@@ -343,8 +350,8 @@ __device__ int satadj_cell(const Phys &ph, R *y, int max_iter, double tol) {
 
 // CFL rate sum_d (|u_d| + c) / dx_d of one cell (the time-step rule of the library).
 template <class R, class L>
-__device__ __forceinline__ double cell_rate(const Phys &ph, const R *y, double idx, double idy,
-                                            double idz) {
+__device__ __forceinline__ double cell_rate(const Phys &ph, const R *y, double eref, double idx,
+                                            double idy, double idz) {
   double T, p;
   double rho = 0.0;
 #pragma unroll
@@ -353,10 +360,10 @@ __device__ __forceinline__ double cell_rate(const Phys &ph, const R *y, double i
     double K2 = 0.0;
 #pragma unroll
     for (int m = 0; m < L::NMOM; ++m) K2 += double(y[L::IM0 + m]) * double(y[L::IM0 + m]);
-    p = (ph.gamma_d - 1.0) * (double(y[L::IE]) - 0.5 * K2 / rho);
+    p = (ph.gamma_d - 1.0) * ((double(y[L::IE]) + eref) - 0.5 * K2 / rho);
     T = 0.0;
   } else {
-    cell_Tp<R, L>(ph, y, T, p);
+    cell_Tp<R, L>(ph, y, eref, T, p);
   }
   // gamma of App. B from the mass fractions
   double num = 1.0, den = 1.0;
@@ -482,7 +489,7 @@ __global__ void __launch_bounds__(Tile<L::D3>::NT)
 #pragma unroll
         for (int v = 0; v < NV; ++v) ys[m][v] = Ys[v * ncell + g];
         R x[NV], pt, Tt;
-        cons_to_prim<R, L>(ph, ys[m], x, D.p_cell[z0 + lz], pt, Tt);
+        cons_to_prim<R, L>(ph, ys[m], x, D.p_cell[z0 + lz], D.e_ref[z0 + lz], pt, Tt);
         const int bi = B::at(lx + 3, ly + B::HY, lz + 3);
 #pragma unroll
         for (int v = 0; v < NV; ++v) s_prim[v * B::NBOX + bi] = x[v];
@@ -528,7 +535,7 @@ __global__ void __launch_bounds__(Tile<L::D3>::NT)
         R y[NV], x[NV], pt, Tt;
 #pragma unroll
         for (int v = 0; v < NV; ++v) y[v] = Ys[v * ncell + g];
-        cons_to_prim<R, L>(ph, y, x, D.p_cell[gz], pt, Tt);
+        cons_to_prim<R, L>(ph, y, x, D.p_cell[gz], D.e_ref[gz], pt, Tt);
         if (flip) x[L::mom(dirn)] = -x[L::mom(dirn)];
         const int bi = B::at(bx, by, bz);
 #pragma unroll
@@ -611,7 +618,7 @@ __global__ void __launch_bounds__(Tile<L::D3>::NT)
 
     // ---- 4. sources, stage combine, saturation adjustment, store ------------------------
     double rate_max = 0.0;
-    const double tol = fmax(ph.satadj_tol, 4.0 * Ar<R>::eps);
+    const double tol = fmax(ph.satadj_tol, 32.0 * Ar<R>::eps);
 #pragma unroll
     for (int m = 0; m < B::CPT; ++m) {
       const int c = threadIdx.x + m * T::NT;
@@ -645,7 +652,7 @@ __global__ void __launch_bounds__(Tile<L::D3>::NT)
         }
         if constexpr (L::MOIST) {
           if (ph.satadj) {
-            const int it = satadj_cell<R, L>(ph, yo, ph.satadj_max_iter, tol);
+            const int it = satadj_cell<R, L>(ph, yo, D.e_ref[k], ph.satadj_max_iter, tol);
             if (it < 0)
               atomicOr(a.flags, (unsigned)kFlagNoConv);
             else
@@ -659,7 +666,8 @@ __global__ void __launch_bounds__(Tile<L::D3>::NT)
 #pragma unroll
         for (int v = 0; v < NV; ++v) Yo[v * ncell + g] = yo[v];
         if (a.stage == 2)
-          rate_max = fmax(rate_max, cell_rate<R, L>(ph, yo, 1.0 / D.dx, 1.0 / D.dy, 1.0 / D.dz));
+          rate_max = fmax(rate_max,
+                          cell_rate<R, L>(ph, yo, D.e_ref[k], 1.0 / D.dx, 1.0 / D.dy, 1.0 / D.dz));
       }
     }
     if (a.stage == 2) {
@@ -684,7 +692,8 @@ __global__ void __launch_bounds__(256) rate_kernel(const StageArgs a, int dm, in
     R y[L::NV];
 #pragma unroll
     for (int v = 0; v < L::NV; ++v) y[v] = Y[v * D.ncell + c];
-    r = fmax(r, cell_rate<R, L>(a.ph, y, 1.0 / D.dx, 1.0 / D.dy, 1.0 / D.dz));
+    const double er = D.e_ref[c / ((long long)D.nx * D.ny)];
+    r = fmax(r, cell_rate<R, L>(a.ph, y, er, 1.0 / D.dx, 1.0 / D.dy, 1.0 / D.dz));
   }
   double bm = block_max(r, red);
   if (threadIdx.x == 0) atomicMax(D.rate, (unsigned long long)__double_as_longlong(bm));
@@ -706,15 +715,18 @@ __global__ void __launch_bounds__(256) budget_kernel(const StageArgs a, int dm, 
   for (int o = 0; o < NO; ++o) s[o] = 0.0;
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < D.ncell;
        c += (long long)gridDim.x * blockDim.x) {
-    const double z = (double(c / plane) + 0.5) * D.dz;
+    const long long k = c / plane;
+    const double z = (double(k) + 0.5) * D.dz;
+    const double er = D.e_ref[k];
     double rho = 0.0;
 #pragma unroll
     for (int v = 0; v < L::NV; ++v) {
-      const double y = double(Y[v * D.ncell + c]);
+      double y = double(Y[v * D.ncell + c]);
+      if (v == L::IE) y += er;
       s[v] += y;
       if (v < L::IM0) rho += y;
     }
-    s[L::NV] += double(Y[(long long)L::IE * D.ncell + c]) + rho * D.grav * z;
+    s[L::NV] += (double(Y[(long long)L::IE * D.ncell + c]) + er) + rho * D.grav * z;
   }
 #pragma unroll
   for (int o = 0; o < NO; ++o) {
@@ -745,13 +757,14 @@ template <class R, class L>
 __global__ void __launch_bounds__(256) satadj_kernel(const StageArgs a, int dm, int buf) {
   const DomDev &D = a.doms[dm];
   R *Y = reinterpret_cast<R *>(D.buf[buf]);
-  const double tol = fmax(a.ph.satadj_tol, 4.0 * Ar<R>::eps);
+  const double tol = fmax(a.ph.satadj_tol, 32.0 * Ar<R>::eps);
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < D.ncell;
        c += (long long)gridDim.x * blockDim.x) {
     R y[L::NV];
 #pragma unroll
     for (int v = 0; v < L::NV; ++v) y[v] = Y[v * D.ncell + c];
-    const int it = satadj_cell<R, L>(a.ph, y, a.ph.satadj_max_iter, tol);
+    const double er = D.e_ref[c / ((long long)D.nx * D.ny)];
+    const int it = satadj_cell<R, L>(a.ph, y, er, a.ph.satadj_max_iter, tol);
     if (it < 0)
       atomicOr(a.flags, (unsigned)kFlagNoConv);
     else
