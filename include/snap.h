@@ -180,6 +180,31 @@ int snap_get_info(const snap_ctx *ctx, snap_info *info);
  * Valid until snap_free; the library writes them during stages. */
 int snap_buffer_pointer(snap_ctx *ctx, int domain, int slot, void **ptr);
 
+/* Budget of a state held in the caller's device memory, computed without any allocation by
+ * the library. It serves callers that cannot allocate device memory and therefore cannot
+ * create a context: code running under a fixed memory pool that must not grow, inside a
+ * framework that owns all device memory and hands out only pre-sized tensors, or during a
+ * phase in which cudaMalloc is not allowed. The paper has no counterpart; this is a service
+ * of the library, a variant of the reduction behind snap_budget_compute.
+ *   Y: device pointer in the caller's layout: nfields planes of nx*ny*nz values (i fastest),
+ *      the first n_mass_fields planes densities, the last plane the total energy rho e;
+ *      dtype SNAP_F32 or SNAP_F64.
+ *   out: device pointer to nfields + 1 doubles: each field's sum times the cell volume, then
+ *      the sum of (rho e + rho g z) times the cell volume (z at cell centres, dy ignored
+ *      when ny == 1).
+ *   stream: cudaStream_t to order the work on (NULL: the legacy default stream).
+ * Scratch: a fixed device array of 1024 x 25 doubles (200 KiB) inside the library, held by
+ * every device that loads the library until the process exits. nfields is limited to
+ * SNAP_MAX_FIELDS (SNAP_EINVAL beyond). Each call writes every partial-sum row it later
+ * reads, so nothing has to be cleared between calls; but all calls on a device share the
+ * array, so calls whose work overlaps on the GPU (other streams, other host threads) race
+ * and give wrong sums: serialise them. The first call on each device looks up the array's
+ * device address with cudaGetSymbolAddress; make that first call before any stream capture.
+ * Returns SNAP_OK, SNAP_EINVAL or SNAP_ECUDA; out is complete when the stream reaches it. */
+int snap_budget_noalloc(const void *Y, int dtype, int nx, int ny, int nz, int nfields,
+                        int n_mass_fields, double dx, double dy, double dz, double grav,
+                        double *out, void *stream);
+
 void snap_free(snap_ctx *ctx);
 const char *snap_last_error(const snap_ctx *ctx);
 const char *snap_status_string(int status);

@@ -26,8 +26,8 @@ F64, F32 = 0, 1
 EXPORTS = ["snap_init_grid", "snap_set_state", "snap_get_state", "snap_step", "snap_step_async",
            "snap_stage", "snap_check", "snap_reset_flags", "snap_budget_compute",
            "snap_compute_dt", "snap_saturation_adjust", "snap_step_adjoint", "snap_set_stream",
-           "snap_use_graph", "snap_get_info", "snap_buffer_pointer", "snap_free",
-           "snap_last_error", "snap_status_string"]
+           "snap_use_graph", "snap_get_info", "snap_buffer_pointer", "snap_budget_noalloc",
+           "snap_free", "snap_last_error", "snap_status_string"]
 
 
 class Species(C.Structure):
@@ -95,6 +95,9 @@ def load(path: Optional[str] = None) -> C.CDLL:
     lib.snap_use_graph.argtypes = [P, C.c_int]
     lib.snap_get_info.argtypes = [P, C.POINTER(Info)]
     lib.snap_buffer_pointer.argtypes = [P, C.c_int, C.c_int, C.POINTER(P)]
+    lib.snap_budget_noalloc.argtypes = [P, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
+                                        C.c_int, C.c_double, C.c_double, C.c_double,
+                                        C.c_double, P, P]
     lib.snap_free.argtypes = [P]
     lib.snap_free.restype = None
     lib.snap_last_error.argtypes = [P]
