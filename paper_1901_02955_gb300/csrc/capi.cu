@@ -85,6 +85,7 @@ struct snap_ctx {
   DomDev *doms_dev = nullptr;
   int *prefix_dev = nullptr;
   double *prof_dev = nullptr;
+  float *proff_dev = nullptr;
   unsigned long long *rate_dev = nullptr;
   double *dt_dev = nullptr;
   unsigned int *flags_dev = nullptr;
@@ -131,6 +132,7 @@ static void release(snap_ctx *ctx) {
   cudaFree(ctx->doms_dev);
   cudaFree(ctx->prefix_dev);
   cudaFree(ctx->prof_dev);
+  cudaFree(ctx->proff_dev);
   cudaFree(ctx->rate_dev);
   cudaFree(ctx->dt_dev);
   cudaFree(ctx->flags_dev);
@@ -225,6 +227,38 @@ static void derive_phys(const snap_grid_desc &d, Phys &ph) {
   ph.satadj_tol = d.satadj_tol;
 }
 
+template <class T>
+static void derive_cst(const Phys &ph, double tol_floor, CstT<T> &c) {
+  memset(&c, 0, sizeof c);
+  c.gamma_d = T(ph.gamma_d);
+  c.gm1 = T(ph.gamma_d - 1.0);
+  c.igm1 = T(1.0 / (ph.gamma_d - 1.0));
+  c.R_d = T(ph.R_d);
+  c.iR_d = T(1.0 / ph.R_d);
+  c.kappa = T(ph.kappa);
+  c.c_pd = T(ph.c_pd);
+  c.nu = T(ph.nu);
+  c.weno_eps = T(ph.weno_eps);
+  c.satadj_tol = T(ph.satadj_tol > tol_floor ? ph.satadj_tol : tol_floor);
+  for (int i = 0; i < kMaxVap; ++i) {
+    c.eps[i] = T(ph.eps[i]);
+    c.inv_eps[i] = T(ph.inv_eps[i]);
+    c.ieps_m1[i] = T(ph.inv_eps[i] - 1.0);
+    c.sig_v[i] = T(ph.sig_v[i]);
+    c.sigv_m1[i] = T(ph.sig_v[i] - 1.0);
+    c.pref[i] = T(ph.pref[i]);
+    c.beta[i] = T(ph.beta[i]);
+    c.delta[i] = T(ph.delta[i]);
+    c.inv_Tref[i] = T(ph.Tref[i] > 0 ? 1.0 / ph.Tref[i] : 0.0);
+    c.sighat_m1[i] = T(ph.sig_hat[i] - 1.0);
+    for (int j = 0; j < kMaxCond; ++j) {
+      c.sig_c[i][j] = T(ph.sig_c[i][j]);
+      c.sigc_m1[i][j] = T(ph.sig_c[i][j] - 1.0);
+      c.mu[i][j] = T(ph.mu[i][j]);
+    }
+  }
+}
+
 static StageArgs args_of(snap_ctx *ctx, int stage) {
   StageArgs a;
   a.doms = ctx->doms_dev;
@@ -235,6 +269,9 @@ static StageArgs args_of(snap_ctx *ctx, int stage) {
   a.flags = ctx->flags_dev;
   a.max_sweeps = ctx->sweeps_dev;
   a.ph = ctx->ph;
+  // stop tolerance of the adjustment: at least 32 machine epsilons of the arithmetic type
+  derive_cst<float>(ctx->ph, 32.0 * 1.1920928955078125e-07, a.cf);
+  derive_cst<double>(ctx->ph, 32.0 * 2.220446049250313e-16, a.cd);
   return a;
 }
 
@@ -282,7 +319,7 @@ extern "C" int snap_init_grid(snap_ctx **out, const snap_grid_desc *d, int n_dom
   // layout of the state arena and tile table
   std::vector<size_t> off(n_domains);
   size_t total = 0, maxcell = 0;
-  size_t nprof = 0;
+  size_t nprof = 0, nproff = 0;
   ctx->prefix.assign(n_domains + 1, 0);
   ctx->dom.resize(n_domains);
   for (int i = 0; i < n_domains; ++i) {
@@ -295,6 +332,7 @@ extern "C" int snap_init_grid(snap_ctx **out, const snap_grid_desc *d, int n_dom
     ctx->ncells += (long long)nc;
     ctx->state_bytes += (long long)(nc * ctx->nv * ctx->word);
     nprof += 4 * (size_t)g.nz + 1;
+    nproff += 5 * (size_t)g.nz + 1;
     DomDev &D = ctx->dom[i];
     D.nx = g.nx;
     D.ny = g.ny;
@@ -325,6 +363,7 @@ extern "C" int snap_init_grid(snap_ctx **out, const snap_grid_desc *d, int n_dom
     if ((e = cudaMalloc(&ctx->doms_dev, sizeof(DomDev) * n_domains)) != cudaSuccess) break;
     if ((e = cudaMalloc(&ctx->prefix_dev, sizeof(int) * (n_domains + 1))) != cudaSuccess) break;
     if ((e = cudaMalloc(&ctx->prof_dev, sizeof(double) * nprof)) != cudaSuccess) break;
+    if ((e = cudaMalloc(&ctx->proff_dev, sizeof(float) * nproff)) != cudaSuccess) break;
     if ((e = cudaMalloc(&ctx->rate_dev, sizeof(unsigned long long) * n_domains)) != cudaSuccess) break;
     if ((e = cudaMalloc(&ctx->dt_dev, sizeof(double) * n_domains)) != cudaSuccess) break;
     if ((e = cudaMalloc(&ctx->flags_dev, sizeof(unsigned int))) != cudaSuccess) break;
@@ -338,7 +377,8 @@ extern "C" int snap_init_grid(snap_ctx **out, const snap_grid_desc *d, int n_dom
     if ((e = cudaMemset(ctx->flags_dev, 0, sizeof(unsigned int))) != cudaSuccess) break;
     if ((e = cudaMemset(ctx->sweeps_dev, 0, sizeof(int))) != cudaSuccess) break;
     std::vector<double> prof(nprof);
-    size_t po = 0;
+    std::vector<float> proff(nproff);
+    size_t po = 0, pof = 0;
     for (int i = 0; i < n_domains; ++i) {
       const snap_grid_desc &g = d[i];
       DomDev &D = ctx->dom[i];
@@ -357,11 +397,35 @@ extern "C" int snap_init_grid(snap_ctx **out, const snap_grid_desc *d, int n_dom
       D.p_face = pf;
       D.p_cell = pc;
       D.e_ref = er;
+      // FP32 copies: rho_bar as hi + lo, reference pressures and energies rounded
+      float *fb = ctx->proff_dev + pof;
+      for (int k = 0; k < g.nz; ++k) {
+        const float hi = (float)g.rho_bar[k];
+        proff[pof + k] = hi;
+        proff[pof + g.nz + k] = (float)(g.rho_bar[k] - (double)hi);
+        proff[pof + 2 * g.nz + k] = (float)prof[po + 2 * g.nz + 1 + k];
+        proff[pof + 4 * g.nz + 1 + k] = (float)prof[po + 3 * g.nz + 1 + k];
+      }
+      for (int k = 0; k <= g.nz; ++k) proff[pof + 3 * g.nz + k] = (float)g.p_bar_face[k];
+      D.rb_hi = fb;
+      D.rb_lo = fb + g.nz;
+      D.pc_f = fb + 2 * g.nz;
+      D.pf_f = fb + 3 * g.nz;
+      D.er_f = fb + 4 * g.nz + 1;
+      D.idx = 1.0 / D.dx;
+      D.idy = 1.0 / D.dy;
+      D.idz = 1.0 / D.dz;
+      D.fidx = (float)D.idx;
+      D.fidy = (float)D.idy;
+      D.fidz = (float)D.idz;
+      D.fgrav = (float)g.grav;
       D.rate = ctx->rate_dev + i;
       D.dt_step = ctx->dt_dev + i;
       po += 4 * (size_t)g.nz + 1;
+      pof += 5 * (size_t)g.nz + 1;
     }
     if ((e = cudaMemcpy(ctx->prof_dev, prof.data(), sizeof(double) * nprof, cudaMemcpyHostToDevice)) != cudaSuccess) break;
+    if ((e = cudaMemcpy(ctx->proff_dev, proff.data(), sizeof(float) * nproff, cudaMemcpyHostToDevice)) != cudaSuccess) break;
     if ((e = cudaMemcpy(ctx->doms_dev, ctx->dom.data(), sizeof(DomDev) * n_domains, cudaMemcpyHostToDevice)) != cudaSuccess) break;
     if ((e = cudaMemcpy(ctx->prefix_dev, ctx->prefix.data(), sizeof(int) * (n_domains + 1), cudaMemcpyHostToDevice)) != cudaSuccess) break;
   } while (0);

@@ -27,6 +27,16 @@ struct Phys {
   double satadj_tol;
 };
 
+// The same constants in the arithmetic type of a kernel, derived on the host, so that FP32
+// kernels execute no double-precision conversion or arithmetic on their hot path.
+template <class T>
+struct CstT {
+  T gamma_d, gm1, igm1, R_d, iR_d, kappa, c_pd, nu, weno_eps, satadj_tol;
+  T eps[kMaxVap], inv_eps[kMaxVap], ieps_m1[kMaxVap], sig_v[kMaxVap], sigv_m1[kMaxVap];
+  T sig_c[kMaxVap][kMaxCond], sigc_m1[kMaxVap][kMaxCond], mu[kMaxVap][kMaxCond];
+  T pref[kMaxVap], beta[kMaxVap], delta[kMaxVap], inv_Tref[kMaxVap], sighat_m1[kMaxVap];
+};
+
 // One domain as the kernels see it (device memory).
 struct DomDev {
   int nx, ny, nz;
@@ -42,6 +52,14 @@ struct DomDev {
   const double *p_cell;      // [nz]
   const double *e_ref;       // [nz]: the stored energy field is rho e - e_ref[k],
                              // e_ref[k] = pbar_k / (gamma_d - 1) (hydrostatic reference)
+  // FP32 copies for the FP32 kernels (no FP64 instruction on their hot path)
+  const float *rb_hi;        // [nz] rho_bar rounded to FP32
+  const float *rb_lo;        // [nz] rho_bar - rb_hi, so (rho - rb_hi) - rb_lo is accurate
+  const float *pc_f;         // [nz]
+  const float *pf_f;         // [nz+1]
+  const float *er_f;         // [nz]
+  double idx, idy, idz;      // inverse cell sizes
+  float fidx, fidy, fidz, fgrav;
   unsigned long long *rate;  // CFL rate max as double bits (non-negative doubles order as
                              // unsigned integers)
   double *dt_step;           // time step of the current step
@@ -56,6 +74,8 @@ struct StageArgs {
   unsigned int *flags;       // bit 0 non-finite, bit 1 no convergence
   int *max_sweeps;
   Phys ph;
+  CstT<float> cf;
+  CstT<double> cd;
 };
 
 enum Flag : unsigned int { kFlagNonFinite = 1u, kFlagNoConv = 2u };

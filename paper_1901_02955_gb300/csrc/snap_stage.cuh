@@ -64,11 +64,19 @@ struct Lay {
   static constexpr bool MOIST = NVAP > 0 && NCOND > 0;
 };
 
+template <class R>
+__device__ __forceinline__ const CstT<R> &cst(const StageArgs &a);
+template <>
+__device__ __forceinline__ const CstT<float> &cst<float>(const StageArgs &a) { return a.cf; }
+template <>
+__device__ __forceinline__ const CstT<double> &cst<double>(const StageArgs &a) { return a.cd; }
+
 template <bool D3>
 struct Tile;
 template <>
-struct Tile<false> {  // x-z plane
-  static constexpr int TX = 32, TY = 1, TZ = 16, NT = 256;
+struct Tile<false> {  // x-z plane: 32 x 14 keeps every per-direction phase of 256 threads
+                      // 87-100 % busy (e.g. 34 x 14 reconstructions, 32 x 15 z-faces)
+  static constexpr int TX = 32, TY = 1, TZ = 14, NT = 256;
 };
 template <>
 struct Tile<true> {
@@ -86,7 +94,7 @@ struct Box {
   static constexpr int NFZ = T::TX * T::TY * (T::TZ + 1);
   static constexpr int NF = NFX > NFZ ? (NFX > NFY ? NFX : NFY) : (NFZ > NFY ? NFZ : NFY);
   static constexpr int NCELL = T::TX * T::TY * T::TZ;
-  static constexpr int CPT = NCELL / T::NT;  // owned cells per thread
+  static constexpr int CPT = (NCELL + T::NT - 1) / T::NT;  // owned cells per thread
   static __device__ __forceinline__ int at(int bx, int by, int bz) {
     return (bz * BY + by) * BX + bx;
   }
@@ -101,8 +109,8 @@ struct Box {
 // formed from small numbers. Moist: the inversion U = rho e - K - A, T = U / C_v, p = R_m T
 // runs in FP64.
 template <class R, class L>
-__device__ __forceinline__ void cons_to_prim(const Phys &ph, const R *y, R *x, double pbar,
-                                             double eref, R &p_tot, R &T_out) {
+__device__ __forceinline__ void cons_to_prim(const Phys &ph, const CstT<R> &C, const R *y, R *x,
+                                             double pbar, double eref, R &p_tot, R &T_out) {
   R rho = y[0];
 #pragma unroll
   for (int s = 1; s < L::IM0; ++s) rho += y[s];
@@ -119,11 +127,11 @@ __device__ __forceinline__ void cons_to_prim(const Phys &ph, const R *y, R *x, d
   K *= R(0.5);
   if constexpr (L::NVAP == 0) {
     // dry: p = (gamma_d - 1) (rho e - K), so p - pbar = (gamma_d - 1) (y_E - K)
-    const R pp = R(ph.gamma_d - 1.0) * (y[L::IE] - K);
+    const R pp = C.gm1 * (y[L::IE] - K);
     x[L::IE] = pp;
     const R p = pp + R(pbar);
     p_tot = p;
-    T_out = p * Ar<R>::rcp(rho * R(ph.R_d));
+    T_out = p * ir * C.iR_d;
     (void)eref;
   } else {
     double A = 0.0, Cv = y[0], Rm = y[0];
@@ -151,16 +159,16 @@ __device__ __forceinline__ void cons_to_prim(const Phys &ph, const R *y, R *x, d
 // mixing factors of App. B: num = 1 + sum q_i (sigma_vi - 1) + sum q_ij (sigma_ij - 1),
 // den = 1 + sum q_i (1/eps_i - 1) - sum q_ij
 template <class R, class L>
-__device__ __forceinline__ void mix_factors(const Phys &ph, const R *x, R &num, R &den) {
+__device__ __forceinline__ void mix_factors(const CstT<R> &C, const R *x, R &num, R &den) {
   num = R(1);
   den = R(1);
 #pragma unroll
   for (int i = 0; i < L::NVAP; ++i) {
-    num += x[1 + i] * R(ph.sig_v[i] - 1.0);
-    den += x[1 + i] * R(ph.inv_eps[i] - 1.0);
+    num += x[1 + i] * C.sigv_m1[i];
+    den += x[1 + i] * C.ieps_m1[i];
 #pragma unroll
     for (int j = 0; j < L::NCOND; ++j) {
-      num += x[L::cond(i, j)] * R(ph.sig_c[i][j] - 1.0);
+      num += x[L::cond(i, j)] * C.sigc_m1[i][j];
       den -= x[L::cond(i, j)];
     }
   }
@@ -201,17 +209,17 @@ __device__ __forceinline__ R weno5(R a, R b, R c, R d, R e, R eps) {
 // Phi = (rho_d, rho_i, rho_ij, rho u, [rho v], rho w, rho e + p) of side S.
 // ------------------------------------------------------------------------------------------
 template <class R, class L>
-__device__ __forceinline__ void lmars(const Phys &ph, const R *XL, const R *XR, int dir,
+__device__ __forceinline__ void lmars(const CstT<R> &C, const R *XL, const R *XR, int dir,
                                       R pref, R *F) {
   const int mn = L::mom(dir);
   R numL, denL, numR, denR;
-  mix_factors<R, L>(ph, XL, numL, denL);
-  mix_factors<R, L>(ph, XR, numR, denR);
-  const R gm1 = R(ph.gamma_d - 1.0);
+  mix_factors<R, L>(C, XL, numL, denL);
+  mix_factors<R, L>(C, XR, numR, denR);
+  const R gm1 = C.gm1;
   R pL = pref + XL[L::IE], pR = pref + XR[L::IE];
   R gamL, gamR;
   if constexpr (L::NVAP == 0) {
-    gamL = gamR = R(ph.gamma_d);
+    gamL = gamR = C.gamma_d;
   } else {
     gamL = R(1) + gm1 * Ar<R>::div(denL, numL);
     gamR = R(1) + gm1 * Ar<R>::div(denR, numR);
@@ -246,13 +254,13 @@ __device__ __forceinline__ void lmars(const Phys &ph, const R *XL, const R *XR, 
 #pragma unroll
   for (int i = 0; i < L::NVAP; ++i)
 #pragma unroll
-    for (int j = 0; j < L::NCOND; ++j) A += R(ph.mu[i][j]) * XS[L::cond(i, j)];
+    for (int j = 0; j < L::NCOND; ++j) A += C.mu[i][j] * XS[L::cond(i, j)];
   A *= rhoS;
   R rhoe;
   if constexpr (L::NVAP == 0)
-    rhoe = pS * Ar<R>::rcp(gm1) + K;
+    rhoe = pS * C.igm1 + K;
   else
-    rhoe = Ar<R>::div(numS, denS) * pS * Ar<R>::rcp(gm1) + K + A;
+    rhoe = Ar<R>::div(numS, denS) * pS * C.igm1 + K + A;
   F[L::IE] = us * (rhoe + pS);
 }
 
@@ -286,7 +294,7 @@ __device__ __forceinline__ void cell_Tp(const Phys &ph, const R *y, double eref,
 }
 
 template <class R, class L>
-__device__ int satadj_cell(const Phys &ph, R *y, double eref, int max_iter, double tol) {
+__device__ int satadj_cell(const Phys &ph, const CstT<R> &C, R *y, double eref, int max_iter) {
   if constexpr (!L::MOIST) {
     return 0;
   } else {
@@ -304,26 +312,26 @@ __device__ int satadj_cell(const Phys &ph, R *y, double eref, int max_iter, doub
           R tot = y[1 + k];
 #pragma unroll
           for (int j = 0; j < L::NCOND; ++j) tot += y[L::cond(k, j)];
-          N += tot * R(ph.inv_eps[k]);
-          gas += y[1 + k] * R(ph.inv_eps[k]);
-          heat += tot * R(ph.inv_eps[k]) * R(ph.sig_hat[k] - 1.0);
+          N += tot * C.inv_eps[k];
+          gas += y[1 + k] * C.inv_eps[k];
+          heat += tot * C.inv_eps[k] * C.sighat_m1[k];
         }
         const R iN = Ar<R>::rcp(N);
         heat *= iN;
-        R qv = y[1 + i] * R(ph.inv_eps[i]) * iN;
-        R qc = y[L::cond(i, 0)] * R(ph.inv_eps[i]) * iN;
+        R qv = y[1 + i] * C.inv_eps[i] * iN;
+        R qc = y[L::cond(i, 0)] * C.inv_eps[i] * iN;
         R gsum = gas * iN - qv;
-        R t = T * R(1.0 / ph.Tref[i]);
+        R t = T * C.inv_Tref[i];
         // p* = p^r exp[beta (1 - 1/t) - delta ln t] with 1 - 1/t = (T - T^r) / T
-        R ps = R(ph.pref[i]) *
-               Ar<R>::exp_(R(ph.beta[i]) * dTr * Ar<R>::rcp(T) - R(ph.delta[i]) * Ar<R>::log_(t));
+        R ps = C.pref[i] *
+               Ar<R>::exp_(C.beta[i] * dTr * Ar<R>::rcp(T) - C.delta[i] * Ar<R>::log_(t));
         R s = Ar<R>::div(ps, p);
         R dq;
         if (s >= R(1)) {
           dq = -qc;
         } else {
-          R bt = R(ph.beta[i]) * Ar<R>::rcp(t) - R(ph.delta[i]);
-          R alpha = R(ph.gamma_d - 1.0) * (bt - R(1)) * Ar<R>::rcp(R(1) + heat);
+          R bt = C.beta[i] * Ar<R>::rcp(t) - C.delta[i];
+          R alpha = C.gm1 * (bt - R(1)) * Ar<R>::rcp(R(1) + heat);
           R om = R(1) - s;
           R r = Ar<R>::div(s, om);
           dq = Ar<R>::div(qv - r * gsum, R(1) + Ar<R>::div(s, om * om) * bt * alpha * gsum);
@@ -336,53 +344,16 @@ __device__ int satadj_cell(const Phys &ph, R *y, double eref, int max_iter, doub
           dq = -qc;
           drho = -y[L::cond(i, 0)];
         } else {
-          drho = dq * R(ph.eps[i]) * N;
+          drho = dq * C.eps[i] * N;
         }
         y[1 + i] -= drho;
         y[L::cond(i, 0)] += drho;
-        if (fabs(double(dq)) > tol * double(qv + qc)) conv = false;
+        if (fabs(dq) > C.satadj_tol * (qv + qc)) conv = false;
       }
       if (conv) return sweep;
     }
     return -1;
   }
-}
-
-// CFL rate sum_d (|u_d| + c) / dx_d of one cell (the time-step rule of the library).
-template <class R, class L>
-__device__ __forceinline__ double cell_rate(const Phys &ph, const R *y, double eref, double idx,
-                                            double idy, double idz) {
-  double T, p;
-  double rho = 0.0;
-#pragma unroll
-  for (int s = 0; s < L::IM0; ++s) rho += double(y[s]);
-  if constexpr (L::NVAP == 0) {
-    double K2 = 0.0;
-#pragma unroll
-    for (int m = 0; m < L::NMOM; ++m) K2 += double(y[L::IM0 + m]) * double(y[L::IM0 + m]);
-    p = (ph.gamma_d - 1.0) * ((double(y[L::IE]) + eref) - 0.5 * K2 / rho);
-    T = 0.0;
-  } else {
-    cell_Tp<R, L>(ph, y, eref, T, p);
-  }
-  // gamma of App. B from the mass fractions
-  double num = 1.0, den = 1.0;
-#pragma unroll
-  for (int i = 0; i < L::NVAP; ++i) {
-    num += double(y[1 + i]) / rho * (ph.sig_v[i] - 1.0);
-    den += double(y[1 + i]) / rho * (ph.inv_eps[i] - 1.0);
-#pragma unroll
-    for (int j = 0; j < L::NCOND; ++j) {
-      num += double(y[L::cond(i, j)]) / rho * (ph.sig_c[i][j] - 1.0);
-      den -= double(y[L::cond(i, j)]) / rho;
-    }
-  }
-  double gam = 1.0 + (ph.gamma_d - 1.0) * den / num;
-  double c = sqrt(gam * p / rho);
-  double r = (fabs(double(y[L::mom(0)])) / rho + c) * idx + (fabs(double(y[L::mom(2)])) / rho + c) * idz;
-  if constexpr (L::D3) r += (fabs(double(y[L::mom(1)])) / rho + c) * idy;
-  (void)T;
-  return r;
 }
 
 __device__ __forceinline__ int map_index(int g, int n, int bc_lo, int bc_hi, bool &flip) {
@@ -430,14 +401,139 @@ __device__ __forceinline__ double block_max(double v, double *red) {
 // ------------------------------------------------------------------------------------------
 // the fused stage kernel
 // ------------------------------------------------------------------------------------------
+// Per-level reference values in the kernel's type: FP32 kernels read FP32 copies, FP64
+// kernels the FP64 originals.
+template <class R>
+struct Prof;
+template <>
+struct Prof<float> {
+  static __device__ __forceinline__ float pc(const DomDev &D, int k) { return D.pc_f[k]; }
+  static __device__ __forceinline__ float pf(const DomDev &D, int k) { return D.pf_f[k]; }
+  static __device__ __forceinline__ float er(const DomDev &D, int k) { return D.er_f[k]; }
+  // rho - rho_bar_k from the conserved densities y: dry air minus the FP32 head of rho_bar is
+  // exact (the two are within a factor of 2), the tracers are added to that small difference,
+  // and the FP32 tail of rho_bar (rb_lo) last
+  template <class L>
+  static __device__ __forceinline__ float drho(const DomDev &D, int k, const float *y) {
+    float r = y[0] - D.rb_hi[k];
+#pragma unroll
+    for (int s = 1; s < L::IM0; ++s) r += y[s];
+    return r - D.rb_lo[k];
+  }
+  static __device__ __forceinline__ float grav(const DomDev &D) { return D.fgrav; }
+  static __device__ __forceinline__ float ih(const DomDev &D, int d) {
+    return d == 0 ? D.fidx : (d == 1 ? D.fidy : D.fidz);
+  }
+};
+template <>
+struct Prof<double> {
+  static __device__ __forceinline__ double pc(const DomDev &D, int k) { return D.p_cell[k]; }
+  static __device__ __forceinline__ double pf(const DomDev &D, int k) { return D.p_face[k]; }
+  static __device__ __forceinline__ double er(const DomDev &D, int k) { return D.e_ref[k]; }
+  template <class L>
+  static __device__ __forceinline__ double drho(const DomDev &D, int k, const double *y) {
+    double r = y[0];
+#pragma unroll
+    for (int s = 1; s < L::IM0; ++s) r += y[s];
+    return r - D.rho_bar[k];
+  }
+  static __device__ __forceinline__ double grav(const DomDev &D) { return D.grav; }
+  static __device__ __forceinline__ double ih(const DomDev &D, int d) {
+    return d == 0 ? D.idx : (d == 1 ? D.idy : D.idz);
+  }
+};
+
+// WENO5 of Sec. 4.2 evaluated once per cell c for both of its faces from the five cells
+// (a, b, c, d, e) = Q_{c-2} .. Q_{c+2}:
+//   qm = left state at face c+1/2   = I_weno(Q_{c-2}, .., Q_{c+2})
+//   qp = right state at face c-1/2  = I_weno(Q_{c+2}, .., Q_{c-2})  (Eq. q+, mirror stencil)
+// The Jiang-Shu smoothness indicator of a 3-cell triple does not depend on the direction the
+// triple is read in, so the three indicators (and their inverse squares) serve both faces; the
+// mirror stencil takes them in reverse order. The weights are rescaled by the smallest
+// (eps + beta)^2, which cancels in the normalisation and keeps every sum in range.
+template <class R>
+__device__ __forceinline__ void weno5_pair(R a, R b, R c, R d, R e, R eps, R &qm, R &qp) {
+  R t;
+  t = a - R(2) * b + c;
+  R b0 = R(13.0 / 12.0) * t * t;
+  t = a - R(4) * b + R(3) * c;
+  b0 += R(0.25) * t * t;
+  t = b - R(2) * c + d;
+  R b1 = R(13.0 / 12.0) * t * t;
+  t = b - d;
+  b1 += R(0.25) * t * t;
+  t = c - R(2) * d + e;
+  R b2 = R(13.0 / 12.0) * t * t;
+  t = R(3) * c - R(4) * d + e;
+  b2 += R(0.25) * t * t;
+  const R s0 = eps + b0, s1 = eps + b1, s2 = eps + b2;
+  const R sm = fmin(s0, fmin(s1, s2));
+  R g0 = sm * Ar<R>::rcp(s0), g1 = sm * Ar<R>::rcp(s1), g2 = sm * Ar<R>::rcp(s2);
+  g0 *= g0;
+  g1 *= g1;
+  g2 *= g2;
+  // six times the candidate interpolants of Eq. weno5, for both faces
+  const R m0 = R(2) * a - R(7) * b + R(11) * c;
+  const R m1 = -b + R(5) * c + R(2) * d;
+  const R m2 = R(2) * c + R(5) * d - e;
+  const R p0 = R(2) * e - R(7) * d + R(11) * c;
+  const R p1 = -d + R(5) * c + R(2) * b;
+  const R p2 = R(2) * c + R(5) * b - a;
+  // left state: weights (0.1, 0.6, 0.3) on (g0, g1, g2); right state: on (g2, g1, g0)
+  const R Sm = R(0.1) * g0 + R(0.6) * g1 + R(0.3) * g2;
+  const R Nm = R(0.1) * g0 * m0 + R(0.6) * g1 * m1 + R(0.3) * g2 * m2;
+  const R Sp = R(0.1) * g2 + R(0.6) * g1 + R(0.3) * g0;
+  const R Np = R(0.1) * g2 * p0 + R(0.6) * g1 * p1 + R(0.3) * g0 * p2;
+  const R r = R(1.0 / 6.0) * Ar<R>::rcp(Sm * Sp);
+  qm = Nm * Sp * r;
+  qp = Np * Sm * r;
+}
+
+// CFL rate sum_d (|u_d| + c) / dx_d in the kernel's type (FP32 kernels: FP32; the time step
+// only needs a few digits). The energy entry is stored as rho e - eref.
+template <class R, class L>
+__device__ __forceinline__ R cell_rate_r(const CstT<R> &C, const R *y, R eref, R idx, R idy,
+                                         R idz) {
+  R rho = y[0];
+#pragma unroll
+  for (int s = 1; s < L::IM0; ++s) rho += y[s];
+  const R ir = Ar<R>::rcp(rho);
+  R K2 = R(0);
+#pragma unroll
+  for (int m = 0; m < L::NMOM; ++m) K2 += y[L::IM0 + m] * y[L::IM0 + m];
+  R num = R(1), den = R(1), A = R(0), Cv = y[0], Rm = y[0];
+#pragma unroll
+  for (int i = 0; i < L::NVAP; ++i) {
+    num += y[1 + i] * ir * C.sigv_m1[i];
+    den += y[1 + i] * ir * C.ieps_m1[i];
+    Cv += C.sig_v[i] * y[1 + i];
+    Rm += C.inv_eps[i] * y[1 + i];
+#pragma unroll
+    for (int j = 0; j < L::NCOND; ++j) {
+      num += y[L::cond(i, j)] * ir * C.sigc_m1[i][j];
+      den -= y[L::cond(i, j)] * ir;
+      Cv += C.sig_c[i][j] * y[L::cond(i, j)];
+      A += C.mu[i][j] * y[L::cond(i, j)];
+    }
+  }
+  const R U = (y[L::IE] + eref) - R(0.5) * K2 * ir - A;
+  // p = R_d R_m T and T = U / (c_vd C_v), with R_m, C_v here the sums over densities
+  const R p = C.gm1 * Rm * Ar<R>::div(U, Cv);
+  const R gam = R(1) + C.gm1 * Ar<R>::div(den, num);
+  const R c = Ar<R>::sqrt_(gam * p * ir);
+  R r = (fabs(y[L::mom(0)]) * ir + c) * idx + (fabs(y[L::mom(2)]) * ir + c) * idz;
+  if constexpr (L::D3) r += (fabs(y[L::mom(1)]) * ir + c) * idy;
+  return r;
+}
+
 template <class R, class L, bool VISC>
 struct StageSmem {
   using B = Box<L::D3>;
   static constexpr size_t prim = sizeof(R) * L::NV * B::NBOX;
   static constexpr size_t visc = VISC ? sizeof(R) * 2 * B::NBOX : 0;
-  static constexpr size_t flux = sizeof(R) * L::NV * B::NF;
+  static constexpr size_t face = sizeof(R) * 2 * L::NV * B::NF;  // left state/flux, right state
   static constexpr size_t red = 32 * sizeof(double);
-  static constexpr size_t total = prim + visc + flux + red;
+  static constexpr size_t total = prim + visc + face + red;
 };
 
 template <class R, class L, bool VISC>
@@ -446,15 +542,20 @@ __global__ void __launch_bounds__(Tile<L::D3>::NT)
   using T = Tile<L::D3>;
   using B = Box<L::D3>;
   using S = StageSmem<R, L, VISC>;
+  using P = Prof<R>;
   constexpr int NV = L::NV;
+  constexpr int TX = T::TX, TY = T::TY, TZ = T::TZ, NT = T::NT;
   extern __shared__ __align__(16) unsigned char smem[];
   R *s_prim = reinterpret_cast<R *>(smem);
   R *s_th = reinterpret_cast<R *>(smem + S::prim);
   R *s_pi = s_th + (VISC ? B::NBOX : 0);
-  R *s_flux = reinterpret_cast<R *>(smem + S::prim + S::visc);
-  double *s_red = reinterpret_cast<double *>(smem + S::prim + S::visc + S::flux);
+  R *s_fl = reinterpret_cast<R *>(smem + S::prim + S::visc);  // left states, then fluxes
+  R *s_fr = s_fl + NV * B::NF;                                 // right states
+  double *s_red = reinterpret_cast<double *>(smem + S::prim + S::visc + S::face);
   const Phys &ph = a.ph;
-  const R weps = R(ph.weno_eps);
+  const CstT<R> &C = cst<R>(a);
+  const R weps = C.weno_eps;
+  const int tid = threadIdx.x;
 
   for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
     const int dm = find_domain(a.tile_domain, a.ndom, tile);
@@ -462,70 +563,79 @@ __global__ void __launch_bounds__(Tile<L::D3>::NT)
     const int nx = D.nx, ny = D.ny, nz = D.nz;
     const long long ncell = D.ncell;
     const int lt = tile - D.tile_begin;
-    const int x0 = (lt % D.tx) * T::TX;
-    const int y0 = ((lt / D.tx) % D.ty) * T::TY;
-    const int z0 = (lt / (D.tx * D.ty)) * T::TZ;
-    const int ex = min(T::TX, nx - x0), ey = min(T::TY, ny - y0), ez = min(T::TZ, nz - z0);
-    const R *Ys = reinterpret_cast<const R *>(D.buf[a.stage == 0 ? 0 : a.stage]);
+    const int x0 = (lt % D.tx) * TX;
+    const int y0 = ((lt / D.tx) % D.ty) * TY;
+    const int z0 = (lt / (D.tx * D.ty)) * TZ;
+    const int ex = min(TX, nx - x0), ey = min(TY, ny - y0), ez = min(TZ, nz - z0);
+    const R *Ys = reinterpret_cast<const R *>(D.buf[a.stage]);
     const R *Yn = reinterpret_cast<const R *>(D.buf[0]);
     R *Yo = reinterpret_cast<R *>(D.buf[a.stage == 0 ? 1 : (a.stage == 1 ? 2 : 0)]);
-    double dt;
-    if (a.stage == 0) {
-      dt = D.dt_fixed > 0.0 ? D.dt_fixed : D.cfl / __longlong_as_double((long long)*D.rate);
-      if (lt == 0 && threadIdx.x == 0) *D.dt_step = dt;
-    } else {
-      dt = *D.dt_step;
-      if (a.stage == 1 && lt == 0 && threadIdx.x == 0) *D.rate = 0ull;
+    // the stage's time step, formed once per CTA
+    if (tid == 0) {
+      double dt;
+      if (a.stage == 0) {
+        dt = D.dt_fixed > 0.0 ? D.dt_fixed : D.cfl / __longlong_as_double((long long)*D.rate);
+        if (lt == 0) *D.dt_step = dt;
+      } else {
+        dt = *D.dt_step;
+        if (a.stage == 1 && lt == 0) *D.rate = 0ull;
+      }
+      s_red[0] = dt;
     }
 
     // ---- 1. owned cells: load, keep the conserved values, store primitives -------------
     R ys[B::CPT][NV];
 #pragma unroll
     for (int m = 0; m < B::CPT; ++m) {
-      const int c = threadIdx.x + m * T::NT;
-      const int lx = c % T::TX, ly = (c / T::TX) % T::TY, lz = c / (T::TX * T::TY);
-      if (lx < ex && ly < ey && lz < ez) {
-        const long long g = ((long long)(z0 + lz) * ny + (y0 + ly)) * nx + (x0 + lx);
+      const int c = tid + m * NT;
+      const int lx = c % TX, ly = (c / TX) % TY, lz = c / (TX * TY);
+      if (c < B::NCELL && lx < ex && ly < ey && lz < ez) {
+        const int k = z0 + lz;
+        const long long g = ((long long)k * ny + (y0 + ly)) * nx + (x0 + lx);
 #pragma unroll
         for (int v = 0; v < NV; ++v) ys[m][v] = Ys[v * ncell + g];
         R x[NV], pt, Tt;
-        cons_to_prim<R, L>(ph, ys[m], x, D.p_cell[z0 + lz], D.e_ref[z0 + lz], pt, Tt);
+        cons_to_prim<R, L>(ph, C, ys[m], x, D.p_cell[k], D.e_ref[k], pt, Tt);
+        if constexpr (L::NVAP == 0) pt = x[L::IE] + P::pc(D, k);
         const int bi = B::at(lx + 3, ly + B::HY, lz + 3);
 #pragma unroll
         for (int v = 0; v < NV; ++v) s_prim[v * B::NBOX + bi] = x[v];
         if constexpr (VISC) {
-          const R Pi = Ar<R>::pow_(pt * R(1e-5), R(ph.kappa));
-          s_th[bi] = Tt * Ar<R>::rcp(Pi);
+          const R Pi = Ar<R>::pow_(pt * R(1e-5), C.kappa);
+          s_th[bi] = pt * Ar<R>::rcp(x[0] * Pi) * C.iR_d;
           s_pi[bi] = Pi;
         }
       }
     }
-    // ---- 2. halo cells of the cross (x, y, z), ghosts synthesised from the boundary rule --
+    // ---- 2. halo of the cross (x, y, z), boundary ghosts synthesised --------------------
     {
-      const int nhx = 6 * ey * ez, nhy = L::D3 ? 6 * ex * ez : 0, nhz = 6 * ex * ey;
-      for (int h = threadIdx.x; h < nhx + nhy + nhz; h += T::NT) {
+      constexpr int NHX = 6 * TY * TZ, NHY = L::D3 ? 6 * TX * TZ : 0, NHZ = 6 * TX * TY;
+      for (int h = tid; h < NHX + NHY + NHZ; h += NT) {
         int bx, by, bz, dirn;
-        if (h < nhx) {
-          int r = h % 6, q = h / 6;
+        bool ok;
+        if (h < NHX) {
+          const int r = h % 6, q = h / 6, ly = q % TY, lz = q / TY;
+          ok = ly < ey && lz < ez;
           bx = r < 3 ? r : ex + r;
-          by = q % ey + B::HY;
-          bz = q / ey + 3;
+          by = ly + B::HY;
+          bz = lz + 3;
           dirn = 0;
-        } else if (h < nhx + nhy) {
-          int hh = h - nhx;
-          int r = (hh / ex) % 6, q = hh / (6 * ex);
-          bx = hh % ex + 3;
+        } else if (h < NHX + NHY) {
+          const int hh = h - NHX, lx = hh % TX, r = (hh / TX) % 6, lz = hh / (6 * TX);
+          ok = lx < ex && lz < ez;
+          bx = lx + 3;
           by = r < 3 ? r : ey + r;
-          bz = q + 3;
+          bz = lz + 3;
           dirn = 1;
         } else {
-          int hh = h - nhx - nhy;
-          int r = (hh / (ex * ey)) % 6;
-          bx = hh % ex + 3;
-          by = (hh / ex) % ey + B::HY;
+          const int hh = h - NHX - NHY, lx = hh % TX, ly = (hh / TX) % TY, r = hh / (TX * TY);
+          ok = lx < ex && ly < ey;
+          bx = lx + 3;
+          by = ly + B::HY;
           bz = r < 3 ? r : ez + r;
           dirn = 2;
         }
+        if (!ok) continue;
         int gx = x0 + bx - 3, gy = y0 + by - B::HY, gz = z0 + bz - 3;
         bool flip = false;
         if (dirn == 0) gx = map_index(gx, nx, D.bc[0], D.bc[1], flip);
@@ -535,19 +645,21 @@ __global__ void __launch_bounds__(Tile<L::D3>::NT)
         R y[NV], x[NV], pt, Tt;
 #pragma unroll
         for (int v = 0; v < NV; ++v) y[v] = Ys[v * ncell + g];
-        cons_to_prim<R, L>(ph, y, x, D.p_cell[gz], D.e_ref[gz], pt, Tt);
+        cons_to_prim<R, L>(ph, C, y, x, D.p_cell[gz], D.e_ref[gz], pt, Tt);
+        if constexpr (L::NVAP == 0) pt = x[L::IE] + P::pc(D, gz);
         if (flip) x[L::mom(dirn)] = -x[L::mom(dirn)];
         const int bi = B::at(bx, by, bz);
 #pragma unroll
         for (int v = 0; v < NV; ++v) s_prim[v * B::NBOX + bi] = x[v];
         if constexpr (VISC) {
-          const R Pi = Ar<R>::pow_(pt * R(1e-5), R(ph.kappa));
-          s_th[bi] = Tt * Ar<R>::rcp(Pi);
+          const R Pi = Ar<R>::pow_(pt * R(1e-5), C.kappa);
+          s_th[bi] = pt * Ar<R>::rcp(x[0] * Pi) * C.iR_d;
           s_pi[bi] = Pi;
         }
       }
     }
     __syncthreads();
+    const R dt = R(s_red[0]);
 
     R acc[B::CPT][NV];
 #pragma unroll
@@ -555,93 +667,123 @@ __global__ void __launch_bounds__(Tile<L::D3>::NT)
 #pragma unroll
       for (int v = 0; v < NV; ++v) acc[m][v] = R(0);
 
-    // ---- 3. per direction: WENO5 both sides, LMARS, flux divergence ---------------------
+    // ---- 3. per direction: WENO5 per cell (both faces), LMARS per face, divergence -------
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       if (d == 1 && !L::D3) continue;
       const int fx = d == 0, fy = d == 1, fz = d == 2;
-      const int nfx = ex + fx, nfy = ey + fy, nfz = ez + fz;
-      const int sx = T::TX + fx, sy = T::TY + fy;  // flux array strides
+      // face array strides: faces along d are numbered 0..T_d
+      const int sx = TX + fx, sy = TY + fy;
       const int stride = d == 0 ? 1 : (d == 1 ? B::BX : B::BX * B::BY);
-      const double hd = d == 0 ? D.dx : (d == 1 ? D.dy : D.dz);
-      for (int f = threadIdx.x; f < nfx * nfy * nfz; f += T::NT) {
-        const int ix = f % nfx, iy = (f / nfx) % nfy, iz = f / (nfx * nfy);
-        const int bi = B::at(ix + 3, iy + B::HY, iz + 3);  // right cell of the face
-        R QL[NV], QR[NV], F[NV];
+      const int ed = d == 0 ? ex : (d == 1 ? ey : ez);
+      // 3a. reconstruction over the owned cells and one more on each side along d
+      {
+        constexpr int RX0 = TX + 2, RY0 = TY + 2, RZ0 = TZ + 2;
+        const int rx = fx ? RX0 : TX, ry = fy ? RY0 : TY;
+        const int nrec = d == 0 ? RX0 * TY * TZ : (d == 1 ? TX * RY0 * TZ : TX * TY * RZ0);
+        for (int it = tid; it < nrec; it += NT) {
+          int lx = it % rx, ly = (it / rx) % ry, lz = it / (rx * ry);
+          lx -= fx;
+          ly -= fy;
+          lz -= fz;
+          const int ld = fx ? lx : (fy ? ly : lz);
+          if (ld > ed || lx >= ex + fx || ly >= ey + fy || lz >= ez + fz) continue;
+          const int bi = B::at(lx + 3, ly + B::HY, lz + 3);
+          const int fl = ((lz + fz) * sy + (ly + fy)) * sx + (lx + fx);  // face c+1/2
+          const int fr = (lz * sy + ly) * sx + lx;                        // face c-1/2
+          const bool has_l = ld < ed, has_r = ld >= 0;
 #pragma unroll
-        for (int v = 0; v < NV; ++v) {
-          const R *q = s_prim + v * B::NBOX + bi;
-          R q0 = q[-3 * stride], q1 = q[-2 * stride], q2 = q[-stride], q3 = q[0],
-            q4 = q[stride], q5 = q[2 * stride];
-          QL[v] = weno5<R>(q0, q1, q2, q3, q4, weps);
-          QR[v] = weno5<R>(q5, q4, q3, q2, q1, weps);
-        }
-        const R pref = R(fz ? D.p_face[z0 + iz] : D.p_cell[z0 + iz]);
-        lmars<R, L>(ph, QL, QR, d, pref, F);
-        if constexpr (VISC) {
-          const int bl = bi - stride;
-          const R rl = s_prim[bl], rr = s_prim[bi];
-          const R rf = R(0.5) * (rl + rr);
-          const R ih = R(1.0 / hd), nu = R(ph.nu);
-          R work = R(0);
-#pragma unroll
-          for (int mm = 0; mm < L::NMOM; ++mm) {
-            const R ul = s_prim[(L::IM0 + mm) * B::NBOX + bl];
-            const R ur = s_prim[(L::IM0 + mm) * B::NBOX + bi];
-            const R grad = (ur - ul) * ih;
-            F[L::IM0 + mm] -= rf * nu * grad;
-            work += R(0.5) * (ul + ur) * grad;
+          for (int v = 0; v < NV; ++v) {
+            const R *q = s_prim + v * B::NBOX + bi;
+            R qm, qp;
+            weno5_pair<R>(q[-2 * stride], q[-stride], q[0], q[stride], q[2 * stride], weps, qm,
+                          qp);
+            if (has_l) s_fl[v * B::NF + fl] = qm;
+            if (has_r) s_fr[v * B::NF + fr] = qp;
           }
-          const R heat = R(0.5) * (s_pi[bl] + s_pi[bi]) * (s_th[bi] - s_th[bl]) * ih;
-          F[L::IE] -= rf * nu * work + rf * R(ph.c_pd) * nu * heat;
         }
-        const int fi = (iz * sy + iy) * sx + ix;
-#pragma unroll
-        for (int v = 0; v < NV; ++v) s_flux[v * B::NF + fi] = F[v];
       }
       __syncthreads();
-      const R ih = R(1.0 / hd);
+      // 3b. LMARS flux per face (and the viscous flux), written over the left state
+      {
+        const int nface = d == 0 ? (TX + 1) * TY * TZ : (d == 1 ? TX * (TY + 1) * TZ : TX * TY * (TZ + 1));
+        for (int f = tid; f < nface; f += NT) {
+          const int ix = f % sx, iy = (f / sx) % sy, iz = f / (sx * sy);
+          if (ix >= ex + fx || iy >= ey + fy || iz >= ez + fz) continue;
+          R QL[NV], QR[NV], F[NV];
+#pragma unroll
+          for (int v = 0; v < NV; ++v) {
+            QL[v] = s_fl[v * B::NF + f];
+            QR[v] = s_fr[v * B::NF + f];
+          }
+          const R pref = fz ? P::pf(D, z0 + iz) : P::pc(D, z0 + iz);
+          lmars<R, L>(C, QL, QR, d, pref, F);
+          if constexpr (VISC) {
+            const int bi = B::at(ix + 3, iy + B::HY, iz + 3);  // right cell of the face
+            const int bl = bi - stride;
+            const R rf = R(0.5) * (s_prim[bl] + s_prim[bi]);
+            const R ih = P::ih(D, d), nu = C.nu;
+            R work = R(0);
+#pragma unroll
+            for (int mm = 0; mm < L::NMOM; ++mm) {
+              const R ul = s_prim[(L::IM0 + mm) * B::NBOX + bl];
+              const R ur = s_prim[(L::IM0 + mm) * B::NBOX + bi];
+              const R grad = (ur - ul) * ih;
+              F[L::IM0 + mm] -= rf * nu * grad;
+              work += R(0.5) * (ul + ur) * grad;
+            }
+            const R heat = R(0.5) * (s_pi[bl] + s_pi[bi]) * (s_th[bi] - s_th[bl]) * ih;
+            F[L::IE] -= rf * nu * work + rf * C.c_pd * nu * heat;
+          }
+#pragma unroll
+          for (int v = 0; v < NV; ++v) s_fl[v * B::NF + f] = F[v];
+        }
+      }
+      __syncthreads();
+      // 3c. flux divergence of the owned cells (Eq. forward)
+      const R ih = P::ih(D, d);
 #pragma unroll
       for (int m = 0; m < B::CPT; ++m) {
-        const int c = threadIdx.x + m * T::NT;
-        const int lx = c % T::TX, ly = (c / T::TX) % T::TY, lz = c / (T::TX * T::TY);
-        if (lx < ex && ly < ey && lz < ez) {
+        const int c = tid + m * NT;
+        const int lx = c % TX, ly = (c / TX) % TY, lz = c / (TX * TY);
+        if (c < B::NCELL && lx < ex && ly < ey && lz < ez) {
           const int f0 = (lz * sy + ly) * sx + lx;
           const int f1 = ((lz + fz) * sy + (ly + fy)) * sx + (lx + fx);
 #pragma unroll
           for (int v = 0; v < NV; ++v)
-            acc[m][v] -= (s_flux[v * B::NF + f1] - s_flux[v * B::NF + f0]) * ih;
+            acc[m][v] -= (s_fl[v * B::NF + f1] - s_fl[v * B::NF + f0]) * ih;
         }
       }
       if (d != 2) __syncthreads();
     }
 
-    // ---- 4. sources, stage combine, saturation adjustment, store ------------------------
-    double rate_max = 0.0;
-    const double tol = fmax(ph.satadj_tol, 32.0 * Ar<R>::eps);
+    // ---- 4. gravity source, stage combine, saturation adjustment, store ------------------
+    R rate_max = R(0);
 #pragma unroll
     for (int m = 0; m < B::CPT; ++m) {
-      const int c = threadIdx.x + m * T::NT;
-      const int lx = c % T::TX, ly = (c / T::TX) % T::TY, lz = c / (T::TX * T::TY);
-      if (lx < ex && ly < ey && lz < ez) {
+      const int c = tid + m * NT;
+      const int lx = c % TX, ly = (c / TX) % TY, lz = c / (TX * TY);
+      if (c < B::NCELL && lx < ex && ly < ey && lz < ez) {
         const int k = z0 + lz;
         const int bi = B::at(lx + 3, ly + B::HY, lz + 3);
-        const R rho = s_prim[bi];
-        acc[m][L::mom(2)] -= (rho - R(D.rho_bar[k])) * R(D.grav);
-        const int f0 = (lz * T::TY + ly) * T::TX + lx;
-        const int f1 = ((lz + 1) * T::TY + ly) * T::TX + lx;
+        const R grav = P::grav(D);
+        // vertical momentum: -(rho - rho_bar) g (Eq. mom3 with the reference balance removed)
+        acc[m][L::mom(2)] -= P::template drho<L>(D, k, ys[m]) * grav;
+        // energy: -g (F_rho,k-1/2 + F_rho,k+1/2) / 2 with the vertical total-mass fluxes
+        const int f0 = (lz * TY + ly) * TX + lx;
+        const int f1 = ((lz + 1) * TY + ly) * TX + lx;
         R mb = R(0), mt = R(0);
 #pragma unroll
         for (int s = 0; s < L::IM0; ++s) {
-          mb += s_flux[s * B::NF + f0];
-          mt += s_flux[s * B::NF + f1];
+          mb += s_fl[s * B::NF + f0];
+          mt += s_fl[s * B::NF + f1];
         }
-        acc[m][L::IE] -= R(D.grav) * R(0.5) * (mb + mt);
+        acc[m][L::IE] -= grav * R(0.5) * (mb + mt);
         const long long g = ((long long)k * ny + (y0 + ly)) * nx + (x0 + lx);
         R yo[NV];
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
-          const R s1 = ys[m][v] + R(dt) * acc[m][v];
+          const R s1 = ys[m][v] + dt * acc[m][v];
           if (a.stage == 0) {
             yo[v] = s1;
           } else {
@@ -652,27 +794,27 @@ __global__ void __launch_bounds__(Tile<L::D3>::NT)
         }
         if constexpr (L::MOIST) {
           if (ph.satadj) {
-            const int it = satadj_cell<R, L>(ph, yo, D.e_ref[k], ph.satadj_max_iter, tol);
+            const int it = satadj_cell<R, L>(ph, C, yo, D.e_ref[k], ph.satadj_max_iter);
             if (it < 0)
               atomicOr(a.flags, (unsigned)kFlagNoConv);
-            else
+            else if (it > 2)
               atomicMax(a.max_sweeps, it);
           }
         }
         R rs = R(0);
 #pragma unroll
         for (int s = 0; s < L::IM0; ++s) rs += yo[s];
-        if (!(rs > R(0)) || !isfinite(double(yo[L::IE]))) atomicOr(a.flags, (unsigned)kFlagNonFinite);
+        if (!(rs > R(0)) || !isfinite(yo[L::IE])) atomicOr(a.flags, (unsigned)kFlagNonFinite);
 #pragma unroll
         for (int v = 0; v < NV; ++v) Yo[v * ncell + g] = yo[v];
         if (a.stage == 2)
-          rate_max = fmax(rate_max,
-                          cell_rate<R, L>(ph, yo, D.e_ref[k], 1.0 / D.dx, 1.0 / D.dy, 1.0 / D.dz));
+          rate_max = fmax(rate_max, cell_rate_r<R, L>(C, yo, P::er(D, k), P::ih(D, 0),
+                                                      P::ih(D, 1), P::ih(D, 2)));
       }
     }
     if (a.stage == 2) {
-      double bm = block_max(rate_max, s_red);
-      if (threadIdx.x == 0) atomicMax(D.rate, (unsigned long long)__double_as_longlong(bm));
+      double bm = block_max(double(rate_max), s_red + 1);
+      if (tid == 0) atomicMax(D.rate, (unsigned long long)__double_as_longlong(bm));
     }
     __syncthreads();
   }
@@ -692,8 +834,9 @@ __global__ void __launch_bounds__(256) rate_kernel(const StageArgs a, int dm, in
     R y[L::NV];
 #pragma unroll
     for (int v = 0; v < L::NV; ++v) y[v] = Y[v * D.ncell + c];
-    const double er = D.e_ref[c / ((long long)D.nx * D.ny)];
-    r = fmax(r, cell_rate<R, L>(a.ph, y, er, 1.0 / D.dx, 1.0 / D.dy, 1.0 / D.dz));
+    const int k = int(c / ((long long)D.nx * D.ny));
+    r = fmax(r, double(cell_rate_r<R, L>(cst<R>(a), y, Prof<R>::er(D, k), Prof<R>::ih(D, 0),
+                                         Prof<R>::ih(D, 1), Prof<R>::ih(D, 2))));
   }
   double bm = block_max(r, red);
   if (threadIdx.x == 0) atomicMax(D.rate, (unsigned long long)__double_as_longlong(bm));
@@ -757,14 +900,13 @@ template <class R, class L>
 __global__ void __launch_bounds__(256) satadj_kernel(const StageArgs a, int dm, int buf) {
   const DomDev &D = a.doms[dm];
   R *Y = reinterpret_cast<R *>(D.buf[buf]);
-  const double tol = fmax(a.ph.satadj_tol, 32.0 * Ar<R>::eps);
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < D.ncell;
        c += (long long)gridDim.x * blockDim.x) {
     R y[L::NV];
 #pragma unroll
     for (int v = 0; v < L::NV; ++v) y[v] = Y[v * D.ncell + c];
     const double er = D.e_ref[c / ((long long)D.nx * D.ny)];
-    const int it = satadj_cell<R, L>(a.ph, y, er, a.ph.satadj_max_iter, tol);
+    const int it = satadj_cell<R, L>(a.ph, cst<R>(a), y, er, a.ph.satadj_max_iter);
     if (it < 0)
       atomicOr(a.flags, (unsigned)kFlagNoConv);
     else
