@@ -33,6 +33,11 @@ struct Ar<float> {
   static __device__ __forceinline__ float exp_(float x) { return expf(x); }
   static __device__ __forceinline__ float log_(float x) { return logf(x); }
   static __device__ __forceinline__ float pow_(float x, float y) { return powf(x, y); }
+  // exp2(y log2 x) on the special-function unit: a few ulp when |y log2 x| is small, as for
+  // the Exner function (p / 1e5)^(R/c_p) near 1 bar
+  static __device__ __forceinline__ float pow_small(float x, float y) { return __powf(x, y); }
+  // sqrt of a positive argument as x * rsqrt(x) (~2 ulp): sound speeds
+  static __device__ __forceinline__ float sqrt_pos(float x) { return x * rsqrtf(x); }
   static constexpr double eps = 1.1920928955078125e-07;
 };
 template <>
@@ -43,6 +48,8 @@ struct Ar<double> {
   static __device__ __forceinline__ double exp_(double x) { return exp(x); }
   static __device__ __forceinline__ double log_(double x) { return log(x); }
   static __device__ __forceinline__ double pow_(double x, double y) { return pow(x, y); }
+  static __device__ __forceinline__ double pow_small(double x, double y) { return pow(x, y); }
+  static __device__ __forceinline__ double sqrt_pos(double x) { return sqrt(x); }
   static constexpr double eps = 2.220446049250313e-16;
 };
 
@@ -224,14 +231,16 @@ __device__ __forceinline__ void lmars(const CstT<R> &C, const R *XL, const R *XR
     gamL = R(1) + gm1 * Ar<R>::div(denL, numL);
     gamR = R(1) + gm1 * Ar<R>::div(denR, numR);
   }
-  R cL = Ar<R>::sqrt_(gamL * pL * Ar<R>::rcp(XL[0]));
-  R cR = Ar<R>::sqrt_(gamR * pR * Ar<R>::rcp(XR[0]));
+  R cL = Ar<R>::sqrt_pos(gamL * pL * Ar<R>::rcp(XL[0]));
+  R cR = Ar<R>::sqrt_pos(gamR * pR * Ar<R>::rcp(XR[0]));
   R rhoc = R(0.5) * (XL[0] + XR[0]) * R(0.5) * (cL + cR);
   R uL = XL[mn], uR = XR[mn];
   R ps = R(0.5) * (XL[L::IE] + XR[L::IE]) - R(0.5) * rhoc * (uR - uL);
   R us = R(0.5) * (uL + uR) - Ar<R>::div(XR[L::IE] - XL[L::IE], R(2) * rhoc);
   const bool left = us > R(0);
-  const R *XS = left ? XL : XR;
+  R XS[L::NV];
+#pragma unroll
+  for (int v = 0; v < L::NV; ++v) XS[v] = left ? XL[v] : XR[v];
   R numS = left ? numL : numR, denS = left ? denL : denR, pS = left ? pL : pR;
   R rhoS = XS[0];
   R mf = us * rhoS;
@@ -466,27 +475,24 @@ __device__ __forceinline__ void weno5_pair(R a, R b, R c, R d, R e, R eps, R &qm
   R b2 = R(13.0 / 12.0) * t * t;
   t = R(3) * c - R(4) * d + e;
   b2 += R(0.25) * t * t;
-  const R s0 = eps + b0, s1 = eps + b1, s2 = eps + b2;
-  const R sm = fmin(s0, fmin(s1, s2));
-  R g0 = sm * Ar<R>::rcp(s0), g1 = sm * Ar<R>::rcp(s1), g2 = sm * Ar<R>::rcp(s2);
+  // inverse squares 1 / (eps + beta_k)^2, shared by both faces
+  R g0 = Ar<R>::rcp(eps + b0), g1 = Ar<R>::rcp(eps + b1), g2 = Ar<R>::rcp(eps + b2);
   g0 *= g0;
   g1 *= g1;
   g2 *= g2;
-  // six times the candidate interpolants of Eq. weno5, for both faces
-  const R m0 = R(2) * a - R(7) * b + R(11) * c;
-  const R m1 = -b + R(5) * c + R(2) * d;
-  const R m2 = R(2) * c + R(5) * d - e;
-  const R p0 = R(2) * e - R(7) * d + R(11) * c;
-  const R p1 = -d + R(5) * c + R(2) * b;
-  const R p2 = R(2) * c + R(5) * b - a;
-  // left state: weights (0.1, 0.6, 0.3) on (g0, g1, g2); right state: on (g2, g1, g0)
+  // linear weight times the candidate interpolant of Eq. weno5: (0.1, 0.6, 0.3) x
+  // (1/3, -7/6, 11/6), (-1/6, 5/6, 1/3), (1/3, 5/6, -1/6); the right state reads the window
+  // backwards and takes the weights in reverse order
+  const R m0 = R(0.1 / 3.0) * a - R(0.7 / 6.0) * b + R(1.1 / 6.0) * c;
+  const R m1 = R(-0.1) * b + R(0.5) * c + R(0.2) * d;
+  const R m2 = R(0.1) * c + R(0.25) * d - R(0.05) * e;
+  const R p0 = R(0.1 / 3.0) * e - R(0.7 / 6.0) * d + R(1.1 / 6.0) * c;
+  const R p1 = R(-0.1) * d + R(0.5) * c + R(0.2) * b;
+  const R p2 = R(0.1) * c + R(0.25) * b - R(0.05) * a;
   const R Sm = R(0.1) * g0 + R(0.6) * g1 + R(0.3) * g2;
-  const R Nm = R(0.1) * g0 * m0 + R(0.6) * g1 * m1 + R(0.3) * g2 * m2;
   const R Sp = R(0.1) * g2 + R(0.6) * g1 + R(0.3) * g0;
-  const R Np = R(0.1) * g2 * p0 + R(0.6) * g1 * p1 + R(0.3) * g0 * p2;
-  const R r = R(1.0 / 6.0) * Ar<R>::rcp(Sm * Sp);
-  qm = Nm * Sp * r;
-  qp = Np * Sm * r;
+  qm = (g0 * m0 + g1 * m1 + g2 * m2) * Ar<R>::rcp(Sm);
+  qp = (g2 * p0 + g1 * p1 + g0 * p2) * Ar<R>::rcp(Sp);
 }
 
 // CFL rate sum_d (|u_d| + c) / dx_d in the kernel's type (FP32 kernels: FP32; the time step
@@ -601,7 +607,7 @@ __global__ void __launch_bounds__(Tile<L::D3>::NT)
 #pragma unroll
         for (int v = 0; v < NV; ++v) s_prim[v * B::NBOX + bi] = x[v];
         if constexpr (VISC) {
-          const R Pi = Ar<R>::pow_(pt * R(1e-5), C.kappa);
+          const R Pi = Ar<R>::pow_small(pt * R(1e-5), C.kappa);
           s_th[bi] = pt * Ar<R>::rcp(x[0] * Pi) * C.iR_d;
           s_pi[bi] = Pi;
         }
@@ -652,7 +658,7 @@ __global__ void __launch_bounds__(Tile<L::D3>::NT)
 #pragma unroll
         for (int v = 0; v < NV; ++v) s_prim[v * B::NBOX + bi] = x[v];
         if constexpr (VISC) {
-          const R Pi = Ar<R>::pow_(pt * R(1e-5), C.kappa);
+          const R Pi = Ar<R>::pow_small(pt * R(1e-5), C.kappa);
           s_th[bi] = pt * Ar<R>::rcp(x[0] * Pi) * C.iR_d;
           s_pi[bi] = Pi;
         }
@@ -678,38 +684,43 @@ __global__ void __launch_bounds__(Tile<L::D3>::NT)
       const int ed = d == 0 ? ex : (d == 1 ? ey : ez);
       // 3a. reconstruction over the owned cells and one more on each side along d
       {
-        constexpr int RX0 = TX + 2, RY0 = TY + 2, RZ0 = TZ + 2;
-        const int rx = fx ? RX0 : TX, ry = fy ? RY0 : TY;
-        const int nrec = d == 0 ? RX0 * TY * TZ : (d == 1 ? TX * RY0 * TZ : TX * TY * RZ0);
-        for (int it = tid; it < nrec; it += NT) {
+        const int rx = TX + 2 * fx, ry = TY + 2 * fy, rz = TZ + 2 * fz;
+        const int nrec = rx * ry * rz;
+        constexpr int MAXREC = (TX + 2) * (TY + (L::D3 ? 2 : 0)) * (TZ + 2);
+#pragma unroll
+        for (int r = 0; r < (MAXREC + NT - 1) / NT; ++r) {
+          const int it = tid + r * NT;
           int lx = it % rx, ly = (it / rx) % ry, lz = it / (rx * ry);
           lx -= fx;
           ly -= fy;
           lz -= fz;
           const int ld = fx ? lx : (fy ? ly : lz);
-          if (ld > ed || lx >= ex + fx || ly >= ey + fy || lz >= ez + fz) continue;
-          const int bi = B::at(lx + 3, ly + B::HY, lz + 3);
-          const int fl = ((lz + fz) * sy + (ly + fy)) * sx + (lx + fx);  // face c+1/2
-          const int fr = (lz * sy + ly) * sx + lx;                        // face c-1/2
-          const bool has_l = ld < ed, has_r = ld >= 0;
+          if (it < nrec && ld <= ed && lx < ex + fx && ly < ey + fy && lz < ez + fz) {
+            const int bi = B::at(lx + 3, ly + B::HY, lz + 3);
+            const int fl = ((lz + fz) * sy + (ly + fy)) * sx + (lx + fx);  // face c+1/2
+            const int fr = (lz * sy + ly) * sx + lx;                        // face c-1/2
+            const bool has_l = ld < ed, has_r = ld >= 0;
 #pragma unroll
-          for (int v = 0; v < NV; ++v) {
-            const R *q = s_prim + v * B::NBOX + bi;
-            R qm, qp;
-            weno5_pair<R>(q[-2 * stride], q[-stride], q[0], q[stride], q[2 * stride], weps, qm,
-                          qp);
-            if (has_l) s_fl[v * B::NF + fl] = qm;
-            if (has_r) s_fr[v * B::NF + fr] = qp;
+            for (int v = 0; v < NV; ++v) {
+              const R *q = s_prim + v * B::NBOX + bi;
+              R qm, qp;
+              weno5_pair<R>(q[-2 * stride], q[-stride], q[0], q[stride], q[2 * stride], weps,
+                            qm, qp);
+              if (has_l) s_fl[v * B::NF + fl] = qm;
+              if (has_r) s_fr[v * B::NF + fr] = qp;
+            }
           }
         }
       }
       __syncthreads();
       // 3b. LMARS flux per face (and the viscous flux), written over the left state
       {
-        const int nface = d == 0 ? (TX + 1) * TY * TZ : (d == 1 ? TX * (TY + 1) * TZ : TX * TY * (TZ + 1));
-        for (int f = tid; f < nface; f += NT) {
+        const int nface = sx * sy * (TZ + fz);
+#pragma unroll
+        for (int r = 0; r < (B::NF + NT - 1) / NT; ++r) {
+          const int f = tid + r * NT;
           const int ix = f % sx, iy = (f / sx) % sy, iz = f / (sx * sy);
-          if (ix >= ex + fx || iy >= ey + fy || iz >= ez + fz) continue;
+          if (f >= nface || ix >= ex + fx || iy >= ey + fy || iz >= ez + fz) continue;
           R QL[NV], QR[NV], F[NV];
 #pragma unroll
           for (int v = 0; v < NV; ++v) {
