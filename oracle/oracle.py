@@ -82,6 +82,10 @@ def _load():
     lib.orc_dt_cfl.argtypes = [G, _D, C.c_double]
     lib.orc_dt_cfl.restype = C.c_double
     lib.orc_budget.argtypes = [G, _D, _D]
+    lib.orc_weno5_gradient.argtypes = [_D, C.c_double, _D]
+    lib.orc_weno5_gradient.restype = C.c_double
+    lib.orc_rhs_adjoint.argtypes = [G, _D, _D, _D]
+    lib.orc_step_adjoint.argtypes = [G, _D, C.c_double, _D, _D]
     return lib
 
 
@@ -203,6 +207,24 @@ class Oracle:
         Y = np.ascontiguousarray(Y, dtype=np.float64).reshape(self.shape)
         return self.lib.orc_dt_cfl(C.byref(self.grid), _ptr(Y), self.w.cfl if cfl is None else cfl)
 
+    def rhs_adjoint(self, Y, mu):
+        Y = np.ascontiguousarray(Y, dtype=np.float64).reshape(self.shape)
+        mu = np.ascontiguousarray(mu, dtype=np.float64).reshape(self.shape)
+        out = np.zeros(self.shape)
+        rc = self.lib.orc_rhs_adjoint(C.byref(self.grid), _ptr(Y), _ptr(mu), _ptr(out))
+        if rc:
+            raise RuntimeError(f"orc_rhs_adjoint failed: {rc}")
+        return out
+
+    def step_adjoint(self, Yn, dt, lam_out):
+        Yn = np.ascontiguousarray(Yn, dtype=np.float64).reshape(self.shape)
+        lam_out = np.ascontiguousarray(lam_out, dtype=np.float64).reshape(self.shape)
+        out = np.zeros(self.shape)
+        rc = self.lib.orc_step_adjoint(C.byref(self.grid), _ptr(Yn), dt, _ptr(lam_out), _ptr(out))
+        if rc:
+            raise RuntimeError(f"orc_step_adjoint failed: {rc}")
+        return out
+
     def budget(self, Y):
         Y = np.ascontiguousarray(Y, dtype=np.float64).reshape(self.shape)
         out = np.zeros(self.nv + 1)
@@ -228,6 +250,13 @@ def weno5(q, eps=1e-6):
 def weno5_poly(q):
     q = np.ascontiguousarray(q, dtype=np.float64)
     return _lib().orc_weno5_poly(_ptr(q))
+
+
+def weno5_gradient(q, eps=1e-6):
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    g = np.zeros(5)
+    v = _lib().orc_weno5_gradient(_ptr(q), eps, _ptr(g))
+    return v, g
 
 
 def weno5_weights(q, eps=1e-6):

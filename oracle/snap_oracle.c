@@ -657,3 +657,346 @@ void orc_budget(const orc_grid *g, const double *Y, double *out) {
     }
   }
 }
+
+/* =======================================================================================
+ * Discrete adjoint of the dry stage (reverse of Eq. forward with WENO5 and LMARS, the
+ * gravity source and the SSP-RK3 combine), written by hand as the transpose of the forward
+ * routines above, step by step in reverse order. Not part of the paper: it differentiates
+ * the paper's discrete scheme. Branches are held fixed (upwind side of LMARS), and the time
+ * step is treated as a given constant.
+ * ======================================================================================= */
+
+/* I = orc_weno5(q) and its gradient dI/dq_j. With w_k = a_k / S, a_k = d_k (eps + b_k)^-2:
+ * dI/dq_j = sum_k w_k dv_k/dq_j + sum_m (v_m - I)/S * (-2 a_m / (eps + b_m)) db_m/dq_j. */
+static double weno5_grad(const double q[5], double eps, double grad[5]) {
+  static const double d[3] = {0.1, 0.6, 0.3};
+  static const double dv[3][5] = {{1.0 / 3.0, -7.0 / 6.0, 11.0 / 6.0, 0.0, 0.0},
+                                  {0.0, -1.0 / 6.0, 5.0 / 6.0, 1.0 / 3.0, 0.0},
+                                  {0.0, 0.0, 1.0 / 3.0, 5.0 / 6.0, -1.0 / 6.0}};
+  double b[3], a[3], v[3], db[3][5], S = 0.0, I = 0.0;
+  double t1, t2;
+  t1 = q[0] - 2.0 * q[1] + q[2];
+  t2 = q[0] - 4.0 * q[1] + 3.0 * q[2];
+  b[0] = 13.0 / 12.0 * t1 * t1 + 0.25 * t2 * t2;
+  {
+    const double e1[5] = {1, -2, 1, 0, 0}, e2[5] = {1, -4, 3, 0, 0};
+    for (int j = 0; j < 5; ++j) db[0][j] = 13.0 / 6.0 * t1 * e1[j] + 0.5 * t2 * e2[j];
+  }
+  t1 = q[1] - 2.0 * q[2] + q[3];
+  t2 = q[1] - q[3];
+  b[1] = 13.0 / 12.0 * t1 * t1 + 0.25 * t2 * t2;
+  {
+    const double e1[5] = {0, 1, -2, 1, 0}, e2[5] = {0, 1, 0, -1, 0};
+    for (int j = 0; j < 5; ++j) db[1][j] = 13.0 / 6.0 * t1 * e1[j] + 0.5 * t2 * e2[j];
+  }
+  t1 = q[2] - 2.0 * q[3] + q[4];
+  t2 = 3.0 * q[2] - 4.0 * q[3] + q[4];
+  b[2] = 13.0 / 12.0 * t1 * t1 + 0.25 * t2 * t2;
+  {
+    const double e1[5] = {0, 0, 1, -2, 1}, e2[5] = {0, 0, 3, -4, 1};
+    for (int j = 0; j < 5; ++j) db[2][j] = 13.0 / 6.0 * t1 * e1[j] + 0.5 * t2 * e2[j];
+  }
+  for (int k = 0; k < 3; ++k) {
+    a[k] = d[k] / ((eps + b[k]) * (eps + b[k]));
+    S += a[k];
+    v[k] = 0.0;
+    for (int j = 0; j < 5; ++j) v[k] += dv[k][j] * q[j];
+  }
+  for (int k = 0; k < 3; ++k) I += a[k] / S * v[k];
+  for (int j = 0; j < 5; ++j) {
+    double gj = 0.0;
+    for (int k = 0; k < 3; ++k) {
+      gj += a[k] / S * dv[k][j];
+      gj += (v[k] - I) / S * (-2.0 * a[k] / (eps + b[k])) * db[k][j];
+    }
+    grad[j] = gj;
+  }
+  return I;
+}
+
+double orc_weno5_gradient(const double q[5], double eps, double grad[5]) {
+  return weno5_grad(q, eps, grad);
+}
+
+/* Transpose of orc_lmars for a dry gas: given Fbar (nvar), accumulate XLbar, XRbar. */
+static void lmars_adjoint_dry(const orc_grid *g, const double *XL, const double *XR, int dir,
+                              double pref, const double *Fbar, double *XLb, double *XRb) {
+  const int im0 = im0_of(g), nm = nmom_of(g), nv = orc_nvar(g), mn = mom_slot(g, dir);
+  const double gam = g->gamma_d, gm1 = g->gamma_d - 1.0;
+  /* forward recomputation */
+  double pL = pref + XL[nv - 1], pR = pref + XR[nv - 1];
+  double cL = sqrt(gam * pL / XL[0]), cR = sqrt(gam * pR / XR[0]);
+  double rhoc = 0.5 * (XL[0] + XR[0]) * 0.5 * (cL + cR);
+  double uL = XL[mn], uR = XR[mn];
+  double us = 0.5 * (uL + uR) - (XR[nv - 1] - XL[nv - 1]) / (2.0 * rhoc);
+  const int left = us > 0.0;
+  const double *XS = left ? XL : XR;
+  double *XSb = left ? XLb : XRb;
+  double pS = left ? pL : pR, rhoS = XS[0], mf = us * rhoS, K = 0.0;
+  for (int m = 0; m < nm; ++m) K += 0.5 * rhoS * XS[im0 + m] * XS[im0 + m];
+  double rhoe = pS / gm1 + K;
+  /* reverse */
+  double mfb = Fbar[0];
+  for (int m = 0; m < nm; ++m) mfb += Fbar[im0 + m] * XS[im0 + m];
+  double psb = Fbar[mn];
+  double usb = mfb * rhoS + Fbar[nv - 1] * (rhoe + pS);
+  double rhoeb = Fbar[nv - 1] * us;
+  double pSb = Fbar[nv - 1] * us + rhoeb / gm1;
+  double Kb = rhoeb;
+  double u2 = 0.0;
+  for (int m = 0; m < nm; ++m) u2 += XS[im0 + m] * XS[im0 + m];
+  XSb[0] += mfb * us + Kb * 0.5 * u2;
+  for (int m = 0; m < nm; ++m) XSb[im0 + m] += Fbar[im0 + m] * mf + Kb * rhoS * XS[im0 + m];
+  XSb[nv - 1] += pSb;
+  double rhocb = 0.0;
+  /* us = (uL + uR)/2 - (p'R - p'L)/(2 rho c) */
+  XLb[mn] += 0.5 * usb;
+  XRb[mn] += 0.5 * usb;
+  XRb[nv - 1] += -usb / (2.0 * rhoc);
+  XLb[nv - 1] += usb / (2.0 * rhoc);
+  rhocb += usb * (XR[nv - 1] - XL[nv - 1]) / (2.0 * rhoc * rhoc);
+  /* ps = (p'L + p'R)/2 - rho c (uR - uL)/2 */
+  XLb[nv - 1] += 0.5 * psb;
+  XRb[nv - 1] += 0.5 * psb;
+  rhocb += -0.5 * (uR - uL) * psb;
+  XRb[mn] += -0.5 * rhoc * psb;
+  XLb[mn] += 0.5 * rhoc * psb;
+  /* rho c = (rhoL + rhoR)/2 (cL + cR)/2 */
+  XLb[0] += 0.25 * (cL + cR) * rhocb;
+  XRb[0] += 0.25 * (cL + cR) * rhocb;
+  double cLb = 0.25 * (XL[0] + XR[0]) * rhocb, cRb = cLb;
+  /* c = sqrt(gamma p / rho) */
+  XLb[nv - 1] += cLb * cL / (2.0 * pL);
+  XLb[0] += -cLb * cL / (2.0 * XL[0]);
+  XRb[nv - 1] += cRb * cR / (2.0 * pR);
+  XRb[0] += -cRb * cR / (2.0 * XR[0]);
+}
+
+int orc_rhs_adjoint(const orc_grid *g, const double *Y, const double *mu, double *Ybar) {
+  const int nx = g->nx, ny = g->ny, nz = g->nz, nv = orc_nvar(g), im0 = im0_of(g);
+  const int nm = nmom_of(g), three_d = ny > 1;
+  if (g->nvap > 0 || g->nu > 0.0) return -3; /* dry, inviscid only */
+  if (nx < 1 || ny < 1 || nz < 3) return -1;
+  ext_dims e = {nx + 6, three_d ? ny + 6 : 1, nz + 6, 3, three_d ? 3 : 0, 3};
+  const long next = (long)e.nxe * e.nye * e.nze;
+  const long ncell = (long)nx * ny * nz;
+  double *X = calloc((size_t)(nv * next), sizeof(double));
+  double *Xb = calloc((size_t)(nv * next), sizeof(double));
+  double *Fbz = calloc((size_t)nx * ny * (nz + 1), sizeof(double));
+  if (!X || !Xb || !Fbz) {
+    free(X); free(Xb); free(Fbz);
+    return -2;
+  }
+  double Yc[64], Xc[64];
+  /* forward: primitives and ghosts, as in orc_rhs */
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        long c = ((long)k * ny + j) * nx + i;
+        for (int v = 0; v < nv; ++v) Yc[v] = Y[v * ncell + c];
+        orc_cons_to_prim(g, Yc, Xc, NULL, NULL);
+        Xc[nv - 1] -= pbar_cell(g, k);
+        long x = ext_index(&e, k, j, i);
+        for (int v = 0; v < nv; ++v) X[v * next + x] = Xc[v];
+      }
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j < ny; ++j)
+      for (int gi = -3; gi < nx + 3; ++gi) {
+        if (gi >= 0 && gi < nx) continue;
+        int flip, si = wrap_or_mirror(gi, nx, g->bc[0], g->bc[1], &flip);
+        long dst = ext_index(&e, k, j, gi), src = ext_index(&e, k, j, si);
+        for (int v = 0; v < nv; ++v) X[v * next + dst] = X[v * next + src];
+        if (flip) X[(long)mom_slot(g, 0) * next + dst] *= -1.0;
+      }
+  if (three_d)
+    for (int k = 0; k < nz; ++k)
+      for (int gj = -3; gj < ny + 3; ++gj)
+        for (int i = 0; i < nx; ++i) {
+          if (gj >= 0 && gj < ny) continue;
+          int flip, sj = wrap_or_mirror(gj, ny, g->bc[2], g->bc[3], &flip);
+          long dst = ext_index(&e, k, gj, i), src = ext_index(&e, k, sj, i);
+          for (int v = 0; v < nv; ++v) X[v * next + dst] = X[v * next + src];
+          if (flip) X[(long)mom_slot(g, 1) * next + dst] *= -1.0;
+        }
+  for (int gk = -3; gk < nz + 3; ++gk)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        if (gk >= 0 && gk < nz) continue;
+        int flip, sk = wrap_or_mirror(gk, nz, g->bc[4], g->bc[5], &flip);
+        long dst = ext_index(&e, gk, j, i), src = ext_index(&e, sk, j, i);
+        for (int v = 0; v < nv; ++v) X[v * next + dst] = X[v * next + src];
+        if (flip) X[(long)mom_slot(g, 2) * next + dst] *= -1.0;
+      }
+  for (long v = 0; v < nv * ncell; ++v) Ybar[v] = 0.0;
+
+  /* reverse of the gravity sources: -(rho - rho_bar) g on rho w, -g (F_rho,b + F_rho,t)/2
+   * on rho e */
+  const int mw = mom_slot(g, 2);
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        long c = ((long)k * ny + j) * nx + i;
+        for (int s = 0; s < im0; ++s) Ybar[(long)s * ncell + c] += -g->grav * mu[(long)mw * ncell + c];
+        double me = mu[(long)(nv - 1) * ncell + c];
+        Fbz[((long)k * ny + j) * nx + i] += -0.5 * g->grav * me;
+        Fbz[((long)(k + 1) * ny + j) * nx + i] += -0.5 * g->grav * me;
+      }
+
+  /* reverse of the flux divergence, LMARS and WENO5 per face */
+  for (int d = 0; d < 3; ++d) {
+    if (d == 1 && !three_d) continue;
+    const int fx = (d == 0), fy = (d == 1), fz = (d == 2);
+    const int nfx = nx + fx, nfy = ny + fy, nfz = nz + fz;
+    const double h = d == 0 ? g->dx : (d == 1 ? g->dy : g->dz);
+    for (int k = 0; k < nfz; ++k)
+      for (int j = 0; j < nfy; ++j)
+        for (int i = 0; i < nfx; ++i) {
+          double XL[64], XR[64], Fb[64], XLb[64], XRb[64], colq[64][6];
+          /* Fbar = (mu_right - mu_left) / h over the interior cells next to the face */
+          for (int v = 0; v < nv; ++v) Fb[v] = 0.0;
+          const int il = i - fx, jl = j - fy, kl = k - fz;
+          if (il >= 0 && jl >= 0 && kl >= 0) {
+            long c = ((long)kl * ny + jl) * nx + il;
+            for (int v = 0; v < nv; ++v) Fb[v] -= mu[v * ncell + c] / h;
+          }
+          if (i < nx && j < ny && k < nz) {
+            long c = ((long)k * ny + j) * nx + i;
+            for (int v = 0; v < nv; ++v) Fb[v] += mu[v * ncell + c] / h;
+          }
+          if (fz) {
+            double fr = Fbz[((long)k * ny + j) * nx + i];
+            for (int s = 0; s < im0; ++s) Fb[s] += fr;
+          }
+          /* forward face states */
+          for (int v = 0; v < nv; ++v) {
+            double st[5];
+            for (int s = -3; s <= 2; ++s)
+              colq[v][s + 3] = X[v * next + ext_index(&e, k + s * fz, j + s * fy, i + s * fx)];
+            for (int s = 0; s < 5; ++s) st[s] = colq[v][s];
+            XL[v] = orc_weno5(st, g->weno_eps);
+            for (int s = 0; s < 5; ++s) st[s] = colq[v][5 - s];
+            XR[v] = orc_weno5(st, g->weno_eps);
+            XLb[v] = XRb[v] = 0.0;
+          }
+          double pref = fz ? g->p_bar_face[k] : pbar_cell(g, k);
+          lmars_adjoint_dry(g, XL, XR, d, pref, Fb, XLb, XRb);
+          /* WENO5 transposes onto the stencil cells s = -3..2 */
+          for (int v = 0; v < nv; ++v) {
+            double st[5], gr[5];
+            for (int s = 0; s < 5; ++s) st[s] = colq[v][s];
+            weno5_grad(st, g->weno_eps, gr);
+            for (int s = 0; s < 5; ++s)
+              Xb[v * next + ext_index(&e, k + (s - 3) * fz, j + (s - 3) * fy, i + (s - 3) * fx)] +=
+                  XLb[v] * gr[s];
+            for (int s = 0; s < 5; ++s) st[s] = colq[v][5 - s];
+            weno5_grad(st, g->weno_eps, gr);
+            for (int s = 0; s < 5; ++s)
+              Xb[v * next + ext_index(&e, k + (2 - s) * fz, j + (2 - s) * fy, i + (2 - s) * fx)] +=
+                  XRb[v] * gr[s];
+          }
+        }
+  }
+
+  /* reverse of the ghost fill: fold ghost adjoints onto their source cells */
+  for (int gk = -3; gk < nz + 3; ++gk)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        if (gk >= 0 && gk < nz) continue;
+        int flip, sk = wrap_or_mirror(gk, nz, g->bc[4], g->bc[5], &flip);
+        long dst = ext_index(&e, gk, j, i), src = ext_index(&e, sk, j, i);
+        for (int v = 0; v < nv; ++v) {
+          double b = Xb[v * next + dst];
+          if (flip && v == mom_slot(g, 2)) b = -b;
+          Xb[v * next + src] += b;
+        }
+      }
+  if (three_d)
+    for (int k = 0; k < nz; ++k)
+      for (int gj = -3; gj < ny + 3; ++gj)
+        for (int i = 0; i < nx; ++i) {
+          if (gj >= 0 && gj < ny) continue;
+          int flip, sj = wrap_or_mirror(gj, ny, g->bc[2], g->bc[3], &flip);
+          long dst = ext_index(&e, k, gj, i), src = ext_index(&e, k, sj, i);
+          for (int v = 0; v < nv; ++v) {
+            double b = Xb[v * next + dst];
+            if (flip && v == mom_slot(g, 1)) b = -b;
+            Xb[v * next + src] += b;
+          }
+        }
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j < ny; ++j)
+      for (int gi = -3; gi < nx + 3; ++gi) {
+        if (gi >= 0 && gi < nx) continue;
+        int flip, si = wrap_or_mirror(gi, nx, g->bc[0], g->bc[1], &flip);
+        long dst = ext_index(&e, k, j, gi), src = ext_index(&e, k, j, si);
+        for (int v = 0; v < nv; ++v) {
+          double b = Xb[v * next + dst];
+          if (flip && v == mom_slot(g, 0)) b = -b;
+          Xb[v * next + src] += b;
+        }
+      }
+
+  /* reverse of the primitive map (App. B, dry): rho = Y0, u_c = m_c / rho,
+   * p' = (gamma_d - 1)(rho e - |m|^2 / (2 rho)) - pbar_k */
+  const double gm1 = g->gamma_d - 1.0;
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        long c = ((long)k * ny + j) * nx + i;
+        long x = ext_index(&e, k, j, i);
+        double rho = Y[c], u2 = 0.0;
+        double pb = Xb[(long)(nv - 1) * next + x];
+        double r0 = Xb[x];
+        for (int m = 0; m < nm; ++m) {
+          double u = Y[(long)(im0 + m) * ncell + c] / rho;
+          double ub = Xb[(long)(im0 + m) * next + x];
+          r0 += -ub * u / rho;
+          u2 += u * u;
+          Ybar[(long)(im0 + m) * ncell + c] += ub / rho - pb * gm1 * u;
+        }
+        r0 += pb * gm1 * 0.5 * u2;
+        Ybar[c] += r0;
+        Ybar[(long)(nv - 1) * ncell + c] += pb * gm1;
+      }
+  free(X);
+  free(Xb);
+  free(Fbz);
+  return 0;
+}
+
+/* Adjoint of one SSP-RK3 step with time step dt (Sec. 4.3 in reverse): given lam_out =
+ * dJ/dY^{n+1}, returns lam_in = dJ/dY^n. The intermediate stages are recomputed from Yn. */
+int orc_step_adjoint(const orc_grid *g, const double *Yn, double dt, const double *lam_out,
+                     double *lam_in) {
+  const int nv = orc_nvar(g);
+  const long n = (long)nv * g->nx * g->ny * g->nz;
+  double *Y1 = malloc(sizeof(double) * (size_t)n), *Y2 = malloc(sizeof(double) * (size_t)n);
+  double *mu = malloc(sizeof(double) * (size_t)n), *Yb = malloc(sizeof(double) * (size_t)n);
+  double *l2 = malloc(sizeof(double) * (size_t)n), *l1 = malloc(sizeof(double) * (size_t)n);
+  int rc = -2;
+  if (!Y1 || !Y2 || !mu || !Yb || !l2 || !l1) goto done;
+  if ((rc = orc_stage(g, 0, Yn, Yn, dt, Y1)) < 0) goto done;
+  if ((rc = orc_stage(g, 1, Yn, Y1, dt, Y2)) < 0) goto done;
+  /* stage 2: Y3 = Yn/3 + 2/3 (Y2 + dt L(Y2)) */
+  for (long c = 0; c < n; ++c) mu[c] = 2.0 / 3.0 * dt * lam_out[c];
+  if ((rc = orc_rhs_adjoint(g, Y2, mu, Yb))) goto done;
+  for (long c = 0; c < n; ++c) {
+    l2[c] = 2.0 / 3.0 * lam_out[c] + Yb[c];
+    lam_in[c] = lam_out[c] / 3.0;
+  }
+  /* stage 1: Y2 = 3/4 Yn + 1/4 (Y1 + dt L(Y1)) */
+  for (long c = 0; c < n; ++c) mu[c] = 0.25 * dt * l2[c];
+  if ((rc = orc_rhs_adjoint(g, Y1, mu, Yb))) goto done;
+  for (long c = 0; c < n; ++c) {
+    l1[c] = 0.25 * l2[c] + Yb[c];
+    lam_in[c] += 0.75 * l2[c];
+  }
+  /* stage 0: Y1 = Yn + dt L(Yn) */
+  for (long c = 0; c < n; ++c) mu[c] = dt * l1[c];
+  if ((rc = orc_rhs_adjoint(g, Yn, mu, Yb))) goto done;
+  for (long c = 0; c < n; ++c) lam_in[c] += l1[c] + Yb[c];
+  rc = 0;
+done:
+  free(Y1); free(Y2); free(mu); free(Yb); free(l2); free(l1);
+  return rc;
+}

@@ -96,6 +96,14 @@ double orc_dt_cfl(const orc_grid *g, const double *Y, double cfl);
  * (rho e + rho g z) times the cell volume. */
 void orc_budget(const orc_grid *g, const double *Y, double *out);
 
+/* ---- discrete adjoint (dry, inviscid): transposes of the routines above ---- */
+double orc_weno5_gradient(const double q[5], double eps, double grad[5]);
+/* Ybar = (dL/dY)^T mu at state Y (returns -3 for moist or viscous grids). */
+int orc_rhs_adjoint(const orc_grid *g, const double *Y, const double *mu, double *Ybar);
+/* lam_in = (dY^{n+1}/dY^n)^T lam_out for one step of time step dt from Yn. */
+int orc_step_adjoint(const orc_grid *g, const double *Yn, double dt, const double *lam_out,
+                     double *lam_in);
+
 #ifdef __cplusplus
 }
 #endif
