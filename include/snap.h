@@ -149,8 +149,25 @@ int snap_compute_dt(snap_ctx *ctx, int domain, double *dt);
 /* Apply the App. D saturation adjustment to every cell of one domain's current state. */
 int snap_saturation_adjust(snap_ctx *ctx, int domain);
 
-/* Discrete adjoint of snap_step (reverse of the stages with recomputation from checkpoints).
- * Not built in this library version: returns SNAP_ENOTSUP. */
+/* Forward run recorded for the adjoint: advances the (single, dry, inviscid) domain by
+ * nsteps steps like snap_step, keeping a checkpoint of the state every ckpt_every steps, the
+ * final state and the time step of every step. Allocates the checkpoints
+ * (nsteps/ckpt_every + 2 state copies), one segment of ckpt_every states, four adjoint
+ * vectors and the per-face work arrays of the adjoint. SNAP_ENOTSUP for moist, viscous or
+ * multi-domain contexts. */
+int snap_record(snap_ctx *ctx, int nsteps, int ckpt_every, double dt_fixed);
+
+/* Discrete adjoint of the recorded run: lambda_init = (dY_N / dY_0)^T lambda_final, with
+ * Y_0 the state at the start of the last snap_record and Y_N the state at its end; nsteps
+ * must equal the recorded step count. The transpose of each stage (SSP-RK3 combine of Sec.
+ * 4.3, flux divergence and gravity source, LMARS of Sec. 4.1, WENO5 of Sec. 4.2, primitive
+ * map of App. B) is applied in reverse order, segment by segment, with the forward states of
+ * a segment recomputed from its checkpoint. The recorded time steps are constants; the
+ * upwind side of LMARS is held, except at u* = 0 where the mean of both one-sided derivatives
+ * is used. Both vectors have the state layout (total energy; the reference offset of the
+ * stored energy has unit derivative), dtype SNAP_F32/F64, host or device memory. The context
+ * state is restored to Y_N afterwards. SNAP_ENOTSUP for moist, viscous or multi-domain
+ * contexts. */
 int snap_step_adjoint(snap_ctx *ctx, int nsteps, const void *lambda_final, void *lambda_init,
                       int dtype, void *stream);
 
@@ -162,6 +179,22 @@ int snap_set_stream(snap_ctx *ctx, void *stream);
 /* 1 (default): snap_step replays one captured CUDA graph per step; 0: plain launches. */
 int snap_use_graph(snap_ctx *ctx, int enable);
 
+/* Select one of the tile shapes built for the context's layout (0 is the default; count in
+ * snap_info.n_tile_variants). Domains are re-tiled; results do not depend on the shape. */
+int snap_set_tile_variant(snap_ctx *ctx, int variant);
+
+/* 1: each step is one persistent cooperative launch whose CTAs (all co-resident) walk the tile
+ * queue of every domain and meet at a grid barrier between the three stages; every barrier
+ * wait is bounded (about 2 s) and reports SNAP_ETIMEOUT instead of hanging. 0 (default):
+ * three launches per step. */
+int snap_use_persistent(snap_ctx *ctx, int enable);
+
+/* Autotuner: times `steps` steps of every tile shape in both launch modes on the current
+ * state (which is restored afterwards) and keeps the fastest. best_ms (may be NULL) receives
+ * its time per step, choice (may be NULL) variant * 2 + persistent. Allocates one temporary
+ * copy of the state. */
+int snap_autotune(snap_ctx *ctx, int steps, double *best_ms, int *choice);
+
 /* Sizes the context was built with. */
 typedef struct snap_info {
   int n_domains;
@@ -171,6 +204,10 @@ typedef struct snap_info {
   int tile[3];                /* cells per tile in x, y, z */
   int tiles_total;            /* tiles over all domains */
   int kernel_launches_per_step;
+  int tile_variant;           /* active tile shape (see snap_set_tile_variant) */
+  int n_tile_variants;
+  int persistent;             /* 1: one cooperative launch per step */
+  int persistent_grid;        /* CTAs of that launch (all co-resident) */
 } snap_info;
 int snap_get_info(const snap_ctx *ctx, snap_info *info);
 

@@ -729,25 +729,31 @@ static void lmars_adjoint_dry(const orc_grid *g, const double *XL, const double 
   double rhoc = 0.5 * (XL[0] + XR[0]) * 0.5 * (cL + cR);
   double uL = XL[mn], uR = XR[mn];
   double us = 0.5 * (uL + uR) - (XR[nv - 1] - XL[nv - 1]) / (2.0 * rhoc);
-  const int left = us > 0.0;
-  const double *XS = left ? XL : XR;
-  double *XSb = left ? XLb : XRb;
-  double pS = left ? pL : pR, rhoS = XS[0], mf = us * rhoS, K = 0.0;
-  for (int m = 0; m < nm; ++m) K += 0.5 * rhoS * XS[im0 + m] * XS[im0 + m];
-  double rhoe = pS / gm1 + K;
-  /* reverse */
-  double mfb = Fbar[0];
-  for (int m = 0; m < nm; ++m) mfb += Fbar[im0 + m] * XS[im0 + m];
-  double psb = Fbar[mn];
-  double usb = mfb * rhoS + Fbar[nv - 1] * (rhoe + pS);
-  double rhoeb = Fbar[nv - 1] * us;
-  double pSb = Fbar[nv - 1] * us + rhoeb / gm1;
-  double Kb = rhoeb;
-  double u2 = 0.0;
-  for (int m = 0; m < nm; ++m) u2 += XS[im0 + m] * XS[im0 + m];
-  XSb[0] += mfb * us + Kb * 0.5 * u2;
-  for (int m = 0; m < nm; ++m) XSb[im0 + m] += Fbar[im0 + m] * mf + Kb * rhoS * XS[im0 + m];
-  XSb[nv - 1] += pSb;
+  /* reverse of the upwind part; at u* = 0 the flux has a kink between the two sides and
+   * the average of both one-sided derivatives is taken (what a central difference sees) */
+  double usb = 0.0;
+  const double psb = Fbar[mn];
+  for (int side = 0; side < 2; ++side) {
+    const int use_left = side == 0;
+    double wgt = us > 0.0 ? (use_left ? 1.0 : 0.0) : (us < 0.0 ? (use_left ? 0.0 : 1.0) : 0.5);
+    if (wgt == 0.0) continue;
+    const double *XS = use_left ? XL : XR;
+    double *XSb = use_left ? XLb : XRb;
+    double pS = use_left ? pL : pR, rhoS = XS[0], mf = us * rhoS, K = 0.0, u2 = 0.0;
+    for (int m = 0; m < nm; ++m) u2 += XS[im0 + m] * XS[im0 + m];
+    K = 0.5 * rhoS * u2;
+    double rhoe = pS / gm1 + K;
+    double mfb = Fbar[0];
+    for (int m = 0; m < nm; ++m) mfb += Fbar[im0 + m] * XS[im0 + m];
+    usb += wgt * (mfb * rhoS + Fbar[nv - 1] * (rhoe + pS));
+    double rhoeb = Fbar[nv - 1] * us;
+    double pSb = Fbar[nv - 1] * us + rhoeb / gm1;
+    double Kb = rhoeb;
+    XSb[0] += wgt * (mfb * us + Kb * 0.5 * u2);
+    for (int m = 0; m < nm; ++m)
+      XSb[im0 + m] += wgt * (Fbar[im0 + m] * mf + Kb * rhoS * XS[im0 + m]);
+    XSb[nv - 1] += wgt * pSb;
+  }
   double rhocb = 0.0;
   /* us = (uL + uR)/2 - (p'R - p'L)/(2 rho c) */
   XLb[mn] += 0.5 * usb;

@@ -1,0 +1,53 @@
+"""torch.autograd binding of the library's discrete adjoint (snap_record / snap_step_adjoint).
+
+SnapSteps.apply(Y0, context, nsteps, ckpt_every, dt_fixed) advances a conserved state by
+nsteps steps in the CUDA library and returns Y_N; its backward is the library's hand-written
+adjoint of those steps (checkpointed every ckpt_every steps, recomputed in between). The
+forward and the adjoint both run in the library's kernels; torch only holds the tensors.
+Dry, inviscid, single-domain contexts (the library returns SNAP_ENOTSUP otherwise)."""
+import torch
+
+
+class SnapSteps(torch.autograd.Function):
+    @staticmethod
+    def forward(fctx, Y0, context, nsteps, ckpt_every=20, dt_fixed=0.0):
+        if not Y0.is_cuda:
+            raise ValueError("SnapSteps needs a CUDA tensor")
+        context.set_state(Y0.detach().contiguous())
+        context.record(nsteps, ckpt_every, dt_fixed)
+        YN = torch.empty_like(Y0)
+        context.get_state(out=YN)
+        fctx.context = context
+        fctx.nsteps = nsteps
+        return YN
+
+    @staticmethod
+    def backward(fctx, gYN):
+        lam0 = fctx.context.step_adjoint(fctx.nsteps, gYN.contiguous())
+        return lam0, None, None, None, None
+
+
+def dry_state_from_theta(theta, p_cell, R_d=287.0, gamma_d=1.4, p0=1e5, velocity=None):
+    """Conserved state of a dry gas with potential temperature theta[k, j, i] on the reference
+    pressure p_cell[k] (the initial-state map of the warm-bubble workloads):
+    rho = p / (R_d theta (p/p0)^kappa), rho e = p / (gamma_d - 1) + |m|^2 / (2 rho), with
+    momenta rho u from an optional velocity[comp, k, j, i] (default: at rest)."""
+    kappa = (gamma_d - 1.0) / gamma_d
+    p = p_cell.reshape(-1, 1, 1).to(theta)
+    rho = p / (R_d * theta * (p / p0) ** kappa)
+    nmom = 3 if theta.shape[1] > 1 else 2
+    if velocity is None:
+        mom = [torch.zeros_like(rho)] * nmom
+        ke = torch.zeros_like(rho)
+    else:
+        mom = [rho * velocity[c] for c in range(nmom)]
+        ke = 0.5 * rho * (velocity ** 2).sum(dim=0)
+    rhoe = p / (gamma_d - 1.0) + ke
+    return torch.stack([rho] + mom + [rhoe])
+
+
+def kinetic_energy(Y, cell_volume):
+    """Domain kinetic energy sum |m|^2 / (2 rho) dV of a dry state."""
+    rho = Y[0]
+    m2 = (Y[1:-1] ** 2).sum(dim=0)
+    return 0.5 * (m2 / rho).sum() * cell_volume

@@ -25,8 +25,10 @@ F64, F32 = 0, 1
 # every function declared in include/snap.h
 EXPORTS = ["snap_init_grid", "snap_set_state", "snap_get_state", "snap_step", "snap_step_async",
            "snap_stage", "snap_check", "snap_reset_flags", "snap_budget_compute",
-           "snap_compute_dt", "snap_saturation_adjust", "snap_step_adjoint", "snap_set_stream",
-           "snap_use_graph", "snap_get_info", "snap_buffer_pointer", "snap_budget_noalloc",
+           "snap_compute_dt", "snap_saturation_adjust", "snap_record", "snap_step_adjoint",
+           "snap_set_stream",
+           "snap_use_graph", "snap_set_tile_variant", "snap_use_persistent", "snap_autotune",
+           "snap_get_info", "snap_buffer_pointer", "snap_budget_noalloc",
            "snap_free", "snap_last_error", "snap_status_string"]
 
 
@@ -57,7 +59,9 @@ class Budget(C.Structure):
 class Info(C.Structure):
     _fields_ = [("n_domains", C.c_int), ("nfields", C.c_int), ("ncells_total", C.c_longlong),
                 ("state_bytes", C.c_longlong), ("tile", C.c_int * 3), ("tiles_total", C.c_int),
-                ("kernel_launches_per_step", C.c_int)]
+                ("kernel_launches_per_step", C.c_int), ("tile_variant", C.c_int),
+                ("n_tile_variants", C.c_int), ("persistent", C.c_int),
+                ("persistent_grid", C.c_int)]
 
 
 class SnapError(RuntimeError):
@@ -91,9 +95,13 @@ def load(path: Optional[str] = None) -> C.CDLL:
     lib.snap_compute_dt.argtypes = [P, C.c_int, C.POINTER(C.c_double)]
     lib.snap_saturation_adjust.argtypes = [P, C.c_int]
     lib.snap_step_adjoint.argtypes = [P, C.c_int, P, P, C.c_int, P]
+    lib.snap_record.argtypes = [P, C.c_int, C.c_int, C.c_double]
     lib.snap_set_stream.argtypes = [P, P]
     lib.snap_use_graph.argtypes = [P, C.c_int]
     lib.snap_get_info.argtypes = [P, C.POINTER(Info)]
+    lib.snap_set_tile_variant.argtypes = [P, C.c_int]
+    lib.snap_use_persistent.argtypes = [P, C.c_int]
+    lib.snap_autotune.argtypes = [P, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int)]
     lib.snap_buffer_pointer.argtypes = [P, C.c_int, C.c_int, C.POINTER(P)]
     lib.snap_budget_noalloc.argtypes = [P, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                                         C.c_int, C.c_double, C.c_double, C.c_double,
@@ -222,6 +230,23 @@ class Context:
     def saturation_adjust(self, domain=0):
         return self._check(self.lib.snap_saturation_adjust(self._ptr, domain))
 
+    def record(self, nsteps, ckpt_every=20, dt_fixed=0.0):
+        """Forward run kept for the adjoint (see snap_record)."""
+        return self._check(self.lib.snap_record(self._ptr, nsteps, ckpt_every, dt_fixed))
+
+    def step_adjoint(self, nsteps, lam_final, out=None):
+        """lambda_init = (dY_N/dY_0)^T lambda_final for the last recorded run; lam_final is a
+        numpy array or torch tensor in the state layout."""
+        if out is None:
+            out = np.empty_like(lam_final) if isinstance(lam_final, np.ndarray) else \
+                lam_final.new_empty(lam_final.shape)
+        pin, dt_in, _ = _buffer(lam_final)
+        pout, dt_out, _ = _buffer(out)
+        if dt_in != dt_out:
+            raise TypeError("lam_final and out must have the same dtype")
+        self._check(self.lib.snap_step_adjoint(self._ptr, nsteps, pin, pout, dt_in, None))
+        return out
+
     def set_stream(self, stream):
         """stream: a torch.cuda.Stream, a raw cudaStream_t integer, or None."""
         h = getattr(stream, "cuda_stream", stream)
@@ -235,7 +260,22 @@ class Context:
         self._check(self.lib.snap_get_info(self._ptr, C.byref(i)))
         return {"n_domains": i.n_domains, "nfields": i.nfields, "ncells_total": i.ncells_total,
                 "state_bytes": i.state_bytes, "tile": tuple(i.tile), "tiles_total": i.tiles_total,
-                "kernel_launches_per_step": i.kernel_launches_per_step}
+                "kernel_launches_per_step": i.kernel_launches_per_step,
+                "tile_variant": i.tile_variant, "n_tile_variants": i.n_tile_variants,
+                "persistent": i.persistent, "persistent_grid": i.persistent_grid}
+
+    def set_tile_variant(self, variant):
+        return self._check(self.lib.snap_set_tile_variant(self._ptr, variant))
+
+    def use_persistent(self, enable=True):
+        return self._check(self.lib.snap_use_persistent(self._ptr, int(enable)))
+
+    def autotune(self, steps=5):
+        ms = C.c_double(0.0)
+        choice = C.c_int(0)
+        self._check(self.lib.snap_autotune(self._ptr, steps, C.byref(ms), C.byref(choice)))
+        return {"ms_per_step": ms.value, "variant": choice.value // 2,
+                "persistent": choice.value % 2}
 
     def buffer_pointer(self, domain=0, slot=0):
         p = C.c_void_p()

@@ -19,6 +19,13 @@ bool find_kernels_dry3d(int f32, int visc, KernelSet *out);
 bool find_kernels_moist2d(int f32, int visc, KernelSet *out);
 bool find_kernels_moist3d(int f32, int visc, KernelSet *out);
 
+bool find_adjoint_kernels_dry2d(int f32, AdjKernels *out);
+bool find_adjoint_kernels_dry3d(int f32, AdjKernels *out);
+
+bool find_adjoint_kernels(int f32, int three_d, AdjKernels *out) {
+  return three_d ? find_adjoint_kernels_dry3d(f32, out) : find_adjoint_kernels_dry2d(f32, out);
+}
+
 bool find_kernels(int f32, int nvap, int ncond, int three_d, int visc, KernelSet *out) {
   if (nvap == 0 && ncond == 0) return three_d ? find_kernels_dry3d(f32, visc, out)
                                               : find_kernels_dry2d(f32, visc, out);
@@ -40,7 +47,7 @@ __global__ void state_copy_kernel(const S *src, D *dst, int nv, long long ncell,
   const long long n = (long long)nv * ncell, e0 = (long long)(nv - 1) * ncell;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
-    if (i >= e0)
+    if (i >= e0 && e_ref)
       dst[i] = D(double(src[i]) + sign * e_ref[(i - e0) / plane]);
     else
       dst[i] = D(src[i]);
@@ -80,6 +87,20 @@ struct snap_ctx {
   std::vector<DomDev> dom;   // host mirror of doms_dev
   std::vector<int> prefix;   // tile prefix per domain
   int ntiles = 0, grid = 0;
+  int tv = 0;                // active tile variant
+  int persistent = 0;        // 1: one cooperative launch per step
+  int grid_persistent = 0;
+  GridSync *gsync = nullptr;
+  // discrete adjoint (dry, inviscid, one domain): recording and work buffers
+  int has_adj = 0;
+  AdjKernels adj{};
+  int rec_steps = 0, ckpt_every = 0;
+  std::vector<double> rec_dt;
+  void *ckpt = nullptr;       // checkpoints every ckpt_every steps, then the final state
+  void *segbuf = nullptr;     // states of one segment
+  void *lam = nullptr;        // four adjoint vectors
+  void *gface = nullptr;      // per-direction face contributions
+  size_t gface_off[3] = {0, 0, 0};
   // device memory
   void *arena = nullptr;
   DomDev *doms_dev = nullptr;
@@ -131,6 +152,11 @@ static void release(snap_ctx *ctx) {
   cudaFree(ctx->arena);
   cudaFree(ctx->doms_dev);
   cudaFree(ctx->prefix_dev);
+  cudaFree(ctx->gsync);
+  cudaFree(ctx->ckpt);
+  cudaFree(ctx->segbuf);
+  cudaFree(ctx->lam);
+  cudaFree(ctx->gface);
   cudaFree(ctx->prof_dev);
   cudaFree(ctx->proff_dev);
   cudaFree(ctx->rate_dev);
@@ -268,6 +294,7 @@ static StageArgs args_of(snap_ctx *ctx, int stage) {
   a.stage = stage;
   a.flags = ctx->flags_dev;
   a.max_sweeps = ctx->sweeps_dev;
+  a.gsync = ctx->gsync;
   a.ph = ctx->ph;
   // stop tolerance of the adjustment: at least 32 machine epsilons of the arithmetic type
   derive_cst<float>(ctx->ph, 32.0 * 1.1920928955078125e-07, a.cf);
@@ -310,7 +337,10 @@ extern "C" int snap_init_grid(snap_ctx **out, const snap_grid_desc *d, int n_dom
   }
   derive_phys(d[0], ctx->ph);
   ctx->desc.assign(d, d + n_domains);
-  cudaError_t e = ctx->ks.prepare();
+  if (ctx->nvap == 0 && !ctx->visc && n_domains == 1)
+    ctx->has_adj = find_adjoint_kernels(ctx->f32, ctx->three_d, &ctx->adj) ? 1 : 0;
+  cudaError_t e = cudaSuccess;
+  for (int v = 0; v < ctx->ks.nvariants && e == cudaSuccess; ++v) e = ctx->ks.var[v].prepare();
   if (e != cudaSuccess) {
     int rc = cuda_fail(nullptr, e, "snap_init_grid: kernel attributes");
     delete ctx;
@@ -337,9 +367,10 @@ extern "C" int snap_init_grid(snap_ctx **out, const snap_grid_desc *d, int n_dom
     D.nx = g.nx;
     D.ny = g.ny;
     D.nz = g.nz;
-    D.tx = (g.nx + ctx->ks.tile[0] - 1) / ctx->ks.tile[0];
-    D.ty = (g.ny + ctx->ks.tile[1] - 1) / ctx->ks.tile[1];
-    D.tz = (g.nz + ctx->ks.tile[2] - 1) / ctx->ks.tile[2];
+    const int *tl = ctx->ks.var[0].tile;
+    D.tx = (g.nx + tl[0] - 1) / tl[0];
+    D.ty = (g.ny + tl[1] - 1) / tl[1];
+    D.tz = (g.nz + tl[2] - 1) / tl[2];
     D.tile_begin = ctx->prefix[i];
     ctx->prefix[i + 1] = ctx->prefix[i] + D.tx * D.ty * D.tz;
     for (int s = 0; s < 6; ++s) D.bc[s] = g.bc[s];
@@ -362,6 +393,8 @@ extern "C" int snap_init_grid(snap_ctx **out, const snap_grid_desc *d, int n_dom
     if ((e = cudaMemset(ctx->arena, 0, total)) != cudaSuccess) break;
     if ((e = cudaMalloc(&ctx->doms_dev, sizeof(DomDev) * n_domains)) != cudaSuccess) break;
     if ((e = cudaMalloc(&ctx->prefix_dev, sizeof(int) * (n_domains + 1))) != cudaSuccess) break;
+    if ((e = cudaMalloc(&ctx->gsync, sizeof(GridSync))) != cudaSuccess) break;
+    if ((e = cudaMemset(ctx->gsync, 0, sizeof(GridSync))) != cudaSuccess) break;
     if ((e = cudaMalloc(&ctx->prof_dev, sizeof(double) * nprof)) != cudaSuccess) break;
     if ((e = cudaMalloc(&ctx->proff_dev, sizeof(float) * nproff)) != cudaSuccess) break;
     if ((e = cudaMalloc(&ctx->rate_dev, sizeof(unsigned long long) * n_domains)) != cudaSuccess) break;
@@ -435,7 +468,41 @@ extern "C" int snap_init_grid(snap_ctx **out, const snap_grid_desc *d, int n_dom
     delete ctx;
     return ret;
   }
+  {
+    int mrb = ctx->ks.var[0].max_resident_blocks();
+    ctx->grid_persistent = mrb < ctx->ntiles ? mrb : ctx->ntiles;
+  }
   *out = ctx;
+  return SNAP_OK;
+}
+
+// Rebuild the tile tables of every domain for tile variant v and upload them.
+static int apply_variant(snap_ctx *ctx, int v) {
+  const int *tl = ctx->ks.var[v].tile;
+  ctx->prefix[0] = 0;
+  for (int i = 0; i < ctx->ndom; ++i) {
+    DomDev &D = ctx->dom[i];
+    D.tx = (D.nx + tl[0] - 1) / tl[0];
+    D.ty = (D.ny + tl[1] - 1) / tl[1];
+    D.tz = (D.nz + tl[2] - 1) / tl[2];
+    D.tile_begin = ctx->prefix[i];
+    ctx->prefix[i + 1] = ctx->prefix[i] + D.tx * D.ty * D.tz;
+  }
+  ctx->ntiles = ctx->prefix[ctx->ndom];
+  ctx->grid = ctx->ntiles;
+  const int mrb = ctx->ks.var[v].max_resident_blocks();
+  if (mrb <= 0) return fail(ctx, SNAP_ECUDA, "occupancy query of the step kernel failed");
+  ctx->grid_persistent = mrb < ctx->ntiles ? mrb : ctx->ntiles;
+  ctx->tv = v;
+  CK(cudaMemcpyAsync(ctx->doms_dev, ctx->dom.data(), sizeof(DomDev) * ctx->ndom,
+                     cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->prefix_dev, ctx->prefix.data(), sizeof(int) * (ctx->ndom + 1),
+                     cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (ctx->graph) {
+    cudaGraphExecDestroy(ctx->graph);
+    ctx->graph = nullptr;
+  }
   return SNAP_OK;
 }
 
@@ -499,9 +566,15 @@ static int set_dt_fixed(snap_ctx *ctx, double dt_fixed) {
 }
 
 static int enqueue_stages(snap_ctx *ctx, cudaStream_t s) {
+  const TileVariant &tv = ctx->ks.var[ctx->tv];
+  if (ctx->persistent) {
+    StageArgs a = args_of(ctx, 0);
+    CK(tv.step(a, ctx->grid_persistent, s));
+    return SNAP_OK;
+  }
   for (int st = 0; st < 3; ++st) {
     StageArgs a = args_of(ctx, st);
-    CK(ctx->ks.stage(a, ctx->grid, s));
+    CK(tv.stage(a, ctx->grid, s));
   }
   return SNAP_OK;
 }
@@ -512,7 +585,7 @@ extern "C" int snap_stage(snap_ctx *ctx, int stage, double dt_fixed) {
   int rc = set_dt_fixed(ctx, dt_fixed);
   if (rc) return rc;
   StageArgs a = args_of(ctx, stage);
-  CK(ctx->ks.stage(a, ctx->grid, ctx->stream));
+  CK(ctx->ks.var[ctx->tv].stage(a, ctx->grid, ctx->stream));
   return SNAP_OK;
 }
 
@@ -593,6 +666,7 @@ extern "C" int snap_check(snap_ctx *ctx, unsigned int *flags) {
   int rc = read_status(ctx, &f, nullptr);
   if (rc) return rc;
   if (flags) *flags = f;
+  if (f & kFlagTimeout) return fail(ctx, SNAP_ETIMEOUT, "a grid barrier of the persistent step kernel timed out");
   if (f & kFlagNonFinite) return fail(ctx, SNAP_ENONFINITE, "a step produced a non-finite value or non-positive density");
   if (f & kFlagNoConv) return fail(ctx, SNAP_ENOCONV, "saturation adjustment did not converge in some cell");
   return SNAP_OK;
@@ -646,15 +720,260 @@ extern "C" int snap_saturation_adjust(snap_ctx *ctx, int domain) {
   return snap_check(ctx, nullptr);
 }
 
+static size_t state_bytes_dom0(snap_ctx *ctx) {
+  return (size_t)ctx->dom[0].ncell * ctx->nv * ctx->word;
+}
+
+extern "C" int snap_record(snap_ctx *ctx, int nsteps, int ckpt_every, double dt_fixed) {
+  if (!ctx) return fail(nullptr, SNAP_EINVAL, "snap_record: NULL context");
+  if (!ctx->has_adj)
+    return fail(ctx, SNAP_ENOTSUP, "snap_record: the adjoint is built for one dry, inviscid domain");
+  if (nsteps < 1 || ckpt_every < 1) return fail(ctx, SNAP_EINVAL, "snap_record: nsteps and ckpt_every must be >= 1");
+  const size_t sb = state_bytes_dom0(ctx);
+  const int nck = (nsteps + ckpt_every - 1) / ckpt_every + 1;
+  cudaFree(ctx->ckpt);
+  cudaFree(ctx->segbuf);
+  ctx->ckpt = ctx->segbuf = nullptr;
+  CK(cudaMalloc(&ctx->ckpt, sb * nck));
+  CK(cudaMalloc(&ctx->segbuf, sb * ckpt_every));
+  if (!ctx->lam) CK(cudaMalloc(&ctx->lam, sb * 4));
+  if (!ctx->gface) {
+    const DomDev &D = ctx->dom[0];
+    size_t off = 0;
+    for (int d = 0; d < 3; ++d) {
+      if (d == 1 && !ctx->three_d) continue;
+      long long nf = (long long)(D.nx + (d == 0)) * (D.ny + (d == 1)) * (D.nz + (d == 2));
+      ctx->gface_off[d] = off;
+      off += (size_t)nf * ctx->nv * 6 * ctx->word;
+    }
+    CK(cudaMalloc(&ctx->gface, off));
+  }
+  ctx->rec_dt.assign(nsteps, 0.0);
+  ctx->ckpt_every = ckpt_every;
+  const int keep = ctx->use_graph;
+  for (int n = 0; n < nsteps; ++n) {
+    if (n % ckpt_every == 0)
+      CK(cudaMemcpyAsync((char *)ctx->ckpt + sb * (n / ckpt_every), ctx->dom[0].buf[0], sb,
+                         cudaMemcpyDeviceToDevice, ctx->stream));
+    int rc = snap_step_async(ctx, 1, dt_fixed);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(&ctx->rec_dt[n], ctx->dt_dev, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  }
+  CK(cudaMemcpyAsync((char *)ctx->ckpt + sb * (nck - 1), ctx->dom[0].buf[0], sb,
+                     cudaMemcpyDeviceToDevice, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->use_graph = keep;
+  ctx->rec_steps = nsteps;
+  return snap_check(ctx, nullptr);
+}
+
+// Adjoint of one stage: lam_s = b lam_out + (dL/dY_s)^T (b dt lam_out), and the step's
+// initial-state adjoint lam_n according to mode (see AdjArgs).
+static int adjoint_stage(snap_ctx *ctx, int slot, const void *lo, void *ls, void *ln, double a,
+                         double b, double dt, int mode) {
+  AdjArgs A;
+  memset(&A, 0, sizeof A);
+  A.doms = ctx->doms_dev;
+  A.slot_s = slot;
+  A.lam_out = lo;
+  A.lam_s = ls;
+  A.lam_n = ln;
+  A.a = a;
+  A.b = b;
+  A.dt = dt;
+  A.mode = mode;
+  A.ph = ctx->ph;
+  StageArgs sa = args_of(ctx, 0);
+  A.cf = sa.cf;
+  A.cd = sa.cd;
+  const DomDev &D = ctx->dom[0];
+  for (int d = 0; d < 3; ++d) A.G[d] = (char *)ctx->gface + ctx->gface_off[d];
+  for (int d = 0; d < 3; ++d) {
+    if (d == 1 && !ctx->three_d) continue;
+    long long nf = (long long)(D.nx + (d == 0)) * (D.ny + (d == 1)) * (D.nz + (d == 2));
+    CK(ctx->adj.face(A, d, nf, ctx->stream));
+  }
+  CK(ctx->adj.cell(A, D.ncell, ctx->stream));
+  return SNAP_OK;
+}
+
+static int plain_stage(snap_ctx *ctx, int stage) {
+  StageArgs a = args_of(ctx, stage);
+  CK(ctx->ks.var[ctx->tv].stage(a, ctx->grid, ctx->stream));
+  return SNAP_OK;
+}
+
 extern "C" int snap_step_adjoint(snap_ctx *ctx, int nsteps, const void *lambda_final,
                                  void *lambda_init, int dtype, void *stream) {
-  (void)nsteps; (void)lambda_final; (void)lambda_init; (void)dtype; (void)stream;
-  return fail(ctx, SNAP_ENOTSUP, "snap_step_adjoint: the discrete adjoint is not built into this library version");
+  if (!ctx) return fail(nullptr, SNAP_EINVAL, "snap_step_adjoint: NULL context");
+  if (!ctx->has_adj)
+    return fail(ctx, SNAP_ENOTSUP, "snap_step_adjoint: the adjoint is built for one dry, inviscid domain");
+  if (!lambda_final || !lambda_init || (dtype != SNAP_F64 && dtype != SNAP_F32))
+    return fail(ctx, SNAP_EINVAL, "snap_step_adjoint: bad pointers or dtype");
+  if (ctx->rec_steps < 1 || nsteps != ctx->rec_steps)
+    return fail(ctx, SNAP_EINVAL, "snap_step_adjoint: nsteps must equal the steps of the last snap_record");
+  cudaStream_t user = stream ? (cudaStream_t)stream : ctx->stream;
+  CK(cudaStreamSynchronize(user));
+  const DomDev &D = ctx->dom[0];
+  const size_t sb = state_bytes_dom0(ctx);
+  const long long n = D.ncell * ctx->nv;
+  char *LA = (char *)ctx->lam, *LB = LA + sb, *LC = LB + sb, *LN = LC + sb;
+  const int in_f32 = dtype == SNAP_F32;
+  const size_t iw = in_f32 ? 4 : 8;
+  cudaPointerAttributes pa;
+  const bool dev_in = cudaPointerGetAttributes(&pa, lambda_final) == cudaSuccess &&
+                      (pa.type == cudaMemoryTypeDevice || pa.type == cudaMemoryTypeManaged);
+  cudaGetLastError();
+  const void *src = lambda_final;
+  if (!dev_in) {
+    CK(cudaMemcpyAsync(ctx->staging, lambda_final, n * iw, cudaMemcpyHostToDevice, ctx->stream));
+    src = ctx->staging;
+  }
+  // an adjoint vector has no reference offset: plain type conversion
+  CK(launch_state_copy(src, in_f32, LA, ctx->f32, ctx->nv, D.ncell, (long long)D.nx * D.ny,
+                       nullptr, 1, ctx->stream));
+  const int K = ctx->ckpt_every;
+  const int nseg = (nsteps + K - 1) / K;
+  int rc = SNAP_OK;
+  for (int seg = nseg - 1; seg >= 0 && rc == SNAP_OK; --seg) {
+    const int n0 = seg * K, n1 = (n0 + K < nsteps) ? n0 + K : nsteps;
+    CK(cudaMemcpyAsync(D.buf[0], (char *)ctx->ckpt + sb * seg, sb, cudaMemcpyDeviceToDevice, ctx->stream));
+    for (int s = n0; s < n1 && rc == SNAP_OK; ++s) {
+      CK(cudaMemcpyAsync((char *)ctx->segbuf + sb * (s - n0), D.buf[0], sb, cudaMemcpyDeviceToDevice, ctx->stream));
+      if (s < n1 - 1) {
+        if ((rc = set_dt_fixed(ctx, ctx->rec_dt[s]))) break;
+        for (int st = 0; st < 3 && rc == SNAP_OK; ++st) rc = plain_stage(ctx, st);
+      }
+    }
+    for (int s = n1 - 1; s >= n0 && rc == SNAP_OK; --s) {
+      const double dt = ctx->rec_dt[s];
+      CK(cudaMemcpyAsync(D.buf[0], (char *)ctx->segbuf + sb * (s - n0), sb, cudaMemcpyDeviceToDevice, ctx->stream));
+      if ((rc = set_dt_fixed(ctx, dt))) break;
+      if ((rc = plain_stage(ctx, 0))) break;  // B1 = Y1
+      if ((rc = plain_stage(ctx, 1))) break;  // B2 = Y2
+      // Sec. 4.3 in reverse: Y3 = Y/3 + 2/3 (Y2 + dt L(Y2)), Y2 = 3/4 Y + 1/4 (Y1 + dt L(Y1)),
+      // Y1 = Y + dt L(Y)
+      if ((rc = adjoint_stage(ctx, 2, LA, LB, LN, 1.0 / 3.0, 2.0 / 3.0, dt, 2))) break;
+      if ((rc = adjoint_stage(ctx, 1, LB, LC, LN, 0.75, 0.25, dt, 1))) break;
+      if ((rc = adjoint_stage(ctx, 0, LC, LA, LN, 0.0, 1.0, dt, 0))) break;
+    }
+  }
+  if (rc == SNAP_OK) {
+    void *dst = lambda_init;
+    cudaPointerAttributes po;
+    const bool dev_out = cudaPointerGetAttributes(&po, lambda_init) == cudaSuccess &&
+                         (po.type == cudaMemoryTypeDevice || po.type == cudaMemoryTypeManaged);
+    cudaGetLastError();
+    if (!dev_out) dst = ctx->staging;
+    CK(launch_state_copy(LA, ctx->f32, dst, in_f32, ctx->nv, D.ncell, (long long)D.nx * D.ny,
+                         nullptr, 0, ctx->stream));
+    if (!dev_out) CK(cudaMemcpyAsync(lambda_init, ctx->staging, n * iw, cudaMemcpyDeviceToHost, ctx->stream));
+  }
+  // restore the recorded final state
+  const int nck = (ctx->rec_steps + K - 1) / K + 1;
+  CK(cudaMemcpyAsync(D.buf[0], (char *)ctx->ckpt + sb * (nck - 1), sb, cudaMemcpyDeviceToDevice, ctx->stream));
+  int rc2 = set_dt_fixed(ctx, -1.0);
+  if (!rc) rc = rc2;
+  rc2 = refresh_rate(ctx, 0, ctx->stream);
+  if (!rc) rc = rc2;
+  CK(cudaStreamSynchronize(ctx->stream));
+  return rc;
 }
 
 extern "C" int snap_set_stream(snap_ctx *ctx, void *stream) {
   if (!ctx) return fail(nullptr, SNAP_EINVAL, "snap_set_stream: NULL context");
   ctx->stream = (cudaStream_t)stream;  // NULL: the legacy default stream
+  return SNAP_OK;
+}
+
+extern "C" int snap_set_tile_variant(snap_ctx *ctx, int variant) {
+  if (!ctx) return fail(nullptr, SNAP_EINVAL, "snap_set_tile_variant: NULL context");
+  if (variant < 0 || variant >= ctx->ks.nvariants)
+    return fail(ctx, SNAP_EINVAL, "snap_set_tile_variant: no such variant");
+  return apply_variant(ctx, variant);
+}
+
+extern "C" int snap_use_persistent(snap_ctx *ctx, int enable) {
+  if (!ctx) return fail(nullptr, SNAP_EINVAL, "snap_use_persistent: NULL context");
+  if (ctx->grid_persistent <= 0)
+    return fail(ctx, SNAP_ECUDA, "snap_use_persistent: no co-resident CTA for the step kernel");
+  ctx->persistent = enable ? 1 : 0;
+  if (ctx->graph) {
+    cudaGraphExecDestroy(ctx->graph);
+    ctx->graph = nullptr;
+  }
+  return SNAP_OK;
+}
+
+// Times `steps` steps of every tile variant in both launch modes on a copy of the current
+// state, restores the state, and keeps the fastest. best_ms (may be NULL) gets its time per
+// step; choice (may be NULL) gets variant * 2 + persistent.
+extern "C" int snap_autotune(snap_ctx *ctx, int steps, double *best_ms, int *choice) {
+  if (!ctx) return fail(nullptr, SNAP_EINVAL, "snap_autotune: NULL context");
+  if (steps < 1) return fail(ctx, SNAP_EINVAL, "snap_autotune: steps < 1");
+  // save every domain's state (and the CFL maxima) to restore after the trials
+  size_t total = 0;
+  for (int i = 0; i < ctx->ndom; ++i) total += (size_t)ctx->dom[i].ncell * ctx->nv * ctx->word;
+  void *save = nullptr;
+  CK(cudaMalloc(&save, total));
+  std::vector<unsigned long long> rate(ctx->ndom);
+  size_t off = 0;
+  for (int i = 0; i < ctx->ndom; ++i) {
+    size_t b = (size_t)ctx->dom[i].ncell * ctx->nv * ctx->word;
+    CK(cudaMemcpyAsync((char *)save + off, ctx->dom[i].buf[0], b, cudaMemcpyDeviceToDevice, ctx->stream));
+    off += b;
+  }
+  CK(cudaMemcpyAsync(rate.data(), ctx->rate_dev, sizeof(unsigned long long) * ctx->ndom,
+                     cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  const int keep_graph = ctx->use_graph;
+  ctx->use_graph = 0;
+  double best = 1e300;
+  int best_v = 0, best_p = 0, rc = SNAP_OK;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  for (int v = 0; v < ctx->ks.nvariants && rc == SNAP_OK; ++v) {
+    rc = apply_variant(ctx, v);
+    for (int p = 0; p < 2 && rc == SNAP_OK; ++p) {
+      if (p == 1 && ctx->grid_persistent <= 0) continue;
+      ctx->persistent = p;
+      rc = snap_step_async(ctx, 1, 0.0);  // warm-up
+      if (rc) break;
+      CK(cudaEventRecord(e0, ctx->stream));
+      rc = snap_step_async(ctx, steps, 0.0);
+      if (rc) break;
+      CK(cudaEventRecord(e1, ctx->stream));
+      CK(cudaEventSynchronize(e1));
+      float ms = 0.0f;
+      CK(cudaEventElapsedTime(&ms, e0, e1));
+      if (ms / steps < best) {
+        best = ms / steps;
+        best_v = v;
+        best_p = p;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  off = 0;
+  for (int i = 0; i < ctx->ndom; ++i) {
+    size_t b = (size_t)ctx->dom[i].ncell * ctx->nv * ctx->word;
+    CK(cudaMemcpyAsync(ctx->dom[i].buf[0], (char *)save + off, b, cudaMemcpyDeviceToDevice, ctx->stream));
+    off += b;
+  }
+  CK(cudaMemcpyAsync(ctx->rate_dev, rate.data(), sizeof(unsigned long long) * ctx->ndom,
+                     cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  cudaFree(save);
+  ctx->use_graph = keep_graph;
+  if (rc) return rc;
+  rc = apply_variant(ctx, best_v);
+  if (rc) return rc;
+  ctx->persistent = best_p;
+  if (best_ms) *best_ms = best;
+  if (choice) *choice = best_v * 2 + best_p;
+  CK(cudaMemsetAsync(ctx->flags_dev, 0, sizeof(unsigned int), ctx->stream));
   return SNAP_OK;
 }
 
@@ -670,9 +989,13 @@ extern "C" int snap_get_info(const snap_ctx *ctx, snap_info *info) {
   info->nfields = ctx->nv;
   info->ncells_total = ctx->ncells;
   info->state_bytes = ctx->state_bytes;
-  for (int i = 0; i < 3; ++i) info->tile[i] = ctx->ks.tile[i];
+  for (int i = 0; i < 3; ++i) info->tile[i] = ctx->ks.var[ctx->tv].tile[i];
   info->tiles_total = ctx->ntiles;
-  info->kernel_launches_per_step = 3;
+  info->kernel_launches_per_step = ctx->persistent ? 1 : 3;
+  info->tile_variant = ctx->tv;
+  info->n_tile_variants = ctx->ks.nvariants;
+  info->persistent = ctx->persistent;
+  info->persistent_grid = ctx->grid_persistent;
   return SNAP_OK;
 }
 

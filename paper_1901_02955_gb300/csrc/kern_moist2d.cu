@@ -1,13 +1,15 @@
-// kern_moist2d.cu -- instantiation of the stage kernels for n_vapor = 1, n_cond = 2,
-// three-dimensional = false.
+// kern_moist2d.cu -- stage kernels for one vapour with cloud and precipitation, x-z plane.
 #include "snap_stage.cuh"
 
 namespace snap {
 
 bool find_kernels_moist2d(int f32, int visc, KernelSet *out) {
   using L = Lay<1, 2, false>;
+  using A = TileT<32, 1, 14>;
+  using B = TileT<64, 1, 6>;
+  using C = TileT<16, 1, 30>;
   if (visc) return false;
-  *out = f32 ? Family<float, L, false>::set() : Family<double, L, false>::set();
+  *out = f32 ? Family<float, L>::set<false, A, B, C>() : Family<double, L>::set<false, A>();
   return true;
 }
 

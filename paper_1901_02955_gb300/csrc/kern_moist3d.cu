@@ -1,13 +1,14 @@
-// kern_moist3d.cu -- instantiation of the stage kernels for n_vapor = 2, n_cond = 2,
-// three-dimensional = true.
+// kern_moist3d.cu -- stage kernels for two vapours with cloud and precipitation, 3-D.
 #include "snap_stage.cuh"
 
 namespace snap {
 
 bool find_kernels_moist3d(int f32, int visc, KernelSet *out) {
   using L = Lay<2, 2, true>;
+  using A = TileT<8, 8, 4>;
+  using B = TileT<16, 8, 2>;
   if (visc) return false;
-  *out = f32 ? Family<float, L, false>::set() : Family<double, L, false>::set();
+  *out = f32 ? Family<float, L>::set<false, A, B>() : Family<double, L>::set<false, A>();
   return true;
 }
 

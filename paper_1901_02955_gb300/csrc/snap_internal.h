@@ -65,6 +65,12 @@ struct DomDev {
   double *dt_step;           // time step of the current step
 };
 
+// State of the grid-wide barrier of the persistent step kernel (device memory).
+struct GridSync {
+  unsigned int count;
+  unsigned int gen;
+};
+
 struct StageArgs {
   const DomDev *doms;        // device array
   const int *tile_domain;    // device array [ndom+1]: prefix of tiles per domain
@@ -73,25 +79,60 @@ struct StageArgs {
   int stage;                 // 0, 1, 2
   unsigned int *flags;       // bit 0 non-finite, bit 1 no convergence
   int *max_sweeps;
+  GridSync *gsync;           // persistent step kernel only
   Phys ph;
   CstT<float> cf;
   CstT<double> cd;
 };
 
-enum Flag : unsigned int { kFlagNonFinite = 1u, kFlagNoConv = 2u };
+enum Flag : unsigned int { kFlagNonFinite = 1u, kFlagNoConv = 2u, kFlagTimeout = 4u };
 
-// Kernel family entry points (one per instantiated configuration).
-struct KernelSet {
+// One tile shape of a kernel family.
+struct TileVariant {
   int tile[3];
   int threads;
   size_t smem_stage;
   cudaError_t (*stage)(const StageArgs &, int grid, cudaStream_t);
+  // all three stages in one cooperative launch with grid barriers in between
+  cudaError_t (*step)(const StageArgs &, int grid, cudaStream_t);
+  int (*max_resident_blocks)();  // co-resident CTAs of the step kernel on this device
+  cudaError_t (*prepare)();      // one-time attribute setup (dynamic shared memory)
+};
+
+constexpr int kMaxVariants = 4;
+
+// Kernel family entry points (one per instantiated layout and type).
+struct KernelSet {
+  int nvariants;
+  TileVariant var[kMaxVariants];
   cudaError_t (*rate)(const StageArgs &, int dom, int buf, cudaStream_t);
   cudaError_t (*budget)(const StageArgs &, int dom, int buf, double *partials, int nblocks,
                         double *out, cudaStream_t);
   cudaError_t (*satadj)(const StageArgs &, int dom, int buf, cudaStream_t);
-  cudaError_t (*prepare)();  // one-time attribute setup (dynamic shared memory)
 };
+
+// Arguments of the adjoint kernels of one stage (dry, inviscid, single domain).
+struct AdjArgs {
+  const DomDev *doms;
+  int slot_s;            // buffer slot of the stage input state
+  const void *lam_out;   // adjoint of the stage output (context type, state layout)
+  void *lam_s;           // adjoint of the stage input (written)
+  void *lam_n;           // accumulator of the adjoint of the step's initial state
+  double a, b, dt;       // stage output = a Y^n + b (Y_s + dt L(Y_s))
+  int mode;              // 2: lam_n = a lam_out; 1: lam_n += a lam_out; 0: lam_s = lam_n + ...
+  void *G[3];            // per-direction face contributions [nv][6][nfaces_d]
+  Phys ph;
+  CstT<float> cf;
+  CstT<double> cd;
+};
+
+struct AdjKernels {
+  cudaError_t (*face)(const AdjArgs &, int d, long long nfaces, cudaStream_t);
+  cudaError_t (*cell)(const AdjArgs &, long long ncell, cudaStream_t);
+};
+
+// Adjoint kernels of the dry inviscid layouts; false when not built.
+bool find_adjoint_kernels(int f32, int three_d, AdjKernels *out);
 
 // Returns false when the configuration is not built into this library.
 bool find_kernels(int f32, int nvap, int ncond, int three_d, int visc, KernelSet *out);

@@ -78,21 +78,14 @@ __device__ __forceinline__ const CstT<float> &cst<float>(const StageArgs &a) { r
 template <>
 __device__ __forceinline__ const CstT<double> &cst<double>(const StageArgs &a) { return a.cd; }
 
-template <bool D3>
-struct Tile;
-template <>
-struct Tile<false> {  // x-z plane: 32 x 14 keeps every per-direction phase of 256 threads
-                      // 87-100 % busy (e.g. 34 x 14 reconstructions, 32 x 15 z-faces)
-  static constexpr int TX = 32, TY = 1, TZ = 14, NT = 256;
-};
-template <>
-struct Tile<true> {
-  static constexpr int TX = 8, TY = 8, TZ = 4, NT = 256;
+// Tile shape: TX x TY x TZ owned cells per CTA of NT threads (TY = 1 in the x-z plane).
+template <int TX_, int TY_, int TZ_, int NT_ = 256>
+struct TileT {
+  static constexpr int TX = TX_, TY = TY_, TZ = TZ_, NT = NT_;
 };
 
-template <bool D3>
+template <class T, bool D3>
 struct Box {
-  using T = Tile<D3>;
   static constexpr int HX = 3, HY = D3 ? 3 : 0, HZ = 3;
   static constexpr int BX = T::TX + 6, BY = T::TY + 2 * HY, BZ = T::TZ + 6;
   static constexpr int NBOX = BX * BY * BZ;
@@ -107,6 +100,48 @@ struct Box {
   }
 };
 
+// Per-level reference values in the kernel's type: FP32 kernels read FP32 copies, FP64
+// kernels the FP64 originals.
+template <class R>
+struct Prof;
+template <>
+struct Prof<float> {
+  static __device__ __forceinline__ float pc(const DomDev &D, int k) { return D.pc_f[k]; }
+  static __device__ __forceinline__ float pf(const DomDev &D, int k) { return D.pf_f[k]; }
+  static __device__ __forceinline__ float er(const DomDev &D, int k) { return D.er_f[k]; }
+  // rho - rho_bar_k from the conserved densities y: dry air minus the FP32 head of rho_bar is
+  // exact (the two are within a factor of 2), the tracers are added to that small difference,
+  // and the FP32 tail of rho_bar (rb_lo) last
+  template <class L>
+  static __device__ __forceinline__ float drho(const DomDev &D, int k, const float *y) {
+    float r = y[0] - D.rb_hi[k];
+#pragma unroll
+    for (int s = 1; s < L::IM0; ++s) r += y[s];
+    return r - D.rb_lo[k];
+  }
+  static __device__ __forceinline__ float grav(const DomDev &D) { return D.fgrav; }
+  static __device__ __forceinline__ float ih(const DomDev &D, int d) {
+    return d == 0 ? D.fidx : (d == 1 ? D.fidy : D.fidz);
+  }
+};
+template <>
+struct Prof<double> {
+  static __device__ __forceinline__ double pc(const DomDev &D, int k) { return D.p_cell[k]; }
+  static __device__ __forceinline__ double pf(const DomDev &D, int k) { return D.p_face[k]; }
+  static __device__ __forceinline__ double er(const DomDev &D, int k) { return D.e_ref[k]; }
+  template <class L>
+  static __device__ __forceinline__ double drho(const DomDev &D, int k, const double *y) {
+    double r = y[0];
+#pragma unroll
+    for (int s = 1; s < L::IM0; ++s) r += y[s];
+    return r - D.rho_bar[k];
+  }
+  static __device__ __forceinline__ double grav(const DomDev &D) { return D.grav; }
+  static __device__ __forceinline__ double ih(const DomDev &D, int d) {
+    return d == 0 ? D.idx : (d == 1 ? D.idy : D.idz);
+  }
+};
+
 // ------------------------------------------------------------------------------------------
 // thermodynamics (Sec. 2, App. B)
 // ------------------------------------------------------------------------------------------
@@ -116,8 +151,8 @@ struct Box {
 // formed from small numbers. Moist: the inversion U = rho e - K - A, T = U / C_v, p = R_m T
 // runs in FP64.
 template <class R, class L>
-__device__ __forceinline__ void cons_to_prim(const Phys &ph, const CstT<R> &C, const R *y, R *x,
-                                             double pbar, double eref, R &p_tot, R &T_out) {
+__device__ __forceinline__ void cons_to_prim(const Phys &ph, const CstT<R> &C, const DomDev &D,
+                                             int k, const R *y, R *x, R &p_tot, R &T_out) {
   R rho = y[0];
 #pragma unroll
   for (int s = 1; s < L::IM0; ++s) rho += y[s];
@@ -136,11 +171,11 @@ __device__ __forceinline__ void cons_to_prim(const Phys &ph, const CstT<R> &C, c
     // dry: p = (gamma_d - 1) (rho e - K), so p - pbar = (gamma_d - 1) (y_E - K)
     const R pp = C.gm1 * (y[L::IE] - K);
     x[L::IE] = pp;
-    const R p = pp + R(pbar);
+    const R p = pp + Prof<R>::pc(D, k);
     p_tot = p;
     T_out = p * ir * C.iR_d;
-    (void)eref;
-  } else {
+  } else if constexpr (sizeof(R) == 8) {
+    // FP64 kernels: U = rho e - K - A, T = U / C_v, p = R_m T directly
     double A = 0.0, Cv = y[0], Rm = y[0];
 #pragma unroll
     for (int i = 0; i < L::NVAP; ++i) {
@@ -154,12 +189,37 @@ __device__ __forceinline__ void cons_to_prim(const Phys &ph, const CstT<R> &C, c
     }
     Cv *= ph.c_vd;
     Rm *= ph.R_d;
-    double U = (double(y[L::IE]) + eref) - double(K) - A;
+    double U = (double(y[L::IE]) + D.e_ref[k]) - double(K) - A;
     double T = U / Cv;
     double p = Rm * T;
     p_tot = R(p);
     T_out = R(T);
-    x[L::IE] = R(p - pbar);
+    x[L::IE] = R(p - D.p_cell[k]);
+  } else {
+    // FP32 kernels: the same p, rewritten so that only small numbers cancel. With the sums
+    // over densities C = rho_d + sum sigma_v,i rho_i + sum sigma_ij rho_ij and
+    // G = rho_d + sum rho_i / eps_i, p = R_d G T = (gamma_d - 1) (1 + delta) U with
+    // delta = (G - C) / C, a sum over tracers only. Since e_ref = pbar / (gamma_d - 1),
+    //   p - pbar = (gamma_d - 1) [ (y_E - K - A) + delta (y_E + e_ref - K - A) ],
+    // accurate to ~1e-3 Pa at 1e6..1e7 Pa without FP64 (y_E = rho e - e_ref is stored).
+    R A = R(0), Cv = y[0], dG = R(0);
+#pragma unroll
+    for (int i = 0; i < L::NVAP; ++i) {
+      Cv += C.sig_v[i] * y[1 + i];
+      dG += (C.inv_eps[i] - C.sig_v[i]) * y[1 + i];
+#pragma unroll
+      for (int j = 0; j < L::NCOND; ++j) {
+        Cv += C.sig_c[i][j] * y[L::cond(i, j)];
+        dG -= C.sig_c[i][j] * y[L::cond(i, j)];
+        A += C.mu[i][j] * y[L::cond(i, j)];
+      }
+    }
+    const R delta = dG * Ar<R>::rcp(Cv);
+    const R small = y[L::IE] - K - A;
+    const R pp = C.gm1 * (small + delta * (small + Prof<R>::er(D, k)));
+    x[L::IE] = pp;
+    p_tot = pp + Prof<R>::pc(D, k);
+    T_out = R(0);  // not needed by the moist kernels
   }
 }
 
@@ -303,16 +363,58 @@ __device__ __forceinline__ void cell_Tp(const Phys &ph, const R *y, double eref,
 }
 
 template <class R, class L>
-__device__ int satadj_cell(const Phys &ph, const CstT<R> &C, R *y, double eref, int max_iter) {
+__device__ int satadj_cell(const Phys &ph, const CstT<R> &C, R *y, double eref, R eref_r,
+                           int max_iter) {
   if constexpr (!L::MOIST) {
     return 0;
   } else {
+    if constexpr (sizeof(R) == 4) {
+      // FP32 screen: App. D's projected transfer is negative exactly when the vapour's partial
+      // pressure is below saturation, and is then limited to the cloud present. A cloud-free
+      // vapour that is subsaturated by more than the FP32 error of this estimate (1e-3
+      // relative margin) therefore needs no transfer; if all vapours qualify the cell is left
+      // unchanged, as the FP64 iteration would leave it, after one sweep.
+      R rho = y[0], K2 = R(0), A = R(0), Cv = y[0];
+      bool clear = true;
+#pragma unroll
+      for (int s = 1; s < L::IM0; ++s) rho += y[s];
+#pragma unroll
+      for (int m = 0; m < L::NMOM; ++m) K2 += y[L::IM0 + m] * y[L::IM0 + m];
+#pragma unroll
+      for (int i = 0; i < L::NVAP; ++i) {
+        Cv += C.sig_v[i] * y[1 + i];
+        if (y[L::cond(i, 0)] != R(0)) clear = false;
+#pragma unroll
+        for (int j = 0; j < L::NCOND; ++j) {
+          Cv += C.sig_c[i][j] * y[L::cond(i, j)];
+          A += C.mu[i][j] * y[L::cond(i, j)];
+        }
+      }
+      if (clear) {
+        // T = U / (c_vd C) with c_vd = R_d / (gamma_d - 1)
+        const R T = ((y[L::IE] + eref_r) - R(0.5) * K2 * Ar<R>::rcp(rho) - A) *
+                    Ar<R>::rcp(Cv) * C.gm1 * C.iR_d;
+#pragma unroll
+        for (int i = 0; i < L::NVAP; ++i) {
+          const R t = T * C.inv_Tref[i];
+          const R ps = C.pref[i] * Ar<R>::exp_(C.beta[i] * (R(1) - Ar<R>::rcp(t)) -
+                                               C.delta[i] * Ar<R>::log_(t));
+          const R pv = y[1 + i] * C.R_d * C.inv_eps[i] * T;  // rho_i R_i T
+          if (!(pv < R(0.999) * ps)) clear = false;
+        }
+        if (clear) return 1;
+      }
+    }
+    double Td = 0.0, pd = 0.0;
+    bool stale = true;  // T and p must be recomputed from the conserved energy
     for (int sweep = 1; sweep <= max_iter; ++sweep) {
       bool conv = true;
 #pragma unroll
       for (int i = 0; i < L::NVAP; ++i) {
-        double Td, pd;
-        cell_Tp<R, L>(ph, y, eref, Td, pd);
+        if (stale) {
+          cell_Tp<R, L>(ph, y, eref, Td, pd);
+          stale = false;
+        }
         R T = R(Td), p = R(pd);
         const R dTr = R(Td - ph.Tref[i]);  // T - T^r kept accurate: s(T) is steep
         R N = y[0], gas = y[0], heat = R(0);
@@ -355,8 +457,11 @@ __device__ int satadj_cell(const Phys &ph, const CstT<R> &C, R *y, double eref, 
         } else {
           drho = dq * C.eps[i] * N;
         }
-        y[1 + i] -= drho;
-        y[L::cond(i, 0)] += drho;
+        if (drho != R(0)) {
+          y[1 + i] -= drho;
+          y[L::cond(i, 0)] += drho;
+          stale = true;
+        }
         if (fabs(dq) > C.satadj_tol * (qv + qc)) conv = false;
       }
       if (conv) return sweep;
@@ -410,48 +515,6 @@ __device__ __forceinline__ double block_max(double v, double *red) {
 // ------------------------------------------------------------------------------------------
 // the fused stage kernel
 // ------------------------------------------------------------------------------------------
-// Per-level reference values in the kernel's type: FP32 kernels read FP32 copies, FP64
-// kernels the FP64 originals.
-template <class R>
-struct Prof;
-template <>
-struct Prof<float> {
-  static __device__ __forceinline__ float pc(const DomDev &D, int k) { return D.pc_f[k]; }
-  static __device__ __forceinline__ float pf(const DomDev &D, int k) { return D.pf_f[k]; }
-  static __device__ __forceinline__ float er(const DomDev &D, int k) { return D.er_f[k]; }
-  // rho - rho_bar_k from the conserved densities y: dry air minus the FP32 head of rho_bar is
-  // exact (the two are within a factor of 2), the tracers are added to that small difference,
-  // and the FP32 tail of rho_bar (rb_lo) last
-  template <class L>
-  static __device__ __forceinline__ float drho(const DomDev &D, int k, const float *y) {
-    float r = y[0] - D.rb_hi[k];
-#pragma unroll
-    for (int s = 1; s < L::IM0; ++s) r += y[s];
-    return r - D.rb_lo[k];
-  }
-  static __device__ __forceinline__ float grav(const DomDev &D) { return D.fgrav; }
-  static __device__ __forceinline__ float ih(const DomDev &D, int d) {
-    return d == 0 ? D.fidx : (d == 1 ? D.fidy : D.fidz);
-  }
-};
-template <>
-struct Prof<double> {
-  static __device__ __forceinline__ double pc(const DomDev &D, int k) { return D.p_cell[k]; }
-  static __device__ __forceinline__ double pf(const DomDev &D, int k) { return D.p_face[k]; }
-  static __device__ __forceinline__ double er(const DomDev &D, int k) { return D.e_ref[k]; }
-  template <class L>
-  static __device__ __forceinline__ double drho(const DomDev &D, int k, const double *y) {
-    double r = y[0];
-#pragma unroll
-    for (int s = 1; s < L::IM0; ++s) r += y[s];
-    return r - D.rho_bar[k];
-  }
-  static __device__ __forceinline__ double grav(const DomDev &D) { return D.grav; }
-  static __device__ __forceinline__ double ih(const DomDev &D, int d) {
-    return d == 0 ? D.idx : (d == 1 ? D.idy : D.idz);
-  }
-};
-
 // WENO5 of Sec. 4.2 evaluated once per cell c for both of its faces from the five cells
 // (a, b, c, d, e) = Q_{c-2} .. Q_{c+2}:
 //   qm = left state at face c+1/2   = I_weno(Q_{c-2}, .., Q_{c+2})
@@ -532,9 +595,9 @@ __device__ __forceinline__ R cell_rate_r(const CstT<R> &C, const R *y, R eref, R
   return r;
 }
 
-template <class R, class L, bool VISC>
+template <class R, class L, bool VISC, class T>
 struct StageSmem {
-  using B = Box<L::D3>;
+  using B = Box<T, L::D3>;
   static constexpr size_t prim = sizeof(R) * L::NV * B::NBOX;
   static constexpr size_t visc = VISC ? sizeof(R) * 2 * B::NBOX : 0;
   static constexpr size_t face = sizeof(R) * 2 * L::NV * B::NF;  // left state/flux, right state
@@ -542,16 +605,44 @@ struct StageSmem {
   static constexpr size_t total = prim + visc + face + red;
 };
 
-template <class R, class L, bool VISC>
-__global__ void __launch_bounds__(Tile<L::D3>::NT)
-    stage_kernel(const StageArgs a) {
-  using T = Tile<L::D3>;
-  using B = Box<L::D3>;
-  using S = StageSmem<R, L, VISC>;
+// Grid-wide barrier of the persistent step kernel (all CTAs co-resident by a cooperative
+// launch). Every wait is bounded: after ~2 s of spinning the CTA records kFlagTimeout and
+// proceeds, so a fault can corrupt results but never hang the device.
+__device__ __forceinline__ void grid_barrier(GridSync *gs, unsigned int nblocks,
+                                             unsigned int *flags) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned int *vgen = &gs->gen;
+    const unsigned int g = *vgen;
+    __threadfence();
+    const unsigned int arrived = atomicAdd(&gs->count, 1u);
+    if (arrived == nblocks - 1) {
+      atomicExch(&gs->count, 0u);
+      __threadfence();
+      atomicAdd(&gs->gen, 1u);
+    } else {
+      const long long t0 = clock64();
+      while (*vgen == g) {
+        if (clock64() - t0 > 4000000000ll) {
+          atomicOr(flags, (unsigned)kFlagTimeout);
+          break;
+        }
+        __nanosleep(128);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+}
+
+template <class R, class L, bool VISC, class T>
+__device__ __forceinline__ void stage_tiles(const StageArgs &a, const int stage,
+                                            unsigned char *smem) {
+  using B = Box<T, L::D3>;
+  using S = StageSmem<R, L, VISC, T>;
   using P = Prof<R>;
   constexpr int NV = L::NV;
   constexpr int TX = T::TX, TY = T::TY, TZ = T::TZ, NT = T::NT;
-  extern __shared__ __align__(16) unsigned char smem[];
   R *s_prim = reinterpret_cast<R *>(smem);
   R *s_th = reinterpret_cast<R *>(smem + S::prim);
   R *s_pi = s_th + (VISC ? B::NBOX : 0);
@@ -573,18 +664,18 @@ __global__ void __launch_bounds__(Tile<L::D3>::NT)
     const int y0 = ((lt / D.tx) % D.ty) * TY;
     const int z0 = (lt / (D.tx * D.ty)) * TZ;
     const int ex = min(TX, nx - x0), ey = min(TY, ny - y0), ez = min(TZ, nz - z0);
-    const R *Ys = reinterpret_cast<const R *>(D.buf[a.stage]);
+    const R *Ys = reinterpret_cast<const R *>(D.buf[stage]);
     const R *Yn = reinterpret_cast<const R *>(D.buf[0]);
-    R *Yo = reinterpret_cast<R *>(D.buf[a.stage == 0 ? 1 : (a.stage == 1 ? 2 : 0)]);
+    R *Yo = reinterpret_cast<R *>(D.buf[stage == 0 ? 1 : (stage == 1 ? 2 : 0)]);
     // the stage's time step, formed once per CTA
     if (tid == 0) {
       double dt;
-      if (a.stage == 0) {
+      if (stage == 0) {
         dt = D.dt_fixed > 0.0 ? D.dt_fixed : D.cfl / __longlong_as_double((long long)*D.rate);
         if (lt == 0) *D.dt_step = dt;
       } else {
-        dt = *D.dt_step;
-        if (a.stage == 1 && lt == 0) *D.rate = 0ull;
+        dt = *(volatile double *)D.dt_step;
+        if (stage == 1 && lt == 0) *D.rate = 0ull;
       }
       s_red[0] = dt;
     }
@@ -601,8 +692,7 @@ __global__ void __launch_bounds__(Tile<L::D3>::NT)
 #pragma unroll
         for (int v = 0; v < NV; ++v) ys[m][v] = Ys[v * ncell + g];
         R x[NV], pt, Tt;
-        cons_to_prim<R, L>(ph, C, ys[m], x, D.p_cell[k], D.e_ref[k], pt, Tt);
-        if constexpr (L::NVAP == 0) pt = x[L::IE] + P::pc(D, k);
+        cons_to_prim<R, L>(ph, C, D, k, ys[m], x, pt, Tt);
         const int bi = B::at(lx + 3, ly + B::HY, lz + 3);
 #pragma unroll
         for (int v = 0; v < NV; ++v) s_prim[v * B::NBOX + bi] = x[v];
@@ -651,8 +741,7 @@ __global__ void __launch_bounds__(Tile<L::D3>::NT)
         R y[NV], x[NV], pt, Tt;
 #pragma unroll
         for (int v = 0; v < NV; ++v) y[v] = Ys[v * ncell + g];
-        cons_to_prim<R, L>(ph, C, y, x, D.p_cell[gz], D.e_ref[gz], pt, Tt);
-        if constexpr (L::NVAP == 0) pt = x[L::IE] + P::pc(D, gz);
+        cons_to_prim<R, L>(ph, C, D, gz, y, x, pt, Tt);
         if (flip) x[L::mom(dirn)] = -x[L::mom(dirn)];
         const int bi = B::at(bx, by, bz);
 #pragma unroll
@@ -795,17 +884,18 @@ __global__ void __launch_bounds__(Tile<L::D3>::NT)
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
           const R s1 = ys[m][v] + dt * acc[m][v];
-          if (a.stage == 0) {
+          if (stage == 0) {
             yo[v] = s1;
           } else {
             const R yn = Yn[v * ncell + g];
-            yo[v] = a.stage == 1 ? R(0.75) * yn + R(0.25) * s1
-                                 : yn * R(1.0 / 3.0) + R(2.0 / 3.0) * s1;
+            yo[v] = stage == 1 ? R(0.75) * yn + R(0.25) * s1
+                               : yn * R(1.0 / 3.0) + R(2.0 / 3.0) * s1;
           }
         }
         if constexpr (L::MOIST) {
           if (ph.satadj) {
-            const int it = satadj_cell<R, L>(ph, C, yo, D.e_ref[k], ph.satadj_max_iter);
+            const int it =
+                satadj_cell<R, L>(ph, C, yo, D.e_ref[k], P::er(D, k), ph.satadj_max_iter);
             if (it < 0)
               atomicOr(a.flags, (unsigned)kFlagNoConv);
             else if (it > 2)
@@ -818,16 +908,35 @@ __global__ void __launch_bounds__(Tile<L::D3>::NT)
         if (!(rs > R(0)) || !isfinite(yo[L::IE])) atomicOr(a.flags, (unsigned)kFlagNonFinite);
 #pragma unroll
         for (int v = 0; v < NV; ++v) Yo[v * ncell + g] = yo[v];
-        if (a.stage == 2)
+        if (stage == 2)
           rate_max = fmax(rate_max, cell_rate_r<R, L>(C, yo, P::er(D, k), P::ih(D, 0),
                                                       P::ih(D, 1), P::ih(D, 2)));
       }
     }
-    if (a.stage == 2) {
+    if (stage == 2) {
       double bm = block_max(double(rate_max), s_red + 1);
       if (tid == 0) atomicMax(D.rate, (unsigned long long)__double_as_longlong(bm));
     }
     __syncthreads();
+  }
+}
+
+// One Runge-Kutta stage over all tiles of all domains.
+template <class R, class L, bool VISC, class T>
+__global__ void __launch_bounds__(T::NT) stage_kernel(const StageArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  stage_tiles<R, L, VISC, T>(a, a.stage, smem);
+}
+
+// One whole step (three stages) in a single persistent cooperative launch: the CTAs walk the
+// tile queue of every domain per stage and meet at a grid barrier between stages.
+template <class R, class L, bool VISC, class T>
+__global__ void __launch_bounds__(T::NT) step_kernel(const StageArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+#pragma unroll 1
+  for (int st = 0; st < 3; ++st) {
+    stage_tiles<R, L, VISC, T>(a, st, smem);
+    if (st < 2) grid_barrier(a.gsync, gridDim.x, a.flags);
   }
 }
 
@@ -917,7 +1026,9 @@ __global__ void __launch_bounds__(256) satadj_kernel(const StageArgs a, int dm, 
 #pragma unroll
     for (int v = 0; v < L::NV; ++v) y[v] = Y[v * D.ncell + c];
     const double er = D.e_ref[c / ((long long)D.nx * D.ny)];
-    const int it = satadj_cell<R, L>(a.ph, cst<R>(a), y, er, a.ph.satadj_max_iter);
+    const int it = satadj_cell<R, L>(a.ph, cst<R>(a), y, er,
+                                     Prof<R>::er(D, int(c / ((long long)D.nx * D.ny))),
+                                     a.ph.satadj_max_iter);
     if (it < 0)
       atomicOr(a.flags, (unsigned)kFlagNoConv);
     else
@@ -930,17 +1041,61 @@ __global__ void __launch_bounds__(256) satadj_kernel(const StageArgs a, int dm, 
 // ------------------------------------------------------------------------------------------
 // host launchers of one configuration
 // ------------------------------------------------------------------------------------------
-template <class R, class L, bool VISC>
-struct Family {
-  using S = StageSmem<R, L, VISC>;
+template <class R, class L, bool VISC, class T>
+struct Variant {
+  using S = StageSmem<R, L, VISC, T>;
   static cudaError_t prepare() {
-    return cudaFuncSetAttribute(stage_kernel<R, L, VISC>,
+    cudaError_t e = cudaFuncSetAttribute(stage_kernel<R, L, VISC, T>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         int(S::total));
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(step_kernel<R, L, VISC, T>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, int(S::total));
   }
   static cudaError_t stage(const StageArgs &a, int grid, cudaStream_t s) {
-    stage_kernel<R, L, VISC><<<grid, Tile<L::D3>::NT, S::total, s>>>(a);
+    stage_kernel<R, L, VISC, T><<<grid, T::NT, S::total, s>>>(a);
     return cudaGetLastError();
   }
+  static int max_resident_blocks() {
+    int dev = 0, nsm = 0, per = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, step_kernel<R, L, VISC, T>, T::NT,
+                                                      S::total) != cudaSuccess)
+      return 0;
+    return per * nsm;
+  }
+  static cudaError_t step(const StageArgs &a, int grid, cudaStream_t s) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(T::NT);
+    cfg.dynamicSmemBytes = S::total;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, step_kernel<R, L, VISC, T>, a);
+  }
+  static TileVariant get() {
+    TileVariant v;
+    v.tile[0] = T::TX;
+    v.tile[1] = T::TY;
+    v.tile[2] = T::TZ;
+    v.threads = T::NT;
+    v.smem_stage = S::total;
+    v.stage = &stage;
+    v.step = &step;
+    v.max_resident_blocks = &max_resident_blocks;
+    v.prepare = &prepare;
+    return v;
+  }
+};
+
+template <class R, class L>
+struct Family {
   static cudaError_t rate(const StageArgs &a, int dm, int buf, cudaStream_t s) {
     rate_kernel<R, L><<<304, 256, 0, s>>>(a, dm, buf);
     return cudaGetLastError();
@@ -955,18 +1110,16 @@ struct Family {
     satadj_kernel<R, L><<<608, 256, 0, s>>>(a, dm, buf);
     return cudaGetLastError();
   }
+  // The tile shapes offered to the autotuner; the first is the default.
+  template <bool VISC, class... Ts>
   static KernelSet set() {
     KernelSet k;
-    k.tile[0] = Tile<L::D3>::TX;
-    k.tile[1] = Tile<L::D3>::TY;
-    k.tile[2] = Tile<L::D3>::TZ;
-    k.threads = Tile<L::D3>::NT;
-    k.smem_stage = S::total;
-    k.stage = &stage;
+    k.nvariants = 0;
+    TileVariant vs[] = {Variant<R, L, VISC, Ts>::get()...};
+    for (const TileVariant &v : vs) k.var[k.nvariants++] = v;
     k.rate = &rate;
     k.budget = &budget;
     k.satadj = &satadj;
-    k.prepare = &prepare;
     return k;
   }
 };

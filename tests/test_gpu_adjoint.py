@@ -1,0 +1,172 @@
+"""Discrete adjoint in the CUDA library against the oracle's adjoint
+(whose own pins are central differences of the oracle step), against central differences of
+the library's forward run, between FP32 and FP64, and across checkpoint spacings; and the
+gradient of the final kinetic energy with respect to the initial potential temperature
+through torch.autograd against central differences."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import Oracle
+
+from test_oracle_adjoint import with_pressure_waves
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    t = pytest.importorskip("torch")
+    if not t.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1901_02955_gb300 import build
+    build.build()
+    return t
+
+
+def cases():
+    return {
+        "bubble_walls_ragged": with_pressure_waves(W.add_random_motion(W.warm_bubble(n=37))),
+        "bubble_3d_periodic": with_pressure_waves(
+            W.add_random_motion(W.dry_bubble_3d(nx=11, ny=9, nz=7))),
+    }
+
+
+def oracle_adjoint(w, nsteps, dt, lam):
+    o = Oracle(w)
+    states = [w.Y.copy()]
+    for _ in range(nsteps - 1):
+        states.append(o.step(states[-1], 1, dt=dt)[0])
+    for Yn in reversed(states):
+        lam = o.step_adjoint(Yn, dt, lam)
+    return lam
+
+
+@pytest.mark.parametrize("name", list(cases()))
+def test_fp64_adjoint_matches_oracle(torch, name):
+    from paper_1901_02955_gb300 import Context
+    w = cases()[name]
+    dt = Oracle(w).dt_cfl(w.Y, 0.8)
+    nsteps = 5
+    lam = np.random.default_rng(41).normal(size=w.Y.shape)
+    ctx = Context(w, dtype="f64")
+    ctx.set_state(w.Y)
+    ctx.record(nsteps, ckpt_every=2, dt_fixed=dt)
+    got = ctx.step_adjoint(nsteps, lam)
+    want = oracle_adjoint(w, nsteps, dt, lam)
+    err = np.linalg.norm(got - want) / np.linalg.norm(want)
+    assert err < 1e-10, err
+    # the state after the adjoint is the recorded final state
+    YN = Oracle(w).step(w.Y, nsteps, dt=dt)[0]
+    assert np.linalg.norm(ctx.get_state() - YN) / np.linalg.norm(YN) < 1e-12
+
+
+def test_checkpoint_spacing_does_not_change_the_adjoint(torch):
+    from paper_1901_02955_gb300 import Context
+    w = cases()["bubble_walls_ragged"]
+    dt = Oracle(w).dt_cfl(w.Y, 0.8)
+    lam = np.random.default_rng(42).normal(size=w.Y.shape)
+    outs = []
+    for k in (1, 3, 7):
+        ctx = Context(w, dtype="f64")
+        ctx.set_state(w.Y)
+        ctx.record(7, ckpt_every=k, dt_fixed=dt)
+        outs.append(ctx.step_adjoint(7, lam))
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
+
+
+def test_fp32_adjoint_tracks_fp64_adjoint(torch):
+    from paper_1901_02955_gb300 import Context
+    w = cases()["bubble_walls_ragged"]
+    dt = Oracle(w).dt_cfl(w.Y, 0.8)
+    lam = np.random.default_rng(43).normal(size=w.Y.shape)
+    res = {}
+    for dt_name in ("f64", "f32"):
+        ctx = Context(w, dtype=dt_name)
+        ctx.set_state(w.Y)
+        ctx.record(4, ckpt_every=2, dt_fixed=dt)
+        res[dt_name] = ctx.step_adjoint(4, lam.astype(np.float32 if dt_name == "f32" else np.float64))
+    for f in range(w.nv):
+        a, b = res["f32"][f].astype(np.float64), res["f64"][f]
+        assert np.linalg.norm(a - b) <= 1e-3 * np.linalg.norm(b) + 1e-30, f
+
+
+def test_adjoint_dot_product_with_forward_differences(torch):
+    """<lambda, (Y_N(Y0 + h v) - Y_N(Y0 - h v)) / 2h> = <lambda_0, v> with the library's own
+    FP64 forward run."""
+    from paper_1901_02955_gb300 import Context
+    w = cases()["bubble_walls_ragged"]
+    dt = Oracle(w).dt_cfl(w.Y, 0.8)
+    rs = np.random.default_rng(44)
+    v = rs.normal(size=w.Y.shape)
+    for f in range(w.nv):
+        v[f] *= 1e-3 * np.ptp(w.Y[f])
+    lam = rs.normal(size=w.Y.shape)
+    nsteps = 6
+    ctx = Context(w, dtype="f64")
+
+    def run(Y):
+        ctx.set_state(np.ascontiguousarray(Y))
+        ctx.step(nsteps, dt_fixed=dt)
+        return ctx.get_state()
+
+    def fd(h):
+        return np.sum(lam * (run(w.Y + h * v) - run(w.Y - h * v)) / (2 * h))
+
+    rich = (4.0 * fd(1e-4) - fd(2e-4)) / 3.0
+    ctx.set_state(w.Y)
+    ctx.record(nsteps, ckpt_every=4, dt_fixed=dt)
+    lam0 = ctx.step_adjoint(nsteps, lam)
+    assert rich == pytest.approx(np.sum(lam0 * v), rel=1e-6)
+
+
+def theta_gradient_check(torch, moving, tol, ndir=4):
+    from paper_1901_02955_gb300 import Context
+    from paper_1901_02955_gb300.autograd import SnapSteps, dry_state_from_theta, kinetic_energy
+    w = W.warm_bubble(n=48)
+    pk = torch.tensor(0.5 * (w.p_bar_face[:-1] + w.p_bar_face[1:]), dtype=torch.float64,
+                      device="cuda")
+    kappa = (w.gamma_d - 1.0) / w.gamma_d
+    T = w.Y[-1] * (w.gamma_d - 1.0) / (w.R_d * w.Y[0])  # at rest: p = (gamma - 1) rho e
+    theta0 = torch.tensor(T * (1e5 / pk.cpu().numpy()[:, None, None]) ** kappa,
+                          dtype=torch.float64, device="cuda")
+    vel = None
+    if moving:
+        rs = np.random.default_rng(46)
+        vel = torch.tensor(rs.uniform(-2.0, 2.0, size=(2,) + theta0.shape), device="cuda")
+    ctx = Context(w, dtype="f64")
+    dt = 0.5 * Oracle(w).dt_cfl(w.Y, 0.8)
+    nsteps = 12
+    vol = w.dx * w.dz
+
+    def J(theta):
+        Y0 = dry_state_from_theta(theta, pk, w.R_d, w.gamma_d, velocity=vel)
+        YN = SnapSteps.apply(Y0.contiguous(), ctx, nsteps, 5, dt)
+        return kinetic_energy(YN, vol)
+
+    th = theta0.clone().requires_grad_(True)
+    J(th).backward()
+    grad = th.grad.detach()
+    rs = np.random.default_rng(45)
+    for _ in range(ndir):
+        d = torch.tensor(rs.normal(size=theta0.shape), device="cuda")
+        with torch.no_grad():
+            def fd(h):
+                return (J(theta0 + h * d) - J(theta0 - h * d)).item() / (2 * h)
+            rich = (4.0 * fd(1e-4) - fd(2e-4)) / 3.0
+        assert rich == pytest.approx(float((grad * d).sum()), rel=tol)
+
+
+def test_kinetic_energy_gradient_wrt_initial_theta_moving_flow(torch):
+    """dJ/dtheta_0 through torch.autograd (initial-state map in torch, steps and their
+    adjoint in the library) against central differences along random directions, for a
+    bubble in a random flow (no face with u* = 0, so J is differentiable)."""
+    theta_gradient_check(torch, moving=True, tol=1e-6)
+
+
+def test_kinetic_energy_gradient_wrt_initial_theta_from_rest(torch):
+    """From rest u* = 0 at nearly every face, where the upwind flux has a kink: J is not
+    differentiable at theta_0. The adjoint takes the mean of the one-sided derivatives face
+    by face; central differences average whole products of one-sided Jacobians, which
+    differ at second order in the kink jumps (~1e-3 relative here)."""
+    theta_gradient_check(torch, moving=False, tol=1e-4)

@@ -1,0 +1,83 @@
+"""Ensemble launch modes: every tile shape and the persistent one-launch
+step give bitwise the same result as the default three-launch step (the per-cell and
+per-face arithmetic does not depend on the tiling), and the autotuner leaves the state
+untouched. The oracle comparison of an ensemble is in test_gpu_parity.py."""
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1901_02955_gb300 import build
+    build.build()
+
+
+def members():
+    return [W.add_random_motion(W.moist_bubble(n=n, A=A, R=R), seed=W.BASE_SEED + n)
+            for n, A, R in [(20, 0.5, 200.0), (64, 1.5, 300.0), (37, 1.0, 150.0), (96, 2.0, 390.0)]]
+
+
+def run(ws, dtype, variant=None, persistent=False, steps=3, graph=True):
+    from paper_1901_02955_gb300 import Context
+    ctx = Context(ws, dtype=dtype)
+    if variant is not None:
+        ctx.set_tile_variant(variant)
+    ctx.use_persistent(persistent)
+    ctx.use_graph(graph)
+    for d, w in enumerate(ws):
+        ctx.set_state(w.Y, domain=d)
+    ctx.step(steps)
+    out = [ctx.get_state(domain=d) for d in range(len(ws))]
+    info = ctx.info()
+    ctx.close()
+    return out, info
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_tile_variants_and_persistent_step_agree_bitwise(dtype):
+    ws = members()
+    ref, info = run(ws, dtype)
+    assert info["kernel_launches_per_step"] == 3
+    for v in range(info["n_tile_variants"]):
+        for persistent in (False, True):
+            for graph in (True, False):
+                out, inf = run(ws, dtype, v, persistent, graph=graph)
+                assert inf["tile_variant"] == v
+                assert inf["kernel_launches_per_step"] == (1 if persistent else 3)
+                for a, b in zip(out, ref):
+                    assert np.array_equal(a, b), (v, persistent, graph)
+
+
+def test_persistent_step_on_3d_and_dry_layouts():
+    for ws in ([W.add_random_motion(W.jovian(nx=13, ny=11, nz=18))],
+               [W.add_random_motion(W.density_current(nx=70, nz=37, dtype="f32"))],
+               [W.add_random_motion(W.dry_bubble_3d(nx=19, ny=10, nz=9))]):
+        ref, info = run(ws, "f32")
+        for v in range(info["n_tile_variants"]):
+            out, _ = run(ws, "f32", v, True)
+            assert all(np.array_equal(a, b) for a, b in zip(out, ref)), v
+
+
+def test_autotune_keeps_state_and_picks_a_mode():
+    from paper_1901_02955_gb300 import Context
+    ws = members()
+    ctx = Context(ws, dtype="f32")
+    for d, w in enumerate(ws):
+        ctx.set_state(w.Y, domain=d)
+    before = [ctx.get_state(domain=d) for d in range(len(ws))]
+    res = ctx.autotune(steps=3)
+    assert res["ms_per_step"] > 0
+    info = ctx.info()
+    assert info["tile_variant"] == res["variant"] and info["persistent"] == res["persistent"]
+    after = [ctx.get_state(domain=d) for d in range(len(ws))]
+    assert all(np.array_equal(a, b) for a, b in zip(before, after))
+    ctx.step(3)
+    ref, _ = run(ws, "f32")
+    assert all(np.array_equal(ctx.get_state(domain=d), ref[d]) for d in range(len(ws)))

@@ -230,11 +230,16 @@ def test_satadj_sweep_limit_is_reported():
     assert e.value.code == capi.ENOCONV
 
 
-def test_adjoint_entry_reports_not_supported():
+def test_adjoint_entry_reports_not_supported_for_moist_contexts():
+    import ctypes
     from paper_1901_02955_gb300 import capi
-    w = W.warm_bubble(n=8)
+    w = W.moist_bubble(n=8)
     ctx = Context(w)
-    rc = ctx.lib.snap_step_adjoint(ctx._ptr, 1, None, None, capi.F64, None)
+    buf = np.zeros(w.Y.shape)
+    out = np.zeros(w.Y.shape)
+    assert ctx.lib.snap_record(ctx._ptr, 1, 1, 0.0) == capi.ENOTSUP
+    rc = ctx.lib.snap_step_adjoint(ctx._ptr, 1, ctypes.c_void_p(buf.ctypes.data),
+                                   ctypes.c_void_p(out.ctypes.data), capi.F64, None)
     assert rc == capi.ENOTSUP
 
 
@@ -291,7 +296,9 @@ def test_jovian_full_size_sampled_stage_and_conservation():
     for i in range(2):  # condensates are judged against their vapour's magnitude
         for j in range(2):
             scale[3 + 2 * i + j] = max(scale[3 + 2 * i + j], scale[1 + i])
-    scale[7:10] = scale[7:10].max()  # momentum components against the momentum vector
+    # momentum components against the momentum vector, floored at max(rho) x 1 m/s as in
+    # rel_errs (the column starts at rest)
+    scale[7:10] = max(scale[7:10].max(), scale[:7].sum() * 1.0)
     assert np.all(np.abs(got - want) <= 1e-5 * scale), np.abs(got - want).max(axis=0) / scale
     # one full step conserves dry air and rho e + rho g z (periodic x, y; walls in z)
     ctx.set_state(Y0)

@@ -100,3 +100,23 @@ def test_adjoint_refuses_moist_and_viscous():
     for w in (W.moist_bubble(n=8), W.density_current(nx=16, nz=8)):
         with pytest.raises(RuntimeError):
             Oracle(w).rhs_adjoint(w.Y, np.zeros_like(w.Y))
+
+
+def test_step_adjoint_at_rest_uses_the_average_at_zero_face_velocity():
+    """From rest every face has u* = 0, a kink of the upwind flux; the adjoint takes the mean
+    of both one-sided derivatives, which is what central differences measure."""
+    w = W.warm_bubble(n=12)
+    o = Oracle(w)
+    dt = o.dt_cfl(w.Y, 0.8)
+    rs = np.random.default_rng(34)
+    # perturb temperature only (energy), as a theta perturbation would
+    v = np.zeros(w.Y.shape)
+    v[-1] = rs.normal(size=v[-1].shape) * 1e-2
+    lam = rs.normal(size=w.Y.shape)
+
+    def fd(h):
+        d = (o.step(w.Y + h * v, 1, dt=dt)[0] - o.step(w.Y - h * v, 1, dt=dt)[0]) / (2 * h)
+        return np.sum(lam * d)
+
+    rich = (4.0 * fd(1e-3) - fd(2e-3)) / 3.0  # Richardson: removes the O(h^2) term
+    assert rich == pytest.approx(np.sum(o.step_adjoint(w.Y, dt, lam) * v), rel=1e-6)
