@@ -39,7 +39,8 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=10.0)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--workload", default=WORKLOAD,
-                   choices=[WORKLOAD, "jovian_256x256x128", "ensemble_96"],
+                   choices=[WORKLOAD, "jovian_256x256x128", "ensemble_96",
+                            "ensemble_96_autotuned", "adjoint_256x256"],
                    help="the default is the headline workload; the others print an extra "
                         "measurement line of the same form (3-D moist column, moist ensemble)")
     return p.parse_args()
@@ -56,7 +57,7 @@ def workload(dtype, name=WORKLOAD):
     import workloads as W
     if name == "jovian_256x256x128":
         return [W.jovian(dtype=dtype)]
-    if name == "ensemble_96":
+    if name.startswith("ensemble_96"):
         return W.ensemble()
     return W.density_current(dtype=dtype)
 
@@ -214,6 +215,9 @@ def extra_workload(args, local):
     ctx.set_stream(stream)
     for d, w in enumerate(ws):
         ctx.set_state(w.Y.astype(np.float32), domain=d)
+    tuned = None
+    if args.workload.endswith("_autotuned"):
+        tuned = ctx.autotune(steps=3)
     cells = sum(w.ncells for w in ws)
     nv = ws[0].nv
     for _ in range(args.warmup):
@@ -250,11 +254,57 @@ def extra_workload(args, local):
             "config": {"workload": args.workload, "cells": cells, "nfields": nv,
                        "domains": len(ws), "l2": "inputs larger than L2",
                        "device_checks": {"rc": rc, "flags": flags},
-                       "info": ctx.info()},
+                       "info": ctx.info(), "autotune": tuned},
             "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
                          "frac": ach / peak, "traffic": None, "peak_source": src,
                          "stage_ms": stage_ms, "algorithmic_bytes_per_launch": alg},
             "gpu_launches": 3 * args.steps, "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
+def adjoint_workload(args, local):
+    """Forward and discrete-adjoint cost of the 2-D warm bubble at 256 x 256, 400 steps with a
+    checkpoint every 20 steps, FP64 and FP32 (fixed time step from the initial CFL)."""
+    import torch
+    import workloads as W
+    from paper_1901_02955_gb300 import Context
+    torch.cuda.set_device(local)
+    w = W.adjoint_bubble(n=256)
+    nsteps, every = 400, 20
+    out = {}
+    for dt_name in ("f64", "f32"):
+        ctx = Context(w, dtype=dt_name)
+        ctx.set_state(w.Y)
+        dt = ctx.compute_dt()
+        ctx.step(5, dt_fixed=dt)  # warm-up
+        ctx.set_state(w.Y)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.step(nsteps, dt_fixed=dt)
+        t_fwd = time.perf_counter() - t0
+        ctx.set_state(w.Y)
+        t0 = time.perf_counter()
+        ctx.record(nsteps, every, dt)
+        t_rec = time.perf_counter() - t0
+        lam = np.random.default_rng(1).normal(size=w.Y.shape).astype(
+            np.float32 if dt_name == "f32" else np.float64)
+        lam_d = torch.from_numpy(lam).cuda()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.step_adjoint(nsteps, lam_d)
+        torch.cuda.synchronize()
+        t_adj = time.perf_counter() - t0
+        out[dt_name] = {"forward_ms_per_step": 1e3 * t_fwd / nsteps,
+                        "record_ms_per_step": 1e3 * t_rec / nsteps,
+                        "adjoint_ms_per_step": 1e3 * t_adj / nsteps,
+                        "adjoint_over_forward": t_adj / t_fwd}
+        ctx.close()
+    line = {"metric": "discrete adjoint cost relative to the forward run", "unit": "ratio",
+            "value": out["f32"]["adjoint_over_forward"], "higher_is_better": False,
+            "config": {"workload": "adjoint_bubble_256x256", "steps": nsteps,
+                       "checkpoint_every": every, "cells": w.ncells,
+                       "note": "wall clock incl. host orchestration; adjoint includes the "
+                               "segment recomputation", "results": out}}
     print(json.dumps(line), flush=True)
 
 
@@ -263,6 +313,10 @@ def main():
     rank, world, local = dist_info()
     if args.impl == "reference":
         reference_arm(args, rank)
+        return
+    if args.workload == "adjoint_256x256":
+        if rank == 0:
+            adjoint_workload(args, local)
         return
     if args.workload != WORKLOAD:
         if rank == 0:

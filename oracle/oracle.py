@@ -21,7 +21,12 @@ def lib_path() -> str:
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc into oracle/liboracle.so (plain -O2, no fast-math)."""
+    """Compile the oracle with gcc into oracle/liboracle.so (plain -O2, no fast-math).
+    SNAP_ORACLE_LIB names a prebuilt library to load instead (the mutation test uses it to
+    run the pins against deliberately broken copies of the oracle)."""
+    alt = os.environ.get("SNAP_ORACLE_LIB")
+    if alt:
+        return alt
     out = lib_path()
     if (not force and os.path.exists(out)
             and os.path.getmtime(out) >= max(os.path.getmtime(_SRC), os.path.getmtime(_HDR))):
