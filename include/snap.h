@@ -152,8 +152,9 @@ int snap_saturation_adjust(snap_ctx *ctx, int domain);
 /* Forward run recorded for the adjoint: advances the (single, dry, inviscid) domain by
  * nsteps steps like snap_step, keeping a checkpoint of the state every ckpt_every steps, the
  * final state and the time step of every step. Allocates the checkpoints
- * (nsteps/ckpt_every + 2 state copies), one segment of ckpt_every states, four adjoint
- * vectors and the per-face work arrays of the adjoint. SNAP_ENOTSUP for moist, viscous or
+ * (nsteps/ckpt_every + 2 state copies), one segment of 3 x ckpt_every states, four adjoint
+ * vectors and the per-face work arrays of the adjoint; the adjoint keeps three states per
+ * step of a segment (3 x ckpt_every copies). SNAP_ENOTSUP for moist, viscous or
  * multi-domain contexts. */
 int snap_record(snap_ctx *ctx, int nsteps, int ckpt_every, double dt_fixed);
 

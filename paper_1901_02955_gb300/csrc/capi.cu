@@ -98,6 +98,7 @@ struct snap_ctx {
   std::vector<double> rec_dt;
   void *ckpt = nullptr;       // checkpoints every ckpt_every steps, then the final state
   void *segbuf = nullptr;     // states of one segment
+  double *dt_hist = nullptr;  // device copy of the recorded time steps
   void *lam = nullptr;        // four adjoint vectors
   void *gface = nullptr;      // per-direction face contributions
   size_t gface_off[3] = {0, 0, 0};
@@ -155,6 +156,7 @@ static void release(snap_ctx *ctx) {
   cudaFree(ctx->gsync);
   cudaFree(ctx->ckpt);
   cudaFree(ctx->segbuf);
+  cudaFree(ctx->dt_hist);
   cudaFree(ctx->lam);
   cudaFree(ctx->gface);
   cudaFree(ctx->prof_dev);
@@ -295,6 +297,7 @@ static StageArgs args_of(snap_ctx *ctx, int stage) {
   a.flags = ctx->flags_dev;
   a.max_sweeps = ctx->sweeps_dev;
   a.gsync = ctx->gsync;
+  a.dt_override = -1.0;
   a.ph = ctx->ph;
   // stop tolerance of the adjustment: at least 32 machine epsilons of the arithmetic type
   derive_cst<float>(ctx->ph, 32.0 * 1.1920928955078125e-07, a.cf);
@@ -735,7 +738,10 @@ extern "C" int snap_record(snap_ctx *ctx, int nsteps, int ckpt_every, double dt_
   cudaFree(ctx->segbuf);
   ctx->ckpt = ctx->segbuf = nullptr;
   CK(cudaMalloc(&ctx->ckpt, sb * nck));
-  CK(cudaMalloc(&ctx->segbuf, sb * ckpt_every));
+  CK(cudaMalloc(&ctx->segbuf, sb * 3 * ckpt_every));  // Y^n, stage 0 and stage 1 results
+  cudaFree(ctx->dt_hist);
+  ctx->dt_hist = nullptr;
+  CK(cudaMalloc(&ctx->dt_hist, sizeof(double) * nsteps));
   if (!ctx->lam) CK(cudaMalloc(&ctx->lam, sb * 4));
   if (!ctx->gface) {
     const DomDev &D = ctx->dom[0];
@@ -757,10 +763,13 @@ extern "C" int snap_record(snap_ctx *ctx, int nsteps, int ckpt_every, double dt_
                          cudaMemcpyDeviceToDevice, ctx->stream));
     int rc = snap_step_async(ctx, 1, dt_fixed);
     if (rc) return rc;
-    CK(cudaMemcpyAsync(&ctx->rec_dt[n], ctx->dt_dev, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    // the step's dt stays on the device until the end: no host round trip per step
+    CK(cudaMemcpyAsync(ctx->dt_hist + n, ctx->dt_dev, sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
   }
   CK(cudaMemcpyAsync((char *)ctx->ckpt + sb * (nck - 1), ctx->dom[0].buf[0], sb,
                      cudaMemcpyDeviceToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->rec_dt.data(), ctx->dt_hist, sizeof(double) * nsteps,
+                     cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   ctx->use_graph = keep;
   ctx->rec_steps = nsteps;
@@ -769,12 +778,12 @@ extern "C" int snap_record(snap_ctx *ctx, int nsteps, int ckpt_every, double dt_
 
 // Adjoint of one stage: lam_s = b lam_out + (dL/dY_s)^T (b dt lam_out), and the step's
 // initial-state adjoint lam_n according to mode (see AdjArgs).
-static int adjoint_stage(snap_ctx *ctx, int slot, const void *lo, void *ls, void *ln, double a,
-                         double b, double dt, int mode) {
+static int adjoint_stage(snap_ctx *ctx, const StageArgs &sa, const void *Ys, const void *lo,
+                         void *ls, void *ln, double a, double b, double dt, int mode) {
   AdjArgs A;
   memset(&A, 0, sizeof A);
   A.doms = ctx->doms_dev;
-  A.slot_s = slot;
+  A.Ys = Ys;
   A.lam_out = lo;
   A.lam_s = ls;
   A.lam_n = ln;
@@ -783,22 +792,25 @@ static int adjoint_stage(snap_ctx *ctx, int slot, const void *lo, void *ls, void
   A.dt = dt;
   A.mode = mode;
   A.ph = ctx->ph;
-  StageArgs sa = args_of(ctx, 0);
   A.cf = sa.cf;
   A.cd = sa.cd;
   const DomDev &D = ctx->dom[0];
-  for (int d = 0; d < 3; ++d) A.G[d] = (char *)ctx->gface + ctx->gface_off[d];
+  long long ntot = 0;
   for (int d = 0; d < 3; ++d) {
+    A.G[d] = (char *)ctx->gface + ctx->gface_off[d];
     if (d == 1 && !ctx->three_d) continue;
-    long long nf = (long long)(D.nx + (d == 0)) * (D.ny + (d == 1)) * (D.nz + (d == 2));
-    CK(ctx->adj.face(A, d, nf, ctx->stream));
+    ntot += (long long)(D.nx + (d == 0)) * (D.ny + (d == 1)) * (D.nz + (d == 2));
   }
+  CK(ctx->adj.face(A, ntot, ctx->stream));
   CK(ctx->adj.cell(A, D.ncell, ctx->stream));
   return SNAP_OK;
 }
 
-static int plain_stage(snap_ctx *ctx, int stage) {
-  StageArgs a = args_of(ctx, stage);
+// One forward stage with the recorded time step dt passed in the launch arguments.
+static int plain_stage(snap_ctx *ctx, const StageArgs &base, int stage, double dt) {
+  StageArgs a = base;
+  a.stage = stage;
+  a.dt_override = dt;
   CK(ctx->ks.var[ctx->tv].stage(a, ctx->grid, ctx->stream));
   return SNAP_OK;
 }
@@ -834,28 +846,30 @@ extern "C" int snap_step_adjoint(snap_ctx *ctx, int nsteps, const void *lambda_f
                        nullptr, 1, ctx->stream));
   const int K = ctx->ckpt_every;
   const int nseg = (nsteps + K - 1) / K;
+  const StageArgs base = args_of(ctx, 0);
   int rc = SNAP_OK;
   for (int seg = nseg - 1; seg >= 0 && rc == SNAP_OK; --seg) {
     const int n0 = seg * K, n1 = (n0 + K < nsteps) ? n0 + K : nsteps;
+    // recompute the segment forward, keeping Y^n and both intermediate stages of each step
     CK(cudaMemcpyAsync(D.buf[0], (char *)ctx->ckpt + sb * seg, sb, cudaMemcpyDeviceToDevice, ctx->stream));
     for (int s = n0; s < n1 && rc == SNAP_OK; ++s) {
-      CK(cudaMemcpyAsync((char *)ctx->segbuf + sb * (s - n0), D.buf[0], sb, cudaMemcpyDeviceToDevice, ctx->stream));
-      if (s < n1 - 1) {
-        if ((rc = set_dt_fixed(ctx, ctx->rec_dt[s]))) break;
-        for (int st = 0; st < 3 && rc == SNAP_OK; ++st) rc = plain_stage(ctx, st);
-      }
+      char *slot = (char *)ctx->segbuf + sb * 3 * (s - n0);
+      CK(cudaMemcpyAsync(slot, D.buf[0], sb, cudaMemcpyDeviceToDevice, ctx->stream));
+      const double dt = ctx->rec_dt[s];
+      if ((rc = plain_stage(ctx, base, 0, dt))) break;
+      CK(cudaMemcpyAsync(slot + sb, D.buf[1], sb, cudaMemcpyDeviceToDevice, ctx->stream));
+      if ((rc = plain_stage(ctx, base, 1, dt))) break;
+      CK(cudaMemcpyAsync(slot + 2 * sb, D.buf[2], sb, cudaMemcpyDeviceToDevice, ctx->stream));
+      if (s < n1 - 1) rc = plain_stage(ctx, base, 2, dt);
     }
     for (int s = n1 - 1; s >= n0 && rc == SNAP_OK; --s) {
       const double dt = ctx->rec_dt[s];
-      CK(cudaMemcpyAsync(D.buf[0], (char *)ctx->segbuf + sb * (s - n0), sb, cudaMemcpyDeviceToDevice, ctx->stream));
-      if ((rc = set_dt_fixed(ctx, dt))) break;
-      if ((rc = plain_stage(ctx, 0))) break;  // B1 = Y1
-      if ((rc = plain_stage(ctx, 1))) break;  // B2 = Y2
+      const char *slot = (const char *)ctx->segbuf + sb * 3 * (s - n0);
       // Sec. 4.3 in reverse: Y3 = Y/3 + 2/3 (Y2 + dt L(Y2)), Y2 = 3/4 Y + 1/4 (Y1 + dt L(Y1)),
       // Y1 = Y + dt L(Y)
-      if ((rc = adjoint_stage(ctx, 2, LA, LB, LN, 1.0 / 3.0, 2.0 / 3.0, dt, 2))) break;
-      if ((rc = adjoint_stage(ctx, 1, LB, LC, LN, 0.75, 0.25, dt, 1))) break;
-      if ((rc = adjoint_stage(ctx, 0, LC, LA, LN, 0.0, 1.0, dt, 0))) break;
+      if ((rc = adjoint_stage(ctx, base, slot + 2 * sb, LA, LB, LN, 1.0 / 3.0, 2.0 / 3.0, dt, 2))) break;
+      if ((rc = adjoint_stage(ctx, base, slot + sb, LB, LC, LN, 0.75, 0.25, dt, 1))) break;
+      if ((rc = adjoint_stage(ctx, base, slot, LC, LA, LN, 0.0, 1.0, dt, 0))) break;
     }
   }
   if (rc == SNAP_OK) {
@@ -872,9 +886,7 @@ extern "C" int snap_step_adjoint(snap_ctx *ctx, int nsteps, const void *lambda_f
   // restore the recorded final state
   const int nck = (ctx->rec_steps + K - 1) / K + 1;
   CK(cudaMemcpyAsync(D.buf[0], (char *)ctx->ckpt + sb * (nck - 1), sb, cudaMemcpyDeviceToDevice, ctx->stream));
-  int rc2 = set_dt_fixed(ctx, -1.0);
-  if (!rc) rc = rc2;
-  rc2 = refresh_rate(ctx, 0, ctx->stream);
+  int rc2 = refresh_rate(ctx, 0, ctx->stream);
   if (!rc) rc = rc2;
   CK(cudaStreamSynchronize(ctx->stream));
   return rc;

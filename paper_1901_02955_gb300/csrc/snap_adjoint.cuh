@@ -6,9 +6,10 @@
 // used; the time step is a given constant.
 //
 // Two kernels per stage, deterministic (no atomics):
-//   adj_face_kernel (one launch per direction): one thread per face recomputes the face
-//     states from its six-cell stencil, transposes LMARS and WENO5, and writes the
-//     contribution of the face to each of its six stencil cells into G[d][v][s][face];
+//   adj_face_kernel (one launch for the faces of every direction): one thread per face
+//     recomputes the face states from its six-cell stencil, transposes LMARS and WENO5, and
+//     writes the contribution of the face to each of its six stencil cells into
+//     G[d][v][s][face];
 //   adj_cell_kernel: one thread per cell gathers the contributions of every face whose
 //     stencil holds the cell (or a ghost image of it), transposes the primitive map and the
 //     gravity source, and forms the stage combine.
@@ -172,22 +173,31 @@ __device__ __forceinline__ void dry_prim(const CstT<R> &C, const R *y, R *x) {
 }
 
 template <class R, class L>
-__global__ void __launch_bounds__(128) adj_face_kernel(const AdjArgs a, int d) {
+__global__ void __launch_bounds__(128) adj_face_kernel(const AdjArgs a) {
   constexpr int NV = L::NV;
   const DomDev &D = a.doms[0];
   const CstT<R> &C = acst<R>(a);
-  const int fx = d == 0, fy = d == 1, fz = d == 2;
   const int nx = D.nx, ny = D.ny, nz = D.nz;
-  const int nfx = nx + fx, nfy = ny + fy, nfz = nz + fz;
-  const long long nf = (long long)nfx * nfy * nfz, ncell = D.ncell;
-  const R *Ys = reinterpret_cast<const R *>(D.buf[a.slot_s]);
+  const long long ncell = D.ncell;
+  const long long nfd[3] = {(long long)(nx + 1) * ny * nz,
+                            L::D3 ? (long long)nx * (ny + 1) * nz : 0ll,
+                            (long long)nx * ny * (nz + 1)};
+  const long long ntot = nfd[0] + nfd[1] + nfd[2];
+  const R *Ys = reinterpret_cast<const R *>(a.Ys);
   const R *lo = reinterpret_cast<const R *>(a.lam_out);
-  R *G = reinterpret_cast<R *>(a.G[d]);
-  const R ih = Prof<R>::ih(D, d), bdt = R(a.b * a.dt), grav = Prof<R>::grav(D);
-  const int nd = d == 0 ? nx : (d == 1 ? ny : nz);
-  const int bclo = D.bc[2 * d], bchi = D.bc[2 * d + 1];
-  for (long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x; f < nf;
-       f += (long long)gridDim.x * blockDim.x) {
+  const R bdt = R(a.b * a.dt), grav = Prof<R>::grav(D);
+  for (long long gf = blockIdx.x * (long long)blockDim.x + threadIdx.x; gf < ntot;
+       gf += (long long)gridDim.x * blockDim.x) {
+    // faces of x, then y, then z
+    const int d = gf < nfd[0] ? 0 : (gf < nfd[0] + nfd[1] ? 1 : 2);
+    const long long f = gf - (d == 0 ? 0 : (d == 1 ? nfd[0] : nfd[0] + nfd[1]));
+    const long long nf = nfd[d];
+    const int fx = d == 0, fy = d == 1, fz = d == 2;
+    const int nfx = nx + fx, nfy = ny + fy;
+    R *G = reinterpret_cast<R *>(a.G[d]);
+    const R ih = Prof<R>::ih(D, d);
+    const int nd = d == 0 ? nx : (d == 1 ? ny : nz);
+    const int bclo = D.bc[2 * d], bchi = D.bc[2 * d + 1];
     const int i = int(f % nfx), j = int((f / nfx) % nfy), k = int(f / ((long long)nfx * nfy));
     const int pos = d == 0 ? i : (d == 1 ? j : k);
     // Fbar = (mu_right - mu_left) / h with mu = b dt lam_out, plus the gravity-energy term
@@ -259,7 +269,7 @@ __global__ void __launch_bounds__(256) adj_cell_kernel(const AdjArgs a) {
   const CstT<R> &C = acst<R>(a);
   const int nx = D.nx, ny = D.ny, nz = D.nz;
   const long long ncell = D.ncell;
-  const R *Ys = reinterpret_cast<const R *>(D.buf[a.slot_s]);
+  const R *Ys = reinterpret_cast<const R *>(a.Ys);
   const R *lo = reinterpret_cast<const R *>(a.lam_out);
   R *ls = reinterpret_cast<R *>(a.lam_s);
   R *ln = reinterpret_cast<R *>(a.lam_n);
@@ -351,9 +361,9 @@ __global__ void __launch_bounds__(256) adj_cell_kernel(const AdjArgs a) {
 
 template <class R, class L>
 struct AdjFamily {
-  static cudaError_t face(const AdjArgs &a, int d, long long nfaces, cudaStream_t s) {
+  static cudaError_t face(const AdjArgs &a, long long nfaces, cudaStream_t s) {
     long long g = (nfaces + 127) / 128;
-    adj_face_kernel<R, L><<<int(g < 4864 ? g : 4864), 128, 0, s>>>(a, d);
+    adj_face_kernel<R, L><<<int(g < 9728 ? g : 9728), 128, 0, s>>>(a);
     return cudaGetLastError();
   }
   static cudaError_t cell(const AdjArgs &a, long long ncell, cudaStream_t s) {

@@ -80,6 +80,7 @@ struct StageArgs {
   unsigned int *flags;       // bit 0 non-finite, bit 1 no convergence
   int *max_sweeps;
   GridSync *gsync;           // persistent step kernel only
+  double dt_override;        // > 0: time step of this launch, before any domain setting
   Phys ph;
   CstT<float> cf;
   CstT<double> cd;
@@ -114,7 +115,7 @@ struct KernelSet {
 // Arguments of the adjoint kernels of one stage (dry, inviscid, single domain).
 struct AdjArgs {
   const DomDev *doms;
-  int slot_s;            // buffer slot of the stage input state
+  const void *Ys;        // stage input state (context type, stored layout)
   const void *lam_out;   // adjoint of the stage output (context type, state layout)
   void *lam_s;           // adjoint of the stage input (written)
   void *lam_n;           // accumulator of the adjoint of the step's initial state
@@ -127,7 +128,8 @@ struct AdjArgs {
 };
 
 struct AdjKernels {
-  cudaError_t (*face)(const AdjArgs &, int d, long long nfaces, cudaStream_t);
+  // faces of every direction in one launch (nfaces: total over the directions)
+  cudaError_t (*face)(const AdjArgs &, long long nfaces, cudaStream_t);
   cudaError_t (*cell)(const AdjArgs &, long long ncell, cudaStream_t);
 };
 

@@ -671,7 +671,8 @@ __device__ __forceinline__ void stage_tiles(const StageArgs &a, const int stage,
     if (tid == 0) {
       double dt;
       if (stage == 0) {
-        dt = D.dt_fixed > 0.0 ? D.dt_fixed : D.cfl / __longlong_as_double((long long)*D.rate);
+        dt = a.dt_override > 0.0 ? a.dt_override
+             : (D.dt_fixed > 0.0 ? D.dt_fixed : D.cfl / __longlong_as_double((long long)*D.rate));
         if (lt == 0) *D.dt_step = dt;
       } else {
         dt = *(volatile double *)D.dt_step;
