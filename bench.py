@@ -43,6 +43,8 @@ def parse():
                             "ensemble_96_autotuned", "adjoint_256x256"],
                    help="the default is the headline workload; the others print an extra "
                         "measurement line of the same form (3-D moist column, moist ensemble)")
+    p.add_argument("--adjoint-steps", type=int, default=400,
+                   help="steps of the forward and adjoint runs of the adjoint workload")
     return p.parse_args()
 
 
@@ -270,7 +272,7 @@ def adjoint_workload(args, local):
     from paper_1901_02955_gb300 import Context
     torch.cuda.set_device(local)
     w = W.adjoint_bubble(n=256)
-    nsteps, every = 400, 20
+    nsteps, every = args.adjoint_steps, 20
     out = {}
     for dt_name in ("f64", "f32"):
         ctx = Context(w, dtype=dt_name)
@@ -282,29 +284,37 @@ def adjoint_workload(args, local):
         t0 = time.perf_counter()
         ctx.step(nsteps, dt_fixed=dt)
         t_fwd = time.perf_counter() - t0
-        ctx.set_state(w.Y)
-        t0 = time.perf_counter()
-        ctx.record(nsteps, every, dt)
-        t_rec = time.perf_counter() - t0
+        res = {"forward_ms_per_step": 1e3 * t_fwd / nsteps}
         lam = np.random.default_rng(1).normal(size=w.Y.shape).astype(
             np.float32 if dt_name == "f32" else np.float64)
         lam_d = torch.from_numpy(lam).cuda()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        ctx.step_adjoint(nsteps, lam_d)
-        torch.cuda.synchronize()
-        t_adj = time.perf_counter() - t0
-        out[dt_name] = {"forward_ms_per_step": 1e3 * t_fwd / nsteps,
-                        "record_ms_per_step": 1e3 * t_rec / nsteps,
-                        "adjoint_ms_per_step": 1e3 * t_adj / nsteps,
-                        "adjoint_over_forward": t_adj / t_fwd}
+        # every: checkpoints and recomputation; 0: every stage input kept by the record
+        for mode, k in (("checkpointed", every), ("stored", 0)):
+            ctx.set_state(w.Y)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ctx.record(nsteps, k, dt)
+            t_rec = time.perf_counter() - t0
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ctx.step_adjoint(nsteps, lam_d)
+            torch.cuda.synchronize()
+            t_adj = time.perf_counter() - t0
+            res[mode] = {"checkpoint_every": k,
+                         "record_ms_per_step": 1e3 * t_rec / nsteps,
+                         "adjoint_ms_per_step": 1e3 * t_adj / nsteps,
+                         "adjoint_over_forward": t_adj / t_fwd}
+        out[dt_name] = res
         ctx.close()
     line = {"metric": "discrete adjoint cost relative to the forward run", "unit": "ratio",
-            "value": out["f32"]["adjoint_over_forward"], "higher_is_better": False,
+            "value": out["f32"]["checkpointed"]["adjoint_over_forward"],
+            "higher_is_better": False,
             "config": {"workload": "adjoint_bubble_256x256", "steps": nsteps,
                        "checkpoint_every": every, "cells": w.ncells,
-                       "note": "wall clock incl. host orchestration; adjoint includes the "
-                               "segment recomputation", "results": out}}
+                       "note": "wall clock incl. host orchestration; value: FP32 with "
+                               "checkpoints, the adjoint including the segment "
+                               "recomputation; 'stored' keeps every stage input instead",
+                       "results": out}}
     print(json.dumps(line), flush=True)
 
 

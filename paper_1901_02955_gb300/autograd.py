@@ -2,7 +2,8 @@
 
 SnapSteps.apply(Y0, context, nsteps, ckpt_every, dt_fixed) advances a conserved state by
 nsteps steps in the CUDA library and returns Y_N; its backward is the library's hand-written
-adjoint of those steps (checkpointed every ckpt_every steps, recomputed in between). The
+adjoint of those steps (checkpointed every ckpt_every steps and recomputed in between, or,
+with ckpt_every = 0, every stage input kept so that nothing is recomputed). The
 forward and the adjoint both run in the library's kernels; torch only holds the tensors.
 Dry, inviscid, single-domain contexts (the library returns SNAP_ENOTSUP otherwise)."""
 import torch

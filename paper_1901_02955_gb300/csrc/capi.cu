@@ -727,18 +727,33 @@ static size_t state_bytes_dom0(snap_ctx *ctx) {
   return (size_t)ctx->dom[0].ncell * ctx->nv * ctx->word;
 }
 
+// One forward stage; dt > 0 is passed in the launch arguments (the recorded time step).
+static int plain_stage(snap_ctx *ctx, const StageArgs &base, int stage, double dt) {
+  StageArgs a = base;
+  a.stage = stage;
+  a.dt_override = dt;
+  CK(ctx->ks.var[ctx->tv].stage(a, ctx->grid, ctx->stream));
+  return SNAP_OK;
+}
+
 extern "C" int snap_record(snap_ctx *ctx, int nsteps, int ckpt_every, double dt_fixed) {
   if (!ctx) return fail(nullptr, SNAP_EINVAL, "snap_record: NULL context");
   if (!ctx->has_adj)
     return fail(ctx, SNAP_ENOTSUP, "snap_record: the adjoint is built for one dry, inviscid domain");
-  if (nsteps < 1 || ckpt_every < 1) return fail(ctx, SNAP_EINVAL, "snap_record: nsteps and ckpt_every must be >= 1");
+  if (nsteps < 1 || ckpt_every < 0)
+    return fail(ctx, SNAP_EINVAL, "snap_record: nsteps must be >= 1 and ckpt_every >= 0");
   const size_t sb = state_bytes_dom0(ctx);
-  const int nck = (nsteps + ckpt_every - 1) / ckpt_every + 1;
+  const bool store_all = ckpt_every == 0;
+  // store_all: the final state only; else every ckpt_every-th state and the final one
+  const int nck = store_all ? 1 : (nsteps + ckpt_every - 1) / ckpt_every + 1;
+  const int nseg_states = store_all ? nsteps : ckpt_every;
+  ctx->rec_steps = 0;
   cudaFree(ctx->ckpt);
   cudaFree(ctx->segbuf);
   ctx->ckpt = ctx->segbuf = nullptr;
   CK(cudaMalloc(&ctx->ckpt, sb * nck));
-  CK(cudaMalloc(&ctx->segbuf, sb * 3 * ckpt_every));  // Y^n, stage 0 and stage 1 results
+  // per step: the inputs of its three stages (Y^n and the results of stages 0 and 1)
+  CK(cudaMalloc(&ctx->segbuf, sb * 3 * nseg_states));
   cudaFree(ctx->dt_hist);
   ctx->dt_hist = nullptr;
   CK(cudaMalloc(&ctx->dt_hist, sizeof(double) * nsteps));
@@ -757,12 +772,28 @@ extern "C" int snap_record(snap_ctx *ctx, int nsteps, int ckpt_every, double dt_
   ctx->rec_dt.assign(nsteps, 0.0);
   ctx->ckpt_every = ckpt_every;
   const int keep = ctx->use_graph;
-  for (int n = 0; n < nsteps; ++n) {
-    if (n % ckpt_every == 0)
-      CK(cudaMemcpyAsync((char *)ctx->ckpt + sb * (n / ckpt_every), ctx->dom[0].buf[0], sb,
-                         cudaMemcpyDeviceToDevice, ctx->stream));
-    int rc = snap_step_async(ctx, 1, dt_fixed);
+  const StageArgs base = args_of(ctx, 0);
+  if (store_all) {
+    int rc = set_dt_fixed(ctx, dt_fixed);
     if (rc) return rc;
+  }
+  for (int n = 0; n < nsteps; ++n) {
+    if (store_all) {
+      // three launches per step, each stage's input kept in the record
+      const DomDev &D = ctx->dom[0];
+      char *slot = (char *)ctx->segbuf + sb * 3 * n;
+      for (int st = 0; st < 3; ++st) {
+        CK(cudaMemcpyAsync(slot + sb * st, D.buf[st], sb, cudaMemcpyDeviceToDevice, ctx->stream));
+        int rc = plain_stage(ctx, base, st, -1.0);
+        if (rc) return rc;
+      }
+    } else {
+      if (n % ckpt_every == 0)
+        CK(cudaMemcpyAsync((char *)ctx->ckpt + sb * (n / ckpt_every), ctx->dom[0].buf[0], sb,
+                           cudaMemcpyDeviceToDevice, ctx->stream));
+      int rc = snap_step_async(ctx, 1, dt_fixed);
+      if (rc) return rc;
+    }
     // the step's dt stays on the device until the end: no host round trip per step
     CK(cudaMemcpyAsync(ctx->dt_hist + n, ctx->dt_dev, sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
   }
@@ -806,14 +837,6 @@ static int adjoint_stage(snap_ctx *ctx, const StageArgs &sa, const void *Ys, con
   return SNAP_OK;
 }
 
-// One forward stage with the recorded time step dt passed in the launch arguments.
-static int plain_stage(snap_ctx *ctx, const StageArgs &base, int stage, double dt) {
-  StageArgs a = base;
-  a.stage = stage;
-  a.dt_override = dt;
-  CK(ctx->ks.var[ctx->tv].stage(a, ctx->grid, ctx->stream));
-  return SNAP_OK;
-}
 
 extern "C" int snap_step_adjoint(snap_ctx *ctx, int nsteps, const void *lambda_final,
                                  void *lambda_init, int dtype, void *stream) {
@@ -844,15 +867,17 @@ extern "C" int snap_step_adjoint(snap_ctx *ctx, int nsteps, const void *lambda_f
   // an adjoint vector has no reference offset: plain type conversion
   CK(launch_state_copy(src, in_f32, LA, ctx->f32, ctx->nv, D.ncell, (long long)D.nx * D.ny,
                        nullptr, 1, ctx->stream));
-  const int K = ctx->ckpt_every;
+  const bool store_all = ctx->ckpt_every == 0;
+  const int K = store_all ? nsteps : ctx->ckpt_every;
   const int nseg = (nsteps + K - 1) / K;
   const StageArgs base = args_of(ctx, 0);
   int rc = SNAP_OK;
   for (int seg = nseg - 1; seg >= 0 && rc == SNAP_OK; --seg) {
     const int n0 = seg * K, n1 = (n0 + K < nsteps) ? n0 + K : nsteps;
     // recompute the segment forward, keeping Y^n and both intermediate stages of each step
-    CK(cudaMemcpyAsync(D.buf[0], (char *)ctx->ckpt + sb * seg, sb, cudaMemcpyDeviceToDevice, ctx->stream));
-    for (int s = n0; s < n1 && rc == SNAP_OK; ++s) {
+    if (!store_all)
+      CK(cudaMemcpyAsync(D.buf[0], (char *)ctx->ckpt + sb * seg, sb, cudaMemcpyDeviceToDevice, ctx->stream));
+    for (int s = n0; s < n1 && rc == SNAP_OK && !store_all; ++s) {
       char *slot = (char *)ctx->segbuf + sb * 3 * (s - n0);
       CK(cudaMemcpyAsync(slot, D.buf[0], sb, cudaMemcpyDeviceToDevice, ctx->stream));
       const double dt = ctx->rec_dt[s];
@@ -884,7 +909,7 @@ extern "C" int snap_step_adjoint(snap_ctx *ctx, int nsteps, const void *lambda_f
     if (!dev_out) CK(cudaMemcpyAsync(lambda_init, ctx->staging, n * iw, cudaMemcpyDeviceToHost, ctx->stream));
   }
   // restore the recorded final state
-  const int nck = (ctx->rec_steps + K - 1) / K + 1;
+  const int nck = store_all ? 1 : (ctx->rec_steps + K - 1) / K + 1;
   CK(cudaMemcpyAsync(D.buf[0], (char *)ctx->ckpt + sb * (nck - 1), sb, cudaMemcpyDeviceToDevice, ctx->stream));
   int rc2 = refresh_rate(ctx, 0, ctx->stream);
   if (!rc) rc = rc2;

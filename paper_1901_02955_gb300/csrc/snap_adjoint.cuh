@@ -172,102 +172,158 @@ __device__ __forceinline__ void dry_prim(const CstT<R> &C, const R *y, R *x) {
   x[L::IE] = C.gm1 * (y[L::IE] - R(0.5) * K);
 }
 
+// Adjoint of face f of direction DIR (face index in [nz'][ny'][nx'] order of that direction).
+template <class R, class L, int DIR>
+__device__ __forceinline__ void adj_face(const AdjArgs &a, const DomDev &D, const CstT<R> &C,
+                                         long long f) {
+  constexpr int NV = L::NV, MN = L::mom(DIR);
+  constexpr int fx = DIR == 0, fy = DIR == 1, fz = DIR == 2;
+  const int nx = D.nx, ny = D.ny, nz = D.nz;
+  const long long ncell = D.ncell;
+  const int nfx = nx + fx, nfy = ny + fy;
+  const long long nf = (long long)nfx * nfy * (nz + fz);
+  const R *Ys = reinterpret_cast<const R *>(a.Ys);
+  const R *lo = reinterpret_cast<const R *>(a.lam_out);
+  R *G = reinterpret_cast<R *>(a.G[DIR]);
+  const R bdt = R(a.b * a.dt), ih = Prof<R>::ih(D, DIR);
+  const int nd = DIR == 0 ? nx : (DIR == 1 ? ny : nz);
+  const int bclo = D.bc[2 * DIR], bchi = D.bc[2 * DIR + 1];
+  const int i = int(f % nfx), j = int((f / nfx) % nfy), k = int(f / ((long long)nfx * nfy));
+  const int pos = DIR == 0 ? i : (DIR == 1 ? j : k);
+  // Fbar = (mu_right - mu_left) / h with mu = b dt lam_out, plus the gravity-energy term
+  R Fb[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) Fb[v] = R(0);
+  R Fbz = R(0);
+  if (pos > 0) {
+    const long long c = ((long long)(k - fz) * ny + (j - fy)) * nx + (i - fx);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) Fb[v] -= bdt * lo[v * ncell + c] * ih;
+    if (fz) Fbz -= R(0.5) * Prof<R>::grav(D) * bdt * lo[L::IE * ncell + c];
+  }
+  if (pos < nd) {
+    const long long c = ((long long)k * ny + j) * nx + i;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) Fb[v] += bdt * lo[v * ncell + c] * ih;
+    if (fz) Fbz -= R(0.5) * Prof<R>::grav(D) * bdt * lo[L::IE * ncell + c];
+  }
+  if (fz) {
+#pragma unroll
+    for (int s = 0; s < L::IM0; ++s) Fb[s] += Fbz;
+  }
+  // stencil primitives, cells pos-3 .. pos+2 along DIR (ghosts mirrored or wrapped)
+  R X[6][NV];
+#pragma unroll
+  for (int s = 0; s < 6; ++s) {
+    bool flip = false;
+    const int p = map_index(pos - 3 + s, nd, bclo, bchi, flip);
+    const int ci = fx ? p : i, cj = fy ? p : j, ck = fz ? p : k;
+    const long long c = ((long long)ck * ny + cj) * nx + ci;
+    R y[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) y[v] = Ys[v * ncell + c];
+    dry_prim<R, L>(C, y, X[s]);
+    if (flip) X[s][MN] = -X[s][MN];
+  }
+  R QL[NV], QR[NV], gL[NV][5], gR[NV][5], QLb[NV], QRb[NV];
+  const R weps = C.weno_eps;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    R q[5];
+#pragma unroll
+    for (int s = 0; s < 5; ++s) q[s] = X[s][v];
+    QL[v] = weno5_grad<R>(q, weps, gL[v]);
+#pragma unroll
+    for (int s = 0; s < 5; ++s) q[s] = X[5 - s][v];
+    QR[v] = weno5_grad<R>(q, weps, gR[v]);
+    QLb[v] = QRb[v] = R(0);
+  }
+  const R pref = fz ? Prof<R>::pf(D, k) : Prof<R>::pc(D, k);
+  lmars_adj<R, L>(C, QL, QR, DIR, pref, Fb, QLb, QRb);
+#pragma unroll
+  for (int v = 0; v < NV; ++v)
+#pragma unroll
+    for (int s = 0; s < 6; ++s) {
+      R g = R(0);
+      if (s <= 4) g += QLb[v] * gL[v][s];
+      if (s >= 1) g += QRb[v] * gR[v][5 - s];
+      G[((long long)v * 6 + s) * nf + f] = g;
+    }
+}
+
+// One thread per face; the faces of x, then y (3-D), then z.
 template <class R, class L>
 __global__ void __launch_bounds__(128) adj_face_kernel(const AdjArgs a) {
-  constexpr int NV = L::NV;
   const DomDev &D = a.doms[0];
   const CstT<R> &C = acst<R>(a);
   const int nx = D.nx, ny = D.ny, nz = D.nz;
-  const long long ncell = D.ncell;
-  const long long nfd[3] = {(long long)(nx + 1) * ny * nz,
-                            L::D3 ? (long long)nx * (ny + 1) * nz : 0ll,
-                            (long long)nx * ny * (nz + 1)};
-  const long long ntot = nfd[0] + nfd[1] + nfd[2];
-  const R *Ys = reinterpret_cast<const R *>(a.Ys);
-  const R *lo = reinterpret_cast<const R *>(a.lam_out);
-  const R bdt = R(a.b * a.dt), grav = Prof<R>::grav(D);
+  const long long n0 = (long long)(nx + 1) * ny * nz;
+  const long long n1 = L::D3 ? (long long)nx * (ny + 1) * nz : 0ll;
+  const long long ntot = n0 + n1 + (long long)nx * ny * (nz + 1);
   for (long long gf = blockIdx.x * (long long)blockDim.x + threadIdx.x; gf < ntot;
        gf += (long long)gridDim.x * blockDim.x) {
-    // faces of x, then y, then z
-    const int d = gf < nfd[0] ? 0 : (gf < nfd[0] + nfd[1] ? 1 : 2);
-    const long long f = gf - (d == 0 ? 0 : (d == 1 ? nfd[0] : nfd[0] + nfd[1]));
-    const long long nf = nfd[d];
-    const int fx = d == 0, fy = d == 1, fz = d == 2;
-    const int nfx = nx + fx, nfy = ny + fy;
-    R *G = reinterpret_cast<R *>(a.G[d]);
-    const R ih = Prof<R>::ih(D, d);
-    const int nd = d == 0 ? nx : (d == 1 ? ny : nz);
-    const int bclo = D.bc[2 * d], bchi = D.bc[2 * d + 1];
-    const int i = int(f % nfx), j = int((f / nfx) % nfy), k = int(f / ((long long)nfx * nfy));
-    const int pos = d == 0 ? i : (d == 1 ? j : k);
-    // Fbar = (mu_right - mu_left) / h with mu = b dt lam_out, plus the gravity-energy term
-    R Fb[NV];
-#pragma unroll
-    for (int v = 0; v < NV; ++v) Fb[v] = R(0);
-    R Fbz = R(0);
-    if (pos > 0) {
-      const long long c = ((long long)(k - fz) * ny + (j - fy)) * nx + (i - fx);
-#pragma unroll
-      for (int v = 0; v < NV; ++v) Fb[v] -= bdt * lo[v * ncell + c] * ih;
-      if (fz) Fbz -= R(0.5) * grav * bdt * lo[L::IE * ncell + c];
+    if (gf < n0) {
+      adj_face<R, L, 0>(a, D, C, gf);
+    } else if (L::D3 && gf < n0 + n1) {
+      if constexpr (L::D3) adj_face<R, L, 1>(a, D, C, gf - n0);
+    } else {
+      adj_face<R, L, 2>(a, D, C, gf - n0 - n1);
     }
-    if (pos < nd) {
-      const long long c = ((long long)k * ny + j) * nx + i;
+  }
+}
+
+// Adds to Xb the contributions of the faces of direction DIR whose stencil slot holds the
+// position ipos along DIR (the cell itself or a ghost image of it), with the normal velocity
+// entry multiplied by sg (-1 for a mirror image).
+template <class R, class L, int DIR>
+__device__ __forceinline__ void gather_image(const AdjArgs &a, const DomDev &D, int i, int j,
+                                             int k, int ipos, R sg, R (&Xb)[L::NV]) {
+  constexpr int fx = DIR == 0, fy = DIR == 1, fz = DIR == 2, MN = L::mom(DIR);
+  const int nx = D.nx, ny = D.ny, nz = D.nz;
+  const int nfx = nx + fx, nfy = ny + fy;
+  const long long nf = (long long)nfx * nfy * (nz + fz);
+  const int nd = DIR == 0 ? nx : (DIR == 1 ? ny : nz);
+  const R *G = reinterpret_cast<const R *>(a.G[DIR]);
 #pragma unroll
-      for (int v = 0; v < NV; ++v) Fb[v] += bdt * lo[v * ncell + c] * ih;
-      if (fz) Fbz -= R(0.5) * grav * bdt * lo[L::IE * ncell + c];
+  for (int s = 0; s < 6; ++s) {
+    const int fpos = ipos + 3 - s;  // face whose stencil slot s is this position
+    if (fpos < 0 || fpos > nd) continue;
+    const int fi = fx ? fpos : i, fj = fy ? fpos : j, fk = fz ? fpos : k;
+    const long long f = ((long long)fk * nfy + fj) * nfx + fi;
+#pragma unroll
+    for (int v = 0; v < L::NV; ++v) {
+      const R g = G[((long long)v * 6 + s) * nf + f];
+      Xb[v] += v == MN ? sg * g : g;
     }
-    if (fz) {
-#pragma unroll
-      for (int s = 0; s < L::IM0; ++s) Fb[s] += Fbz;
-    }
-    // stencil primitives, cells pos-3 .. pos+2 along d (ghosts mirrored or wrapped)
-    R X[6][NV];
-#pragma unroll
-    for (int s = 0; s < 6; ++s) {
-      bool flip = false;
-      const int p = map_index(pos - 3 + s, nd, bclo, bchi, flip);
-      const int ci = fx ? p : i, cj = fy ? p : j, ck = fz ? p : k;
-      const long long c = ((long long)ck * ny + cj) * nx + ci;
-      R y[NV];
-#pragma unroll
-      for (int v = 0; v < NV; ++v) y[v] = Ys[v * ncell + c];
-      dry_prim<R, L>(C, y, X[s]);
-      if (flip) X[s][L::mom(d)] = -X[s][L::mom(d)];
-    }
-    R QL[NV], QR[NV], gL[NV][5], gR[NV][5], QLb[NV], QRb[NV];
-    const R weps = C.weno_eps;
-#pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      R q[5];
-#pragma unroll
-      for (int s = 0; s < 5; ++s) q[s] = X[s][v];
-      QL[v] = weno5_grad<R>(q, weps, gL[v]);
-#pragma unroll
-      for (int s = 0; s < 5; ++s) q[s] = X[5 - s][v];
-      QR[v] = weno5_grad<R>(q, weps, gR[v]);
-      QLb[v] = QRb[v] = R(0);
-    }
-    const R pref = fz ? Prof<R>::pf(D, k) : Prof<R>::pc(D, k);
-    lmars_adj<R, L>(C, QL, QR, d, pref, Fb, QLb, QRb);
-#pragma unroll
-    for (int v = 0; v < NV; ++v)
-#pragma unroll
-      for (int s = 0; s < 6; ++s) {
-        R g = R(0);
-        if (s <= 4) g += QLb[v] * gL[v][s];
-        if (s >= 1) g += QRb[v] * gR[v][5 - s];
-        G[((long long)v * 6 + s) * nf + f] = g;
-      }
+  }
+}
+
+template <class R, class L, int DIR>
+__device__ __forceinline__ void gather_dir(const AdjArgs &a, const DomDev &D, int i, int j,
+                                           int k, R (&Xb)[L::NV]) {
+  const int nd = DIR == 0 ? D.nx : (DIR == 1 ? D.ny : D.nz);
+  const int pos = DIR == 0 ? i : (DIR == 1 ? j : k);
+  const int bclo = D.bc[2 * DIR], bchi = D.bc[2 * DIR + 1];
+  gather_image<R, L, DIR>(a, D, i, j, k, pos, R(1), Xb);
+  // ghost images within three cells of a boundary: a periodic copy, or a mirror image
+  if (bclo == 1) {
+    if (pos - nd >= -3) gather_image<R, L, DIR>(a, D, i, j, k, pos - nd, R(1), Xb);
+  } else if (pos <= 2) {
+    gather_image<R, L, DIR>(a, D, i, j, k, -1 - pos, R(-1), Xb);
+  }
+  if (bchi == 1) {
+    if (pos + nd <= nd + 2) gather_image<R, L, DIR>(a, D, i, j, k, pos + nd, R(1), Xb);
+  } else if (pos >= nd - 3) {
+    gather_image<R, L, DIR>(a, D, i, j, k, 2 * nd - 1 - pos, R(-1), Xb);
   }
 }
 
 template <class R, class L>
-__global__ void __launch_bounds__(256) adj_cell_kernel(const AdjArgs a) {
+__global__ void __launch_bounds__(128) adj_cell_kernel(const AdjArgs a) {
   constexpr int NV = L::NV, IE = L::IE, IM0 = L::IM0;
   const DomDev &D = a.doms[0];
   const CstT<R> &C = acst<R>(a);
-  const int nx = D.nx, ny = D.ny, nz = D.nz;
+  const int nx = D.nx, ny = D.ny;
   const long long ncell = D.ncell;
   const R *Ys = reinterpret_cast<const R *>(a.Ys);
   const R *lo = reinterpret_cast<const R *>(a.lam_out);
@@ -280,51 +336,9 @@ __global__ void __launch_bounds__(256) adj_cell_kernel(const AdjArgs a) {
     R Xb[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) Xb[v] = R(0);
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      if (d == 1 && !L::D3) continue;
-      const int fx = d == 0, fy = d == 1, fz = d == 2;
-      const int nfx = nx + fx, nfy = ny + fy, nfz = nz + fz;
-      const long long nf = (long long)nfx * nfy * nfz;
-      const R *G = reinterpret_cast<const R *>(a.G[d]);
-      const int nd = d == 0 ? nx : (d == 1 ? ny : nz);
-      const int pos = d == 0 ? i : (d == 1 ? j : k);
-      const int bclo = D.bc[2 * d], bchi = D.bc[2 * d + 1];
-      // the cell itself and its ghost images along d (a ghost of the cell carries its
-      // values, with the normal velocity negated when mirrored)
-      int img[3];
-      R sgn[3];
-      int nimg = 0;
-      img[nimg] = pos;
-      sgn[nimg++] = R(1);
-      if (bclo == 1) {
-        if (pos - nd >= -3) { img[nimg] = pos - nd; sgn[nimg++] = R(1); }
-      } else if (-1 - pos >= -3) {
-        img[nimg] = -1 - pos;
-        sgn[nimg++] = R(-1);
-      }
-      if (bchi == 1) {
-        if (pos + nd <= nd + 2) { img[nimg] = pos + nd; sgn[nimg++] = R(1); }
-      } else if (2 * nd - 1 - pos <= nd + 2) {
-        img[nimg] = 2 * nd - 1 - pos;
-        sgn[nimg++] = R(-1);
-      }
-      for (int m = 0; m < nimg; ++m) {
-#pragma unroll
-        for (int s = 0; s < 6; ++s) {
-          const int fpos = img[m] + 3 - s;  // face whose stencil slot s is this position
-          if (fpos < 0 || fpos > nd) continue;
-          const int fi = fx ? fpos : i, fj = fy ? fpos : j, fk = fz ? fpos : k;
-          const long long f = ((long long)fk * nfy + fj) * nfx + fi;
-#pragma unroll
-          for (int v = 0; v < NV; ++v) {
-            R g = G[((long long)v * 6 + s) * nf + f];
-            if (v == L::mom(d)) g *= sgn[m];
-            Xb[v] += g;
-          }
-        }
-      }
-    }
+    gather_dir<R, L, 0>(a, D, i, j, k, Xb);
+    if constexpr (L::D3) gather_dir<R, L, 1>(a, D, i, j, k, Xb);
+    gather_dir<R, L, 2>(a, D, i, j, k, Xb);
     // transpose of the primitive map and of the gravity source
     R y[NV], Yb[NV];
 #pragma unroll
@@ -341,7 +355,6 @@ __global__ void __launch_bounds__(256) adj_cell_kernel(const AdjArgs a) {
     r0 += Xb[IE] * C.gm1 * R(0.5) * u2;
     Yb[0] = r0 - grav * bdt * lo[L::mom(2) * ncell + c];
     Yb[IE] = Xb[IE] * C.gm1;
-    (void)k;
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       const R l = lo[v * ncell + c];
@@ -367,8 +380,8 @@ struct AdjFamily {
     return cudaGetLastError();
   }
   static cudaError_t cell(const AdjArgs &a, long long ncell, cudaStream_t s) {
-    long long g = (ncell + 255) / 256;
-    adj_cell_kernel<R, L><<<int(g < 2432 ? g : 2432), 256, 0, s>>>(a);
+    long long g = (ncell + 127) / 128;
+    adj_cell_kernel<R, L><<<int(g < 9728 ? g : 9728), 128, 0, s>>>(a);
     return cudaGetLastError();
   }
   static AdjKernels get() {

@@ -66,13 +66,34 @@ def test_checkpoint_spacing_does_not_change_the_adjoint(torch):
     w = cases()["bubble_walls_ragged"]
     dt = Oracle(w).dt_cfl(w.Y, 0.8)
     lam = np.random.default_rng(42).normal(size=w.Y.shape)
-    outs = []
-    for k in (1, 3, 7):
+    outs, finals = [], []
+    for k in (1, 3, 7, 0):  # 0: every stage input kept, nothing recomputed
         ctx = Context(w, dtype="f64")
         ctx.set_state(w.Y)
         ctx.record(7, ckpt_every=k, dt_fixed=dt)
         outs.append(ctx.step_adjoint(7, lam))
-    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
+        finals.append(ctx.get_state())
+    for o, y in zip(outs[1:], finals[1:]):
+        assert np.array_equal(outs[0], o)
+        assert np.array_equal(finals[0], y)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_recorded_cfl_steps_same_with_and_without_recomputation(torch, dtype):
+    """With the time step from the CFL rule at every step, the adjoint that reads the kept
+    stage inputs and the one that recomputes them from checkpoints use the same recorded
+    steps and give the same vector."""
+    from paper_1901_02955_gb300 import Context
+    w = cases()["bubble_3d_periodic"]
+    ft = np.float32 if dtype == "f32" else np.float64
+    lam = np.random.default_rng(44).normal(size=w.Y.shape).astype(ft)
+    outs = []
+    for k in (0, 2):
+        ctx = Context(w, dtype=dtype)
+        ctx.set_state(w.Y)
+        ctx.record(5, ckpt_every=k)
+        outs.append(ctx.step_adjoint(5, lam))
+    assert np.array_equal(outs[0], outs[1])
 
 
 def test_fp32_adjoint_tracks_fp64_adjoint(torch):
