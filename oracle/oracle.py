@@ -91,6 +91,7 @@ def _load():
     lib.orc_weno5_gradient.restype = C.c_double
     lib.orc_rhs_adjoint.argtypes = [G, _D, _D, _D]
     lib.orc_step_adjoint.argtypes = [G, _D, C.c_double, _D, _D]
+    lib.orc_satadj_adjoint_cell.argtypes = [G, _D, _D, _D]
     return lib
 
 
@@ -219,6 +220,17 @@ class Oracle:
         rc = self.lib.orc_rhs_adjoint(C.byref(self.grid), _ptr(Y), _ptr(mu), _ptr(out))
         if rc:
             raise RuntimeError(f"orc_rhs_adjoint failed: {rc}")
+        return out
+
+    def satadj_adjoint_cell(self, Yout, lam_out):
+        """(dYout/dYin)^T lam_out of the saturation adjustment of one cell at its result."""
+        Yout = np.array(Yout, dtype=np.float64)
+        lam_out = np.array(lam_out, dtype=np.float64)
+        out = np.zeros_like(lam_out)
+        rc = self.lib.orc_satadj_adjoint_cell(C.byref(self.grid), _ptr(Yout), _ptr(lam_out),
+                                              _ptr(out))
+        if rc:
+            raise RuntimeError(f"orc_satadj_adjoint_cell failed: {rc}")
         return out
 
     def step_adjoint(self, Yn, dt, lam_out):

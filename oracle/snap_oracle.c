@@ -659,11 +659,11 @@ void orc_budget(const orc_grid *g, const double *Y, double *out) {
 }
 
 /* =======================================================================================
- * Discrete adjoint of the dry stage (reverse of Eq. forward with WENO5 and LMARS, the
- * gravity source and the SSP-RK3 combine), written by hand as the transpose of the forward
- * routines above, step by step in reverse order. Not part of the paper: it differentiates
- * the paper's discrete scheme. Branches are held fixed (upwind side of LMARS), and the time
- * step is treated as a given constant.
+ * Discrete adjoint of the inviscid stage (reverse of Eq. forward with WENO5 and LMARS, the
+ * gravity source, the SSP-RK3 combine and the saturation adjustment), written by hand as
+ * the transpose of the forward routines above, step by step in reverse order. Not part of
+ * the paper: it differentiates the paper's discrete scheme. Branches are held fixed (upwind
+ * side of LMARS, which vapours keep cloud), and the time step is a given constant.
  * ======================================================================================= */
 
 /* I = orc_weno5(q) and its gradient dI/dq_j. With w_k = a_k / S, a_k = d_k (eps + b_k)^-2:
@@ -718,14 +718,27 @@ double orc_weno5_gradient(const double q[5], double eps, double grad[5]) {
   return weno5_grad(q, eps, grad);
 }
 
-/* Transpose of orc_lmars for a dry gas: given Fbar (nvar), accumulate XLbar, XRbar. */
-static void lmars_adjoint_dry(const orc_grid *g, const double *XL, const double *XR, int dir,
-                              double pref, const double *Fbar, double *XLb, double *XRb) {
+/* Transpose of mix_factors: accumulate into Xb the adjoint of (num, den). */
+static void mix_factors_adjoint(const orc_grid *g, double numb, double denb, double *Xb) {
+  for (int i = 0; i < g->nvap; ++i) {
+    Xb[1 + i] += numb * (g->sig_v[i] - 1.0) + denb * (1.0 / g->eps[i] - 1.0);
+    for (int j = 0; j < g->ncond; ++j) Xb[icond(g, i, j)] += numb * (g->sig_c[i][j] - 1.0) - denb;
+  }
+}
+
+/* Transpose of orc_lmars: given Fbar (nvar), accumulate XLbar, XRbar. The forward quantities
+ * are recomputed first, then each assignment of orc_lmars is reversed in the opposite order. */
+static void lmars_adjoint(const orc_grid *g, const double *XL, const double *XR, int dir,
+                          double pref, const double *Fbar, double *XLb, double *XRb) {
   const int im0 = im0_of(g), nm = nmom_of(g), nv = orc_nvar(g), mn = mom_slot(g, dir);
-  const double gam = g->gamma_d, gm1 = g->gamma_d - 1.0;
+  const double gm1 = g->gamma_d - 1.0;
   /* forward recomputation */
+  double numL, denL, numR, denR;
+  mix_factors(g, XL, &numL, &denL);
+  mix_factors(g, XR, &numR, &denR);
   double pL = pref + XL[nv - 1], pR = pref + XR[nv - 1];
-  double cL = sqrt(gam * pL / XL[0]), cR = sqrt(gam * pR / XR[0]);
+  double gamL = 1.0 + gm1 * denL / numL, gamR = 1.0 + gm1 * denR / numR;
+  double cL = sqrt(gamL * pL / XL[0]), cR = sqrt(gamR * pR / XR[0]);
   double rhoc = 0.5 * (XL[0] + XR[0]) * 0.5 * (cL + cR);
   double uL = XL[mn], uR = XR[mn];
   double us = 0.5 * (uL + uR) - (XR[nv - 1] - XL[nv - 1]) / (2.0 * rhoc);
@@ -733,26 +746,55 @@ static void lmars_adjoint_dry(const orc_grid *g, const double *XL, const double 
    * the average of both one-sided derivatives is taken (what a central difference sees) */
   double usb = 0.0;
   const double psb = Fbar[mn];
+  double numLb = 0.0, denLb = 0.0, numRb = 0.0, denRb = 0.0;
   for (int side = 0; side < 2; ++side) {
     const int use_left = side == 0;
     double wgt = us > 0.0 ? (use_left ? 1.0 : 0.0) : (us < 0.0 ? (use_left ? 0.0 : 1.0) : 0.5);
     if (wgt == 0.0) continue;
     const double *XS = use_left ? XL : XR;
     double *XSb = use_left ? XLb : XRb;
-    double pS = use_left ? pL : pR, rhoS = XS[0], mf = us * rhoS, K = 0.0, u2 = 0.0;
+    double numS = use_left ? numL : numR, denS = use_left ? denL : denR;
+    double pS = use_left ? pL : pR, rhoS = XS[0], mf = us * rhoS;
+    double qsum = 0.0, u2 = 0.0, muq = 0.0;
+    for (int t = 1; t < im0; ++t) qsum += XS[t];
     for (int m = 0; m < nm; ++m) u2 += XS[im0 + m] * XS[im0 + m];
-    K = 0.5 * rhoS * u2;
-    double rhoe = pS / gm1 + K;
-    double mfb = Fbar[0];
-    for (int m = 0; m < nm; ++m) mfb += Fbar[im0 + m] * XS[im0 + m];
-    usb += wgt * (mfb * rhoS + Fbar[nv - 1] * (rhoe + pS));
-    double rhoeb = Fbar[nv - 1] * us;
-    double pSb = Fbar[nv - 1] * us + rhoeb / gm1;
-    double Kb = rhoeb;
-    XSb[0] += wgt * (mfb * us + Kb * 0.5 * u2);
-    for (int m = 0; m < nm; ++m)
-      XSb[im0 + m] += wgt * (Fbar[im0 + m] * mf + Kb * rhoS * XS[im0 + m]);
-    XSb[nv - 1] += wgt * pSb;
+    for (int i = 0; i < g->nvap; ++i)
+      for (int j = 0; j < g->ncond; ++j) muq += mu_of(g, i, j) * XS[icond(g, i, j)];
+    double K = 0.5 * rhoS * u2, A = rhoS * muq;
+    double rhoe = numS / denS * pS / gm1 + K + A;
+    /* F[E] = u* (rho e + p_S) */
+    usb += wgt * Fbar[nv - 1] * (rhoe + pS);
+    double rhoeb = wgt * Fbar[nv - 1] * us;
+    double pSb = wgt * Fbar[nv - 1] * us;
+    /* rho e = (num/den) p_S/(gamma_d - 1) + K + A */
+    pSb += rhoeb * numS / denS / gm1;
+    double rb = rhoeb * pS / gm1;
+    if (use_left) {
+      numLb += rb / denS;
+      denLb += -rb * numS / (denS * denS);
+    } else {
+      numRb += rb / denS;
+      denRb += -rb * numS / (denS * denS);
+    }
+    double rhoSb = rhoeb * (0.5 * u2 + muq);
+    for (int i = 0; i < g->nvap; ++i)
+      for (int j = 0; j < g->ncond; ++j) XSb[icond(g, i, j)] += rhoeb * rhoS * mu_of(g, i, j);
+    for (int m = 0; m < nm; ++m) XSb[im0 + m] += rhoeb * rhoS * XS[im0 + m];
+    /* mass, tracer and momentum fluxes: F[t] = mf q_t, F[0] = mf (1 - sum q), F[m] = mf u_m */
+    double mfb = Fbar[0] * (1.0 - qsum);
+    for (int t = 1; t < im0; ++t) {
+      mfb += Fbar[t] * XS[t];
+      XSb[t] += wgt * (Fbar[t] - Fbar[0]) * mf;
+    }
+    for (int m = 0; m < nm; ++m) {
+      mfb += Fbar[im0 + m] * XS[im0 + m];
+      XSb[im0 + m] += wgt * Fbar[im0 + m] * mf;
+    }
+    /* mf = u* rho_S */
+    usb += wgt * mfb * rhoS;
+    rhoSb += wgt * mfb * us;
+    XSb[0] += rhoSb;
+    XSb[nv - 1] += pSb;
   }
   double rhocb = 0.0;
   /* us = (uL + uR)/2 - (p'R - p'L)/(2 rho c) */
@@ -771,17 +813,64 @@ static void lmars_adjoint_dry(const orc_grid *g, const double *XL, const double 
   XLb[0] += 0.25 * (cL + cR) * rhocb;
   XRb[0] += 0.25 * (cL + cR) * rhocb;
   double cLb = 0.25 * (XL[0] + XR[0]) * rhocb, cRb = cLb;
-  /* c = sqrt(gamma p / rho) */
+  /* c = sqrt(gamma p / rho), gamma = 1 + (gamma_d - 1) den / num */
   XLb[nv - 1] += cLb * cL / (2.0 * pL);
   XLb[0] += -cLb * cL / (2.0 * XL[0]);
   XRb[nv - 1] += cRb * cR / (2.0 * pR);
   XRb[0] += -cRb * cR / (2.0 * XR[0]);
+  double gLb = cLb * cL / (2.0 * gamL), gRb = cRb * cR / (2.0 * gamR);
+  denLb += gLb * gm1 / numL;
+  numLb += -gLb * gm1 * denL / (numL * numL);
+  denRb += gRb * gm1 / numR;
+  numRb += -gRb * gm1 * denR / (numR * numR);
+  mix_factors_adjoint(g, numLb, denLb, XLb);
+  mix_factors_adjoint(g, numRb, denRb, XRb);
+}
+
+/* Transpose of orc_cons_to_prim at the cell state Y (the pressure entry of Xb is the adjoint
+ * of p; subtracting the constant p_bar_k has unit derivative). Adds into Yb. */
+static void cons_to_prim_adjoint(const orc_grid *g, const double *Y, const double *Xb,
+                                 double *Yb) {
+  const int im0 = im0_of(g), nm = nmom_of(g), nv = orc_nvar(g);
+  const double gm1 = g->gamma_d - 1.0;
+  double X[64];
+  orc_cons_to_prim(g, Y, X, NULL, NULL);
+  double rho = X[0], K = 0.0, A = 0.0, u2 = 0.0;
+  for (int m = 0; m < nm; ++m) u2 += X[im0 + m] * X[im0 + m];
+  K = 0.5 * rho * u2;
+  for (int i = 0; i < g->nvap; ++i)
+    for (int j = 0; j < g->ncond; ++j) A += mu_of(g, i, j) * Y[icond(g, i, j)];
+  double U = Y[nv - 1] - K - A, num, den;
+  mix_factors(g, X, &num, &den);
+  /* p = (gamma_d - 1) (den / num) U */
+  const double pb = Xb[nv - 1];
+  double Ub = pb * gm1 * den / num, rb = pb * gm1 * U;
+  double Qb[64];
+  for (int t = 0; t < nv; ++t) Qb[t] = 0.0;
+  for (int t = 1; t < im0; ++t) Qb[t] = Xb[t];
+  mix_factors_adjoint(g, -rb * den / (num * num), rb / num, Qb);
+  /* U = Y_E - K - A */
+  Yb[nv - 1] += Ub;
+  double Kb = -Ub;
+  for (int i = 0; i < g->nvap; ++i)
+    for (int j = 0; j < g->ncond; ++j) Yb[icond(g, i, j)] += -Ub * mu_of(g, i, j);
+  /* K = |m|^2 / (2 rho), u = m / rho, q_t = Y_t / rho, rho = sum of the densities */
+  double rhob = Xb[0] - Kb * 0.5 * u2;
+  for (int m = 0; m < nm; ++m) {
+    Yb[im0 + m] += Kb * X[im0 + m] + Xb[im0 + m] / rho;
+    rhob += -Xb[im0 + m] * X[im0 + m] / rho;
+  }
+  for (int t = 1; t < im0; ++t) {
+    Yb[t] += Qb[t] / rho;
+    rhob += -Qb[t] * X[t] / rho;
+  }
+  for (int t = 0; t < im0; ++t) Yb[t] += rhob;
 }
 
 int orc_rhs_adjoint(const orc_grid *g, const double *Y, const double *mu, double *Ybar) {
   const int nx = g->nx, ny = g->ny, nz = g->nz, nv = orc_nvar(g), im0 = im0_of(g);
-  const int nm = nmom_of(g), three_d = ny > 1;
-  if (g->nvap > 0 || g->nu > 0.0) return -3; /* dry, inviscid only */
+  const int three_d = ny > 1;
+  if (g->nu > 0.0) return -3; /* inviscid only */
   if (nx < 1 || ny < 1 || nz < 3) return -1;
   ext_dims e = {nx + 6, three_d ? ny + 6 : 1, nz + 6, 3, three_d ? 3 : 0, 3};
   const long next = (long)e.nxe * e.nye * e.nze;
@@ -885,7 +974,7 @@ int orc_rhs_adjoint(const orc_grid *g, const double *Y, const double *mu, double
             XLb[v] = XRb[v] = 0.0;
           }
           double pref = fz ? g->p_bar_face[k] : pbar_cell(g, k);
-          lmars_adjoint_dry(g, XL, XR, d, pref, Fb, XLb, XRb);
+          lmars_adjoint(g, XL, XR, d, pref, Fb, XLb, XRb);
           /* WENO5 transposes onto the stencil cells s = -3..2 */
           for (int v = 0; v < nv; ++v) {
             double st[5], gr[5];
@@ -942,32 +1031,97 @@ int orc_rhs_adjoint(const orc_grid *g, const double *Y, const double *mu, double
         }
       }
 
-  /* reverse of the primitive map (App. B, dry): rho = Y0, u_c = m_c / rho,
-   * p' = (gamma_d - 1)(rho e - |m|^2 / (2 rho)) - pbar_k */
-  const double gm1 = g->gamma_d - 1.0;
+  /* reverse of the primitive map (App. B) */
   for (int k = 0; k < nz; ++k)
     for (int j = 0; j < ny; ++j)
       for (int i = 0; i < nx; ++i) {
         long c = ((long)k * ny + j) * nx + i;
         long x = ext_index(&e, k, j, i);
-        double rho = Y[c], u2 = 0.0;
-        double pb = Xb[(long)(nv - 1) * next + x];
-        double r0 = Xb[x];
-        for (int m = 0; m < nm; ++m) {
-          double u = Y[(long)(im0 + m) * ncell + c] / rho;
-          double ub = Xb[(long)(im0 + m) * next + x];
-          r0 += -ub * u / rho;
-          u2 += u * u;
-          Ybar[(long)(im0 + m) * ncell + c] += ub / rho - pb * gm1 * u;
+        double Xbc[64], Ybc[64];
+        for (int v = 0; v < nv; ++v) {
+          Yc[v] = Y[v * ncell + c];
+          Xbc[v] = Xb[v * next + x];
+          Ybc[v] = 0.0;
         }
-        r0 += pb * gm1 * 0.5 * u2;
-        Ybar[c] += r0;
-        Ybar[(long)(nv - 1) * ncell + c] += pb * gm1;
+        cons_to_prim_adjoint(g, Yc, Xbc, Ybc);
+        for (int v = 0; v < nv; ++v) Ybar[v * ncell + c] += Ybc[v];
       }
   free(X);
   free(Xb);
   free(Fbz);
   return 0;
+}
+
+/* Transpose of the saturation adjustment of one cell at its converged result Yout (App. D).
+ * The iteration converges to the equilibrium in which every vapour i that keeps cloud holds
+ * the saturation density rho*_i(T) = p*_i(T)/(R_i T), its cloud the rest of the species
+ * total, while a vapour without cloud holds the whole total. T follows from the conserved
+ * energy: F(T) = T C_v(T) + A(T) - (rho e - K) = 0 with C_v = sum of c_k rho_k and
+ * A = sum mu_ij rho_ij over the adjusted composition. The derivative of the map
+ * Yin -> Yout is therefore that of the equilibrium (implicit function theorem on F):
+ *   dT/dy = -(dF/dy)/(dF/dT),  dF/dT = C_v + sum_{saturated i} rho*_i' (T (c_vi - c_i1) - mu_i1),
+ *   rho*_i' = rho*_i ((beta_i/t - delta_i)/T - 1/T), t = T/T^r_i,
+ * and dF/dy at fixed T: -1 for rho e, u_m for the momenta, T c_vd - |u|^2/2 for rho_d,
+ * T c_i1 + mu_i1 - |u|^2/2 for the total of a saturated species, T c_vi - |u|^2/2 for the
+ * total of an unsaturated one, T c_ij + mu_ij - |u|^2/2 for the other condensates.
+ * lam_in = (dYout/dYin)^T lam_out. The saturated set is read from Yout (cloud > 0); at its
+ * edge (cloud appearing or vanishing) the map has a kink, not differentiated here. */
+int orc_satadj_adjoint_cell(const orc_grid *g, const double *Yout, const double *lam_out,
+                            double *lam_in) {
+  const int im0 = im0_of(g), nm = nmom_of(g), nv = orc_nvar(g);
+  for (int v = 0; v < nv; ++v) lam_in[v] = lam_out[v];
+  if (g->nvap == 0 || g->ncond == 0) return 0;
+  double X[64], T;
+  orc_cons_to_prim(g, Yout, X, &T, NULL);
+  const double cvd = c_vd(g);
+  double u2 = 0.0, Cv = cvd * Yout[0];
+  for (int m = 0; m < nm; ++m) u2 += X[im0 + m] * X[im0 + m];
+  for (int i = 0; i < g->nvap; ++i) {
+    Cv += g->sig_v[i] * cvd * Yout[1 + i];
+    for (int j = 0; j < g->ncond; ++j) Cv += g->sig_c[i][j] * cvd * Yout[icond(g, i, j)];
+  }
+  double dFdT = Cv, gT = 0.0, dF[64];
+  dF[0] = T * cvd - 0.5 * u2;
+  for (int m = 0; m < nm; ++m) dF[im0 + m] = X[im0 + m];
+  dF[nv - 1] = -1.0;
+  for (int i = 0; i < g->nvap; ++i) {
+    const int vi = 1 + i, ci = icond(g, i, 0);
+    const int sat = Yout[ci] > 0.0;
+    const double c_v = g->sig_v[i] * cvd, c_c = g->sig_c[i][0] * cvd, mu_c = mu_of(g, i, 0);
+    for (int j = 1; j < g->ncond; ++j)
+      dF[icond(g, i, j)] = T * g->sig_c[i][j] * cvd + mu_of(g, i, j) - 0.5 * u2;
+    if (sat) {
+      double Ri = R_vap(g, i), dc = dc_of(g, i, 0);
+      double beta = (g->Lref[i][0] + dc * g->Tref[i]) / (Ri * g->Tref[i]);
+      double delta = dc / Ri, t = T / g->Tref[i];
+      double rs = orc_sat_pressure(g, i, T) / (Ri * T);
+      double drs = rs * ((beta / t - delta) / T - 1.0 / T);
+      dFdT += drs * (T * (c_v - c_c) - mu_c);
+      gT += drs * (lam_out[vi] - lam_out[ci]);
+      dF[vi] = dF[ci] = T * c_c + mu_c - 0.5 * u2;
+      lam_in[vi] = lam_in[ci] = lam_out[ci];
+    } else {
+      dF[vi] = dF[ci] = T * c_v - 0.5 * u2;
+      lam_in[vi] = lam_in[ci] = lam_out[vi];
+    }
+  }
+  const double coef = -gT / dFdT;
+  for (int v = 0; v < nv; ++v) lam_in[v] += coef * dF[v];
+  return 0;
+}
+
+static void satadj_adjoint_grid(const orc_grid *g, const double *Yout, double *lam) {
+  const int nv = orc_nvar(g);
+  const long ncell = (long)g->nx * g->ny * g->nz;
+  double Yc[64] = {0}, lo[64] = {0}, li[64];
+  for (long c = 0; c < ncell; ++c) {
+    for (int v = 0; v < nv; ++v) {
+      Yc[v] = Yout[v * ncell + c];
+      lo[v] = lam[v * ncell + c];
+    }
+    orc_satadj_adjoint_cell(g, Yc, lo, li);
+    for (int v = 0; v < nv; ++v) lam[v * ncell + c] = li[v];
+  }
 }
 
 /* Adjoint of one SSP-RK3 step with time step dt (Sec. 4.3 in reverse): given lam_out =
@@ -977,19 +1131,26 @@ int orc_step_adjoint(const orc_grid *g, const double *Yn, double dt, const doubl
   const int nv = orc_nvar(g);
   const long n = (long)nv * g->nx * g->ny * g->nz;
   double *Y1 = malloc(sizeof(double) * (size_t)n), *Y2 = malloc(sizeof(double) * (size_t)n);
-  double *mu = malloc(sizeof(double) * (size_t)n), *Yb = malloc(sizeof(double) * (size_t)n);
+  double *mu = calloc((size_t)n, sizeof(double)), *Yb = malloc(sizeof(double) * (size_t)n);
   double *l2 = malloc(sizeof(double) * (size_t)n), *l1 = malloc(sizeof(double) * (size_t)n);
+  double *Y3 = malloc(sizeof(double) * (size_t)n), *l3 = malloc(sizeof(double) * (size_t)n);
+  const int sa = g->satadj && g->nvap > 0 && g->ncond > 0;
   int rc = -2;
-  if (!Y1 || !Y2 || !mu || !Yb || !l2 || !l1) goto done;
+  if (!Y1 || !Y2 || !mu || !Yb || !l2 || !l1 || !Y3 || !l3) goto done;
   if ((rc = orc_stage(g, 0, Yn, Yn, dt, Y1)) < 0) goto done;
   if ((rc = orc_stage(g, 1, Yn, Y1, dt, Y2)) < 0) goto done;
+  if (sa && (rc = orc_stage(g, 2, Yn, Y2, dt, Y3)) < 0) goto done;
+  /* each stage ends with the saturation adjustment: its transpose comes first */
+  for (long c = 0; c < n; ++c) l3[c] = lam_out[c];
+  if (sa) satadj_adjoint_grid(g, Y3, l3);
   /* stage 2: Y3 = Yn/3 + 2/3 (Y2 + dt L(Y2)) */
-  for (long c = 0; c < n; ++c) mu[c] = 2.0 / 3.0 * dt * lam_out[c];
+  for (long c = 0; c < n; ++c) mu[c] = 2.0 / 3.0 * dt * l3[c];
   if ((rc = orc_rhs_adjoint(g, Y2, mu, Yb))) goto done;
   for (long c = 0; c < n; ++c) {
-    l2[c] = 2.0 / 3.0 * lam_out[c] + Yb[c];
-    lam_in[c] = lam_out[c] / 3.0;
+    l2[c] = 2.0 / 3.0 * l3[c] + Yb[c];
+    lam_in[c] = l3[c] / 3.0;
   }
+  if (sa) satadj_adjoint_grid(g, Y2, l2);
   /* stage 1: Y2 = 3/4 Yn + 1/4 (Y1 + dt L(Y1)) */
   for (long c = 0; c < n; ++c) mu[c] = 0.25 * dt * l2[c];
   if ((rc = orc_rhs_adjoint(g, Y1, mu, Yb))) goto done;
@@ -997,12 +1158,13 @@ int orc_step_adjoint(const orc_grid *g, const double *Yn, double dt, const doubl
     l1[c] = 0.25 * l2[c] + Yb[c];
     lam_in[c] += 0.75 * l2[c];
   }
+  if (sa) satadj_adjoint_grid(g, Y1, l1);
   /* stage 0: Y1 = Yn + dt L(Yn) */
   for (long c = 0; c < n; ++c) mu[c] = dt * l1[c];
   if ((rc = orc_rhs_adjoint(g, Yn, mu, Yb))) goto done;
   for (long c = 0; c < n; ++c) lam_in[c] += l1[c] + Yb[c];
   rc = 0;
 done:
-  free(Y1); free(Y2); free(mu); free(Yb); free(l2); free(l1);
+  free(Y1); free(Y2); free(mu); free(Yb); free(l2); free(l1); free(Y3); free(l3);
   return rc;
 }

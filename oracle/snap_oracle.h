@@ -96,11 +96,16 @@ double orc_dt_cfl(const orc_grid *g, const double *Y, double cfl);
  * (rho e + rho g z) times the cell volume. */
 void orc_budget(const orc_grid *g, const double *Y, double *out);
 
-/* ---- discrete adjoint (dry, inviscid): transposes of the routines above ---- */
+/* ---- discrete adjoint (inviscid): transposes of the routines above ---- */
 double orc_weno5_gradient(const double q[5], double eps, double grad[5]);
-/* Ybar = (dL/dY)^T mu at state Y (returns -3 for moist or viscous grids). */
+/* Ybar = (dL/dY)^T mu at state Y (returns -3 for viscous grids). */
 int orc_rhs_adjoint(const orc_grid *g, const double *Y, const double *mu, double *Ybar);
-/* lam_in = (dY^{n+1}/dY^n)^T lam_out for one step of time step dt from Yn. */
+/* lam_in = (dYout/dYin)^T lam_out for the saturation adjustment of one cell, evaluated at its
+ * converged result Yout (App. D equilibrium; see the definition for the derivation). */
+int orc_satadj_adjoint_cell(const orc_grid *g, const double *Yout, const double *lam_out,
+                            double *lam_in);
+/* lam_in = (dY^{n+1}/dY^n)^T lam_out for one step of time step dt from Yn (with the
+ * saturation adjustment after every stage when g->satadj is set). */
 int orc_step_adjoint(const orc_grid *g, const double *Yn, double dt, const double *lam_out,
                      double *lam_in);
 

@@ -43,6 +43,15 @@ MUTANTS = {
     "periodic wrap off by one": ("if (bc_hi == ORC_PERIODIC) return idx % n;", "if (bc_hi == ORC_PERIODIC) return (idx + 1) % n;"),
     "adjoint of u* pressure term sign": ("XLb[nv - 1] += usb / (2.0 * rhoc);", "XLb[nv - 1] -= usb / (2.0 * rhoc);"),
     "adjoint energy gravity dropped": ("Fbz[((long)(k + 1) * ny + j) * nx + i] += -0.5 * g->grav * me;", "(void)me;"),
+    "adjustment adjoint latent term dropped": ("dFdT += drs * (T * (c_v - c_c) - mu_c);",
+                                               "dFdT += drs * (T * (c_v - c_c));"),
+    "adjustment adjoint unsaturated routing": ("lam_in[vi] = lam_in[ci] = lam_out[vi];",
+                                               "lam_in[vi] = lam_in[ci] = lam_out[ci];"),
+    "moist lmars adjoint gamma sign": ("denLb += gLb * gm1 / numL;", "denLb -= gLb * gm1 / numL;"),
+    "moist primitive adjoint chemical potential": ("Yb[icond(g, i, j)] += -Ub * mu_of(g, i, j);",
+                                                   "Yb[icond(g, i, j)] += Ub * mu_of(g, i, j);"),
+    "tracer flux adjoint without dry-air term": ("XSb[t] += wgt * (Fbar[t] - Fbar[0]) * mf;",
+                                                 "XSb[t] += wgt * Fbar[t] * mf;"),
 }
 
 
