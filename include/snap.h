@@ -149,28 +149,30 @@ int snap_compute_dt(snap_ctx *ctx, int domain, double *dt);
 /* Apply the App. D saturation adjustment to every cell of one domain's current state. */
 int snap_saturation_adjust(snap_ctx *ctx, int domain);
 
-/* Forward run recorded for the adjoint: advances the (single, dry, inviscid) domain by
- * nsteps steps like snap_step, keeping the final state, the time step of every step and
+/* Forward run recorded for the adjoint: advances the domain by nsteps steps like snap_step,
+ * keeping the final state, the time step of every step and
  *   ckpt_every >= 1: a checkpoint of the state every ckpt_every steps; the adjoint recomputes
  *     each segment from its checkpoint. Allocates nsteps/ckpt_every + 2 state copies and a
  *     segment of 3 x ckpt_every states (the input of each of the three stages of a step);
  *   ckpt_every == 0: the input of every stage of every step (3 x nsteps + 1 state copies);
  *     the adjoint recomputes nothing.
- * Also allocates four adjoint vectors and the per-face work arrays of the adjoint.
- * SNAP_ENOTSUP for moist, viscous or multi-domain contexts. */
+ * Also allocates four adjoint vectors and the per-face work arrays of the adjoint. The
+ * adjoint is built for a single inviscid domain, dry (x-z or 3-D) or with one vapour and two
+ * condensates in the x-z plane; SNAP_ENOTSUP for any other context. */
 int snap_record(snap_ctx *ctx, int nsteps, int ckpt_every, double dt_fixed);
 
 /* Discrete adjoint of the recorded run: lambda_init = (dY_N / dY_0)^T lambda_final, with
  * Y_0 the state at the start of the last snap_record and Y_N the state at its end; nsteps
- * must equal the recorded step count. The transpose of each stage (SSP-RK3 combine of Sec.
- * 4.3, flux divergence and gravity source, LMARS of Sec. 4.1, WENO5 of Sec. 4.2, primitive
- * map of App. B) is applied in reverse order, segment by segment, with the forward states of
- * a segment recomputed from its checkpoint (or read from the record when ckpt_every was 0).
- * The recorded time steps are constants; the upwind side of LMARS is held, except at u* = 0
- * where the mean of both one-sided derivatives is used. Both vectors have the state layout (total energy; the reference offset of the
- * stored energy has unit derivative), dtype SNAP_F32/F64, host or device memory. The context
- * state is restored to Y_N afterwards. SNAP_ENOTSUP for moist, viscous or multi-domain
- * contexts. */
+ * must equal the recorded step count. The transpose of each stage (saturation adjustment of
+ * App. D, SSP-RK3 combine of Sec. 4.3, flux divergence and gravity source, LMARS of Sec.
+ * 4.1, WENO5 of Sec. 4.2, primitive map of App. B) is applied in reverse order, segment by
+ * segment, with the forward states of a segment recomputed from its checkpoint (or read from
+ * the record when ckpt_every was 0). The recorded time steps are constants; the upwind side
+ * of LMARS is held, except at u* = 0 where the mean of both one-sided derivatives is used;
+ * the adjustment is differentiated through its equilibrium, with the set of vapours that
+ * keep cloud held. Both vectors have the state layout (total energy; the reference offset
+ * of the stored energy has unit derivative), dtype SNAP_F32/F64, host or device memory. The
+ * context state is restored to Y_N afterwards. SNAP_ENOTSUP as for snap_record. */
 int snap_step_adjoint(snap_ctx *ctx, int nsteps, const void *lambda_final, void *lambda_init,
                       int dtype, void *stream);
 

@@ -21,9 +21,12 @@ bool find_kernels_moist3d(int f32, int visc, KernelSet *out);
 
 bool find_adjoint_kernels_dry2d(int f32, AdjKernels *out);
 bool find_adjoint_kernels_dry3d(int f32, AdjKernels *out);
+bool find_adjoint_kernels_moist2d(int f32, AdjKernels *out);
 
-bool find_adjoint_kernels(int f32, int three_d, AdjKernels *out) {
-  return three_d ? find_adjoint_kernels_dry3d(f32, out) : find_adjoint_kernels_dry2d(f32, out);
+bool find_adjoint_kernels(int f32, int nvap, int ncond, int three_d, AdjKernels *out) {
+  if (nvap == 0) return three_d ? find_adjoint_kernels_dry3d(f32, out) : find_adjoint_kernels_dry2d(f32, out);
+  if (nvap == 1 && ncond == 2 && !three_d) return find_adjoint_kernels_moist2d(f32, out);
+  return false;
 }
 
 bool find_kernels(int f32, int nvap, int ncond, int three_d, int visc, KernelSet *out) {
@@ -340,8 +343,8 @@ extern "C" int snap_init_grid(snap_ctx **out, const snap_grid_desc *d, int n_dom
   }
   derive_phys(d[0], ctx->ph);
   ctx->desc.assign(d, d + n_domains);
-  if (ctx->nvap == 0 && !ctx->visc && n_domains == 1)
-    ctx->has_adj = find_adjoint_kernels(ctx->f32, ctx->three_d, &ctx->adj) ? 1 : 0;
+  if (!ctx->visc && n_domains == 1)
+    ctx->has_adj = find_adjoint_kernels(ctx->f32, ctx->nvap, ctx->ncond, ctx->three_d, &ctx->adj) ? 1 : 0;
   cudaError_t e = cudaSuccess;
   for (int v = 0; v < ctx->ks.nvariants && e == cudaSuccess; ++v) e = ctx->ks.var[v].prepare();
   if (e != cudaSuccess) {
@@ -727,6 +730,20 @@ static size_t state_bytes_dom0(snap_ctx *ctx) {
   return (size_t)ctx->dom[0].ncell * ctx->nv * ctx->word;
 }
 
+// Transpose of the saturation adjustment at the stage output Yout, on lam in place.
+static int satadj_adjoint(snap_ctx *ctx, const StageArgs &sa, const void *Yout, void *lam) {
+  AdjArgs A;
+  memset(&A, 0, sizeof A);
+  A.doms = ctx->doms_dev;
+  A.Ys = Yout;
+  A.lam_s = lam;
+  A.ph = ctx->ph;
+  A.cf = sa.cf;
+  A.cd = sa.cd;
+  CK(ctx->adj.satadj(A, ctx->dom[0].ncell, ctx->stream));
+  return SNAP_OK;
+}
+
 // One forward stage; dt > 0 is passed in the launch arguments (the recorded time step).
 static int plain_stage(snap_ctx *ctx, const StageArgs &base, int stage, double dt) {
   StageArgs a = base;
@@ -739,7 +756,7 @@ static int plain_stage(snap_ctx *ctx, const StageArgs &base, int stage, double d
 extern "C" int snap_record(snap_ctx *ctx, int nsteps, int ckpt_every, double dt_fixed) {
   if (!ctx) return fail(nullptr, SNAP_EINVAL, "snap_record: NULL context");
   if (!ctx->has_adj)
-    return fail(ctx, SNAP_ENOTSUP, "snap_record: the adjoint is built for one dry, inviscid domain");
+    return fail(ctx, SNAP_ENOTSUP, "snap_record: the adjoint is built for one inviscid domain, dry or with one vapour (x-z)");
   if (nsteps < 1 || ckpt_every < 0)
     return fail(ctx, SNAP_EINVAL, "snap_record: nsteps must be >= 1 and ckpt_every >= 0");
   const size_t sb = state_bytes_dom0(ctx);
@@ -842,7 +859,7 @@ extern "C" int snap_step_adjoint(snap_ctx *ctx, int nsteps, const void *lambda_f
                                  void *lambda_init, int dtype, void *stream) {
   if (!ctx) return fail(nullptr, SNAP_EINVAL, "snap_step_adjoint: NULL context");
   if (!ctx->has_adj)
-    return fail(ctx, SNAP_ENOTSUP, "snap_step_adjoint: the adjoint is built for one dry, inviscid domain");
+    return fail(ctx, SNAP_ENOTSUP, "snap_step_adjoint: the adjoint is built for one inviscid domain, dry or with one vapour (x-z)");
   if (!lambda_final || !lambda_init || (dtype != SNAP_F64 && dtype != SNAP_F32))
     return fail(ctx, SNAP_EINVAL, "snap_step_adjoint: bad pointers or dtype");
   if (ctx->rec_steps < 1 || nsteps != ctx->rec_steps)
@@ -871,6 +888,7 @@ extern "C" int snap_step_adjoint(snap_ctx *ctx, int nsteps, const void *lambda_f
   const int K = store_all ? nsteps : ctx->ckpt_every;
   const int nseg = (nsteps + K - 1) / K;
   const StageArgs base = args_of(ctx, 0);
+  const bool sa = ctx->adj.satadj && ctx->ph.satadj;
   int rc = SNAP_OK;
   for (int seg = nseg - 1; seg >= 0 && rc == SNAP_OK; --seg) {
     const int n0 = seg * K, n1 = (n0 + K < nsteps) ? n0 + K : nsteps;
@@ -891,9 +909,16 @@ extern "C" int snap_step_adjoint(snap_ctx *ctx, int nsteps, const void *lambda_f
       const double dt = ctx->rec_dt[s];
       const char *slot = (const char *)ctx->segbuf + sb * 3 * (s - n0);
       // Sec. 4.3 in reverse: Y3 = Y/3 + 2/3 (Y2 + dt L(Y2)), Y2 = 3/4 Y + 1/4 (Y1 + dt L(Y1)),
-      // Y1 = Y + dt L(Y)
+      // Y1 = Y + dt L(Y); each stage ends with the saturation adjustment, whose transpose is
+      // taken at the stage's output first. The output of stage 2 is the next step's state:
+      // the next slot, else the next checkpoint (the final state after the last step).
+      const char *out2 = s + 1 < n1 ? slot + 3 * sb
+                                    : (const char *)ctx->ckpt + sb * (store_all ? 0 : seg + 1);
+      if (sa && (rc = satadj_adjoint(ctx, base, out2, LA))) break;
       if ((rc = adjoint_stage(ctx, base, slot + 2 * sb, LA, LB, LN, 1.0 / 3.0, 2.0 / 3.0, dt, 2))) break;
+      if (sa && (rc = satadj_adjoint(ctx, base, slot + 2 * sb, LB))) break;
       if ((rc = adjoint_stage(ctx, base, slot + sb, LB, LC, LN, 0.75, 0.25, dt, 1))) break;
+      if (sa && (rc = satadj_adjoint(ctx, base, slot + sb, LC))) break;
       if ((rc = adjoint_stage(ctx, base, slot, LC, LA, LN, 0.0, 1.0, dt, 0))) break;
     }
   }

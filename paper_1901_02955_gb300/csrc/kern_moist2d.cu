@@ -1,5 +1,6 @@
-// kern_moist2d.cu -- stage kernels for one vapour with cloud and precipitation, x-z plane.
-#include "snap_stage.cuh"
+// kern_moist2d.cu -- stage and adjoint kernels for one vapour with cloud and precipitation,
+// x-z plane.
+#include "snap_adjoint.cuh"
 
 namespace snap {
 
@@ -10,6 +11,12 @@ bool find_kernels_moist2d(int f32, int visc, KernelSet *out) {
   using C = TileT<16, 1, 30>;
   if (visc) return false;
   *out = f32 ? Family<float, L>::set<false, A, B, C>() : Family<double, L>::set<false, A>();
+  return true;
+}
+
+bool find_adjoint_kernels_moist2d(int f32, AdjKernels *out) {
+  using L = Lay<1, 2, false>;
+  *out = f32 ? AdjFamily<float, L>::get() : AdjFamily<double, L>::get();
   return true;
 }
 

@@ -1,11 +1,14 @@
-// snap_adjoint.cuh -- discrete adjoint of one Runge-Kutta stage of the dry, inviscid step
-// (the transpose of stage_tiles in snap_stage.cuh): reverse of the SSP-RK3 combine
-// (Sec. 4.3), of the flux divergence and gravity source (Eq. forward, Eq. mom3), of LMARS
-// (Eqs. rp, ru), of WENO5 (Eq. weno5) and of the primitive map (App. B). The upwind branch
-// of LMARS is held fixed, except at u* = 0 where the mean of both one-sided derivatives is
-// used; the time step is a given constant.
+// snap_adjoint.cuh -- discrete adjoint of one Runge-Kutta stage of the inviscid step (the
+// transpose of stage_tiles in snap_stage.cuh): reverse of the saturation adjustment (App. D,
+// by the derivative of its equilibrium), of the SSP-RK3 combine (Sec. 4.3), of the flux
+// divergence and gravity source (Eq. forward, Eq. mom3), of LMARS (Eqs. rp, ru), of WENO5
+// (Eq. weno5) and of the primitive map (App. B, Eq. p2). The upwind branch of LMARS is held
+// fixed, except at u* = 0 where the mean of both one-sided derivatives is used; which vapours
+// keep cloud is held fixed; the time step is a given constant.
 //
-// Two kernels per stage, deterministic (no atomics):
+// Per stage, deterministic (no atomics):
+//   adj_satadj_kernel (moist layouts): one thread per cell maps the adjoint of the adjusted
+//     state to that of the state before the adjustment, in FP64;
 //   adj_face_kernel (one launch for the faces of every direction): one thread per face
 //     recomputes the face states from its six-cell stencil, transposes LMARS and WENO5, and
 //     writes the contribution of the face to each of its six stencil cells into
@@ -84,21 +87,42 @@ __device__ __forceinline__ R weno5_grad(const R q[5], R eps, R g[5]) {
   return I;
 }
 
-// Transpose of lmars<> for a dry gas: accumulates XLb, XRb from Fb.
+// Transpose of mix_factors<>: adds the adjoint of (num, den) to the tracer entries of Xb.
+template <class R, class L>
+__device__ __forceinline__ void mix_factors_adj(const CstT<R> &C, R numb, R denb, R *Xb) {
+#pragma unroll
+  for (int i = 0; i < L::NVAP; ++i) {
+    Xb[1 + i] += numb * C.sigv_m1[i] + denb * C.ieps_m1[i];
+#pragma unroll
+    for (int j = 0; j < L::NCOND; ++j) Xb[L::cond(i, j)] += numb * C.sigc_m1[i][j] - denb;
+  }
+}
+
+// Transpose of lmars<>: accumulates XLb, XRb from Fb (forward values recomputed first, then
+// each assignment of lmars<> reversed in the opposite order).
 template <class R, class L>
 __device__ __forceinline__ void lmars_adj(const CstT<R> &C, const R *XL, const R *XR, int dir,
                                           R pref, const R *Fb, R *XLb, R *XRb) {
-  static_assert(L::NVAP == 0, "the adjoint is built for a dry gas");
   constexpr int NV = L::NV, IE = L::IE, IM0 = L::IM0, NM = L::NMOM;
   const int mn = L::mom(dir);
-  const R gam = C.gamma_d, igm1 = C.igm1;
+  const R gm1 = C.gm1, igm1 = C.igm1;
+  R numL, denL, numR, denR;
+  mix_factors<R, L>(C, XL, numL, denL);
+  mix_factors<R, L>(C, XR, numR, denR);
   const R pL = pref + XL[IE], pR = pref + XR[IE];
-  const R cL = Ar<R>::sqrt_pos(gam * pL * Ar<R>::rcp(XL[0]));
-  const R cR = Ar<R>::sqrt_pos(gam * pR * Ar<R>::rcp(XR[0]));
+  R gamL, gamR;
+  if constexpr (L::NVAP == 0) {
+    gamL = gamR = C.gamma_d;
+  } else {
+    gamL = R(1) + gm1 * Ar<R>::div(denL, numL);
+    gamR = R(1) + gm1 * Ar<R>::div(denR, numR);
+  }
+  const R cL = Ar<R>::sqrt_pos(gamL * pL * Ar<R>::rcp(XL[0]));
+  const R cR = Ar<R>::sqrt_pos(gamR * pR * Ar<R>::rcp(XR[0]));
   const R rhoc = R(0.5) * (XL[0] + XR[0]) * R(0.5) * (cL + cR);
   const R uL = XL[mn], uR = XR[mn];
   const R us = R(0.5) * (uL + uR) - Ar<R>::div(XR[IE] - XL[IE], R(2) * rhoc);
-  R usb = R(0);
+  R usb = R(0), numLb = R(0), denLb = R(0), numRb = R(0), denRb = R(0);
   const R psb = Fb[mn];
 #pragma unroll
   for (int side = 0; side < 2; ++side) {
@@ -109,32 +133,65 @@ __device__ __forceinline__ void lmars_adj(const CstT<R> &C, const R *XL, const R
     R XS[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) XS[v] = use_left ? XL[v] : XR[v];
+    const R numS = use_left ? numL : numR, denS = use_left ? denL : denR;
     const R pS = use_left ? pL : pR, rhoS = XS[0], mf = us * rhoS;
-    R u2 = R(0), mfb = Fb[0];
+    R qsum = R(0), u2 = R(0), muq = R(0);
+#pragma unroll
+    for (int t = 1; t < IM0; ++t) qsum += XS[t];
+#pragma unroll
+    for (int m = 0; m < NM; ++m) u2 += XS[IM0 + m] * XS[IM0 + m];
+#pragma unroll
+    for (int i = 0; i < L::NVAP; ++i)
+#pragma unroll
+      for (int j = 0; j < L::NCOND; ++j) muq += C.mu[i][j] * XS[L::cond(i, j)];
+    const R K = R(0.5) * rhoS * u2;
+    R rS = R(1);
+    if constexpr (L::NVAP > 0) rS = Ar<R>::div(numS, denS);
+    const R rhoe = rS * pS * igm1 + K + rhoS * muq;
+    // F[E] = u* (rho e + p_S), rho e = (num/den) p_S / (gamma_d - 1) + K + A
+    usb += wgt * Fb[IE] * (rhoe + pS);
+    const R rhoeb = wgt * Fb[IE] * us;
+    const R pSb = rhoeb + rhoeb * rS * igm1;
+    if constexpr (L::NVAP > 0) {
+      const R rb = rhoeb * pS * igm1, iden = Ar<R>::rcp(denS);
+      if (use_left) {
+        numLb += rb * iden;
+        denLb -= rb * numS * iden * iden;
+      } else {
+        numRb += rb * iden;
+        denRb -= rb * numS * iden * iden;
+      }
+    }
+    R rhoSb = rhoeb * (R(0.5) * u2 + muq);
+    R bS[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) bS[v] = R(0);
+#pragma unroll
+    for (int i = 0; i < L::NVAP; ++i)
+#pragma unroll
+      for (int j = 0; j < L::NCOND; ++j) bS[L::cond(i, j)] += rhoeb * rhoS * C.mu[i][j];
+    // F[t] = mf q_t, F[0] = mf (1 - sum q), F[m] = mf u_m, mf = u* rho_S
+    R mfb = Fb[0] * (R(1) - qsum);
+#pragma unroll
+    for (int t = 1; t < IM0; ++t) {
+      mfb += Fb[t] * XS[t];
+      bS[t] += wgt * (Fb[t] - Fb[0]) * mf;
+    }
 #pragma unroll
     for (int m = 0; m < NM; ++m) {
-      u2 += XS[IM0 + m] * XS[IM0 + m];
       mfb += Fb[IM0 + m] * XS[IM0 + m];
+      bS[IM0 + m] += wgt * Fb[IM0 + m] * mf + rhoeb * rhoS * XS[IM0 + m];
     }
-    const R rhoe = pS * igm1 + R(0.5) * rhoS * u2;
-    usb += wgt * (mfb * rhoS + Fb[IE] * (rhoe + pS));
-    const R rhoeb = Fb[IE] * us;
-    const R pSb = Fb[IE] * us + rhoeb * igm1;
-    R b0 = wgt * (mfb * us + rhoeb * R(0.5) * u2);
-    R bp = wgt * pSb;
-    R bm[NM];
-#pragma unroll
-    for (int m = 0; m < NM; ++m) bm[m] = wgt * (Fb[IM0 + m] * mf + rhoeb * rhoS * XS[IM0 + m]);
+    usb += wgt * mfb * rhoS;
+    rhoSb += wgt * mfb * us;
+    bS[0] += rhoSb;
+    bS[IE] += pSb;
     if (use_left) {
-      XLb[0] += b0;
-      XLb[IE] += bp;
 #pragma unroll
-      for (int m = 0; m < NM; ++m) XLb[IM0 + m] += bm[m];
+      for (int v = 0; v < NV; ++v) XLb[v] += bS[v];
     } else {
-      XRb[0] += b0;
-      XRb[IE] += bp;
 #pragma unroll
-      for (int m = 0; m < NM; ++m) XRb[IM0 + m] += bm[m];
+      for (int v = 0; v < NV; ++v) XRb[v] += bS[v];
     }
   }
   R rhocb = R(0);
@@ -156,20 +213,17 @@ __device__ __forceinline__ void lmars_adj(const CstT<R> &C, const R *XL, const R
   XLb[0] -= cb * cL * Ar<R>::rcp(R(2) * XL[0]);
   XRb[IE] += cb * cR * Ar<R>::rcp(R(2) * pR);
   XRb[0] -= cb * cR * Ar<R>::rcp(R(2) * XR[0]);
-}
-
-// primitives of a stored dry state (p' = (gamma_d - 1)(y_E - K), y_E = rho e - e_ref)
-template <class R, class L>
-__device__ __forceinline__ void dry_prim(const CstT<R> &C, const R *y, R *x) {
-  const R ir = Ar<R>::rcp(y[0]);
-  x[0] = y[0];
-  R K = R(0);
-#pragma unroll
-  for (int m = 0; m < L::NMOM; ++m) {
-    x[L::IM0 + m] = y[L::IM0 + m] * ir;
-    K += y[L::IM0 + m] * x[L::IM0 + m];
+  if constexpr (L::NVAP > 0) {
+    // gamma = 1 + (gamma_d - 1) den / num
+    const R gLb = cb * cL * Ar<R>::rcp(R(2) * gamL), gRb = cb * cR * Ar<R>::rcp(R(2) * gamR);
+    const R inL = Ar<R>::rcp(numL), inR = Ar<R>::rcp(numR);
+    denLb += gLb * gm1 * inL;
+    numLb -= gLb * gm1 * denL * inL * inL;
+    denRb += gRb * gm1 * inR;
+    numRb -= gRb * gm1 * denR * inR * inR;
+    mix_factors_adj<R, L>(C, numLb, denLb, XLb);
+    mix_factors_adj<R, L>(C, numRb, denRb, XRb);
   }
-  x[L::IE] = C.gm1 * (y[L::IE] - R(0.5) * K);
 }
 
 // Adjoint of face f of direction DIR (face index in [nz'][ny'][nx'] order of that direction).
@@ -219,10 +273,10 @@ __device__ __forceinline__ void adj_face(const AdjArgs &a, const DomDev &D, cons
     const int p = map_index(pos - 3 + s, nd, bclo, bchi, flip);
     const int ci = fx ? p : i, cj = fy ? p : j, ck = fz ? p : k;
     const long long c = ((long long)ck * ny + cj) * nx + ci;
-    R y[NV];
+    R y[NV], pt, Tt;
 #pragma unroll
     for (int v = 0; v < NV; ++v) y[v] = Ys[v * ncell + c];
-    dry_prim<R, L>(C, y, X[s]);
+    cons_to_prim<R, L>(a.ph, C, D, ck, y, X[s], pt, Tt);
     if (flip) X[s][MN] = -X[s][MN];
   }
   R QL[NV], QR[NV], gL[NV][5], gR[NV][5], QLb[NV], QRb[NV];
@@ -339,22 +393,62 @@ __global__ void __launch_bounds__(128) adj_cell_kernel(const AdjArgs a) {
     gather_dir<R, L, 0>(a, D, i, j, k, Xb);
     if constexpr (L::D3) gather_dir<R, L, 1>(a, D, i, j, k, Xb);
     gather_dir<R, L, 2>(a, D, i, j, k, Xb);
-    // transpose of the primitive map and of the gravity source
+    // transpose of the primitive map (App. B: rho, q_t = y_t / rho, u_m = y_m / rho,
+    // p = (gamma_d - 1) (den/num) U with U = rho e - K - A) and of the gravity source
     R y[NV], Yb[NV];
 #pragma unroll
-    for (int v = 0; v < NV; ++v) y[v] = Ys[v * ncell + c];
-    const R rho = y[0], ir = Ar<R>::rcp(rho);
-    R r0 = Xb[0], u2 = R(0);
+    for (int v = 0; v < NV; ++v) {
+      y[v] = Ys[v * ncell + c];
+      Yb[v] = R(0);
+    }
+    R rho = y[0];
+#pragma unroll
+    for (int t = 1; t < IM0; ++t) rho += y[t];
+    const R ir = Ar<R>::rcp(rho);
+    R u2 = R(0);
+#pragma unroll
+    for (int m = 0; m < L::NMOM; ++m) u2 += (y[IM0 + m] * ir) * (y[IM0 + m] * ir);
+    const R pb = Xb[IE];
+    R Ub = pb * C.gm1;
+    R Qb[NV];
+#pragma unroll
+    for (int t = 0; t < NV; ++t) Qb[t] = t >= 1 && t < IM0 ? Xb[t] : R(0);
+    if constexpr (L::NVAP > 0) {
+      R x[NV], num, den, A = R(0);
+#pragma unroll
+      for (int t = 1; t < IM0; ++t) x[t] = y[t] * ir;
+      mix_factors<R, L>(C, x, num, den);
+#pragma unroll
+      for (int i2 = 0; i2 < L::NVAP; ++i2)
+#pragma unroll
+        for (int j2 = 0; j2 < L::NCOND; ++j2) A += C.mu[i2][j2] * y[L::cond(i2, j2)];
+      const R U = (y[IE] + Prof<R>::er(D, k)) - R(0.5) * rho * u2 - A;
+      const R inum = Ar<R>::rcp(num), rb = pb * C.gm1 * U;
+      Ub = pb * C.gm1 * den * inum;
+      mix_factors_adj<R, L>(C, -rb * den * inum * inum, rb * inum, Qb);
+#pragma unroll
+      for (int i2 = 0; i2 < L::NVAP; ++i2)
+#pragma unroll
+        for (int j2 = 0; j2 < L::NCOND; ++j2) Yb[L::cond(i2, j2)] -= Ub * C.mu[i2][j2];
+    }
+    Yb[IE] += Ub;
+    const R Kb = -Ub;
+    R rhob = Xb[0] - Kb * R(0.5) * u2;
 #pragma unroll
     for (int m = 0; m < L::NMOM; ++m) {
       const R u = y[IM0 + m] * ir;
-      r0 -= Xb[IM0 + m] * u * ir;
-      u2 += u * u;
-      Yb[IM0 + m] = Xb[IM0 + m] * ir - Xb[IE] * C.gm1 * u;
+      Yb[IM0 + m] += Kb * u + Xb[IM0 + m] * ir;
+      rhob -= Xb[IM0 + m] * u * ir;
     }
-    r0 += Xb[IE] * C.gm1 * R(0.5) * u2;
-    Yb[0] = r0 - grav * bdt * lo[L::mom(2) * ncell + c];
-    Yb[IE] = Xb[IE] * C.gm1;
+#pragma unroll
+    for (int t = 1; t < IM0; ++t) {
+      Yb[t] += Qb[t] * ir;
+      rhob -= Qb[t] * (y[t] * ir) * ir;
+    }
+    // momentum source -(rho - rho_bar) g on rho w, rho the sum of the densities
+    rhob -= grav * bdt * lo[L::mom(2) * ncell + c];
+#pragma unroll
+    for (int t = 0; t < IM0; ++t) Yb[t] += rhob;
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       const R l = lo[v * ncell + c];
@@ -372,6 +466,90 @@ __global__ void __launch_bounds__(128) adj_cell_kernel(const AdjArgs a) {
   }
 }
 
+// Transpose of the saturation adjustment of one cell, in FP64, at its adjusted state y (the
+// stage output): the adjustment converges to the equilibrium in which a vapour that keeps
+// cloud holds rho*_i(T) = p*_i(T) / (R_i T) and its cloud the rest of the species total, a
+// vapour without cloud the whole total; T follows from the conserved energy through
+// F(T) = T C_v(T) + A(T) - (rho e - K) = 0. Hence dT/dy = -(dF/dy) / (dF/dT) with
+// dF/dT = C_v + sum over saturated i of rho*_i' (T (c_vi - c_i1) - mu_i1) and, at fixed T,
+// dF/dy = -1 (rho e), u_m (momenta), T c_vd - |u|^2/2 (rho_d), T c_i1 + mu_i1 - |u|^2/2
+// (total of a saturated species), T c_vi - |u|^2/2 (an unsaturated one), T c_ij + mu_ij -
+// |u|^2/2 (other condensates). lam (in place): (dY_out/dY_in)^T lam.
+template <class R, class L>
+__device__ __forceinline__ void satadj_adj_cell(const Phys &ph, const R *y, double eref,
+                                                double *lam) {
+  constexpr int NV = L::NV, IM0 = L::IM0;
+  double T, p;
+  cell_Tp<R, L>(ph, y, eref, T, p);
+  double rho = 0.0, u2 = 0.0, Cv = double(y[0]);
+#pragma unroll
+  for (int s = 0; s < IM0; ++s) rho += double(y[s]);
+  const double ir = 1.0 / rho;
+#pragma unroll
+  for (int m = 0; m < L::NMOM; ++m) u2 += (double(y[IM0 + m]) * ir) * (double(y[IM0 + m]) * ir);
+#pragma unroll
+  for (int i = 0; i < L::NVAP; ++i) {
+    Cv += ph.sig_v[i] * double(y[1 + i]);
+#pragma unroll
+    for (int j = 0; j < L::NCOND; ++j) Cv += ph.sig_c[i][j] * double(y[L::cond(i, j)]);
+  }
+  Cv *= ph.c_vd;
+  double dF[NV], li[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) li[v] = lam[v];
+  dF[0] = T * ph.c_vd - 0.5 * u2;
+#pragma unroll
+  for (int m = 0; m < L::NMOM; ++m) dF[IM0 + m] = double(y[IM0 + m]) * ir;
+  dF[L::IE] = -1.0;
+  double dFdT = Cv, gT = 0.0;
+#pragma unroll
+  for (int i = 0; i < L::NVAP; ++i) {
+    const int vi = 1 + i, ci = L::cond(i, 0);
+    const double c_v = ph.sig_v[i] * ph.c_vd, c_c = ph.sig_c[i][0] * ph.c_vd, mu_c = ph.mu[i][0];
+#pragma unroll
+    for (int j = 1; j < L::NCOND; ++j)
+      dF[L::cond(i, j)] = T * ph.sig_c[i][j] * ph.c_vd + ph.mu[i][j] - 0.5 * u2;
+    if (y[ci] > R(0)) {
+      const double t = T / ph.Tref[i];
+      const double ps = ph.pref[i] * exp(ph.beta[i] * (1.0 - 1.0 / t) - ph.delta[i] * log(t));
+      const double rs = ps / (ph.R_v[i] * T);
+      const double drs = rs * ((ph.beta[i] / t - ph.delta[i]) - 1.0) / T;
+      dFdT += drs * (T * (c_v - c_c) - mu_c);
+      gT += drs * (lam[vi] - lam[ci]);
+      dF[vi] = dF[ci] = T * c_c + mu_c - 0.5 * u2;
+      li[vi] = li[ci] = lam[ci];
+    } else {
+      dF[vi] = dF[ci] = T * c_v - 0.5 * u2;
+      li[vi] = li[ci] = lam[vi];
+    }
+  }
+  const double coef = -gT / dFdT;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) lam[v] = li[v] + coef * dF[v];
+}
+
+// lam_s <- (dY_out / dY_in)^T lam_s of the adjustment, at the stage output a.Ys.
+template <class R, class L>
+__global__ void __launch_bounds__(128) adj_satadj_kernel(const AdjArgs a) {
+  const DomDev &D = a.doms[0];
+  const long long ncell = D.ncell, plane = (long long)D.nx * D.ny;
+  const R *Yo = reinterpret_cast<const R *>(a.Ys);
+  R *lam = reinterpret_cast<R *>(a.lam_s);
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell;
+       c += (long long)gridDim.x * blockDim.x) {
+    R y[L::NV];
+    double l[L::NV];
+#pragma unroll
+    for (int v = 0; v < L::NV; ++v) {
+      y[v] = Yo[v * ncell + c];
+      l[v] = double(lam[v * ncell + c]);
+    }
+    satadj_adj_cell<R, L>(a.ph, y, D.e_ref[c / plane], l);
+#pragma unroll
+    for (int v = 0; v < L::NV; ++v) lam[v * ncell + c] = R(l[v]);
+  }
+}
+
 template <class R, class L>
 struct AdjFamily {
   static cudaError_t face(const AdjArgs &a, long long nfaces, cudaStream_t s) {
@@ -384,10 +562,16 @@ struct AdjFamily {
     adj_cell_kernel<R, L><<<int(g < 9728 ? g : 9728), 128, 0, s>>>(a);
     return cudaGetLastError();
   }
+  static cudaError_t satadj(const AdjArgs &a, long long ncell, cudaStream_t s) {
+    long long g = (ncell + 127) / 128;
+    adj_satadj_kernel<R, L><<<int(g < 9728 ? g : 9728), 128, 0, s>>>(a);
+    return cudaGetLastError();
+  }
   static AdjKernels get() {
     AdjKernels k;
     k.face = &face;
     k.cell = &cell;
+    k.satadj = L::MOIST ? &satadj : nullptr;
     return k;
   }
 };

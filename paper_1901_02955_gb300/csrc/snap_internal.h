@@ -131,10 +131,13 @@ struct AdjKernels {
   // faces of every direction in one launch (nfaces: total over the directions)
   cudaError_t (*face)(const AdjArgs &, long long nfaces, cudaStream_t);
   cudaError_t (*cell)(const AdjArgs &, long long ncell, cudaStream_t);
+  // transpose of the saturation adjustment at the stage output Ys, applied to lam_s in
+  // place (nullptr for dry layouts)
+  cudaError_t (*satadj)(const AdjArgs &, long long ncell, cudaStream_t);
 };
 
-// Adjoint kernels of the dry inviscid layouts; false when not built.
-bool find_adjoint_kernels(int f32, int three_d, AdjKernels *out);
+// Adjoint kernels of the inviscid single-domain layouts; false when not built.
+bool find_adjoint_kernels(int f32, int nvap, int ncond, int three_d, AdjKernels *out);
 
 // Returns false when the configuration is not built into this library.
 bool find_kernels(int f32, int nvap, int ncond, int three_d, int visc, KernelSet *out);

@@ -1,8 +1,11 @@
-"""Discrete adjoint in the CUDA library against the oracle's adjoint
-(whose own pins are central differences of the oracle step), against central differences of
-the library's forward run, between FP32 and FP64, and across checkpoint spacings; and the
-gradient of the final kinetic energy with respect to the initial potential temperature
-through torch.autograd against central differences."""
+"""Discrete adjoint in the CUDA library, dry and moist, against the
+oracle's adjoint (whose own pins are central differences of the oracle step), against central
+differences of the library's forward run, between FP32 and FP64, and across checkpoint
+spacings; and the gradients of the final kinetic energy and of a column's cloud mass with
+respect to the initial potential temperature through torch.autograd against central
+differences."""
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -182,7 +185,7 @@ def test_kinetic_energy_gradient_wrt_initial_theta_moving_flow(torch):
     """dJ/dtheta_0 through torch.autograd (initial-state map in torch, steps and their
     adjoint in the library) against central differences along random directions, for a
     bubble in a random flow (no face with u* = 0, so J is differentiable)."""
-    theta_gradient_check(torch, moving=True, tol=1e-6)
+    theta_gradient_check(torch, moving=True, tol=1e-6, ndir=32)
 
 
 def test_kinetic_energy_gradient_wrt_initial_theta_from_rest(torch):
@@ -191,3 +194,105 @@ def test_kinetic_energy_gradient_wrt_initial_theta_from_rest(torch):
     by face; central differences average whole products of one-sided Jacobians, which
     differ at second order in the kink jumps (~1e-3 relative here)."""
     theta_gradient_check(torch, moving=False, tol=1e-4)
+
+
+# ------------------------------------------------------------------------------------------
+# moist (one vapour, cloud and rain, x-z): saturation adjustment after every stage
+# ------------------------------------------------------------------------------------------
+def moist_case(n=20):
+    """Moist adjoint bubble (cloud forms in its core at the first adjustment) with random
+    motion and pressure waves; the adjustment iterated to rounding."""
+    w = with_pressure_waves(W.add_random_motion(W.moist_adjoint_bubble(n=n)))
+    return dataclasses.replace(w, satadj_tol=1e-14, satadj_max_iter=200)
+
+
+def test_moist_fp64_adjoint_matches_oracle(torch):
+    from paper_1901_02955_gb300 import Context
+    w = moist_case()
+    dt = Oracle(w).dt_cfl(w.Y, 0.8)
+    nsteps = 4
+    lam = np.random.default_rng(51).normal(size=w.Y.shape)
+    ctx = Context(w, dtype="f64")
+    ctx.set_state(w.Y)
+    ctx.record(nsteps, ckpt_every=3, dt_fixed=dt)
+    got = ctx.step_adjoint(nsteps, lam)
+    assert np.sum(ctx.get_state()[2] > 0) > 20  # cloud present in the final state
+    want = oracle_adjoint(w, nsteps, dt, lam)
+    for f in range(w.nv):
+        err = np.linalg.norm(got[f] - want[f]) / np.linalg.norm(want)
+        assert err < 1e-10, (f, err)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_moist_adjoint_same_with_and_without_recomputation(torch, dtype):
+    from paper_1901_02955_gb300 import Context
+    w = moist_case()
+    ft = np.float32 if dtype == "f32" else np.float64
+    lam = np.random.default_rng(52).normal(size=w.Y.shape).astype(ft)
+    outs = []
+    for k in (0, 2, 5):
+        ctx = Context(w, dtype=dtype)
+        ctx.set_state(w.Y)
+        ctx.record(5, ckpt_every=k)
+        outs.append(ctx.step_adjoint(5, lam))
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
+
+
+def test_moist_fp32_adjoint_tracks_fp64_adjoint(torch):
+    from paper_1901_02955_gb300 import Context
+    w = moist_case()
+    dt = Oracle(w).dt_cfl(w.Y, 0.8)
+    lam = np.random.default_rng(53).normal(size=w.Y.shape)
+    res = {}
+    for dt_name in ("f64", "f32"):
+        ctx = Context(w, dtype=dt_name)
+        ctx.set_state(w.Y)
+        ctx.record(4, ckpt_every=2, dt_fixed=dt)
+        res[dt_name] = ctx.step_adjoint(4, lam.astype(np.float32 if dt_name == "f32" else np.float64))
+    a, b = res["f32"].astype(np.float64), res["f64"]
+    assert np.linalg.norm(a - b) <= 1e-3 * np.linalg.norm(b)
+
+
+def test_cloud_mass_gradient_wrt_initial_theta(torch):
+    """dJ/dtheta_0 of the cloud mass of the bubble's centre column after 12 steps (cloud
+    forms in the supersaturated core at the first adjustment and changes with the
+    temperature there), through torch.autograd, against Richardson-extrapolated central
+    differences along 16 random directions, FP64, in a random flow."""
+    from paper_1901_02955_gb300 import Context
+    from paper_1901_02955_gb300.autograd import (SnapSteps, moist_state_from_theta,
+                                                 column_cloud_mass)
+    w = dataclasses.replace(W.moist_adjoint_bubble(n=48), satadj_tol=1e-14,
+                            satadj_max_iter=200)
+    vap = w.vapors[0]
+    c_vd = w.R_d / (w.gamma_d - 1.0)
+    kappa = (w.gamma_d - 1.0) / w.gamma_d
+    pk_np = 0.5 * (w.p_bar_face[:-1] + w.p_bar_face[1:])
+    T = w.Y[-1] / (c_vd * w.Y[0] + vap.sigma_v * c_vd * w.Y[1])  # at rest, no condensate
+    theta0 = torch.tensor(T * (1e5 / pk_np[:, None, None]) ** kappa, device="cuda")
+    qv = torch.tensor(w.Y[1] / (w.Y[0] + w.Y[1]), device="cuda")
+    pk = torch.tensor(pk_np, device="cuda")
+    rs = np.random.default_rng(54)
+    vel = torch.tensor(rs.uniform(-2.0, 2.0, size=(2,) + theta0.shape), device="cuda")
+    ctx = Context(w, dtype="f64")
+    dt = 0.5 * Oracle(w).dt_cfl(w.Y, 0.8)
+    nsteps = 12
+
+    def J(theta):
+        Y0 = moist_state_from_theta(theta, pk, qv, w.R_d, w.gamma_d, vap.eps, vap.sigma_v,
+                                    n_cond=w.ncond, velocity=vel)
+        YN = SnapSteps.apply(Y0.contiguous(), ctx, nsteps, 5, dt)
+        return column_cloud_mass(YN, w.dz, i=w.nx // 2)
+
+    th = theta0.clone().requires_grad_(True)
+    j0 = J(th)
+    assert j0.item() > 0.0
+    j0.backward()
+    grad = th.grad.detach()
+    assert float(grad.abs().max()) > 0.0
+    for _ in range(16):
+        d = torch.tensor(rs.normal(size=theta0.shape), device="cuda")
+        with torch.no_grad():
+            def fd(h):
+                return (J(theta0 + h * d) - J(theta0 - h * d)).item() / (2 * h)
+            rich = (4.0 * fd(1e-4) - fd(2e-4)) / 3.0
+        assert rich == pytest.approx(float((grad * d).sum()), rel=1e-6)

@@ -230,10 +230,13 @@ def test_satadj_sweep_limit_is_reported():
     assert e.value.code == capi.ENOCONV
 
 
-def test_adjoint_entry_reports_not_supported_for_moist_contexts():
+@pytest.mark.parametrize("make", [lambda: W.jovian(nx=4, ny=4, nz=8),
+                                  lambda: W.density_current(nx=16, nz=8)],
+                         ids=["moist_3d", "viscous"])
+def test_adjoint_entry_reports_not_supported(make):
     import ctypes
     from paper_1901_02955_gb300 import capi
-    w = W.moist_bubble(n=8)
+    w = make()
     ctx = Context(w)
     buf = np.zeros(w.Y.shape)
     out = np.zeros(w.Y.shape)

@@ -402,6 +402,35 @@ def moist_bubble(n=64, L=1000.0, A=0.5, R=250.0, xc=500.0, zc=450.0, rh=0.9, nst
                     rho_bar=rho_bar, p_bar_face=pf, Y=Y, nsteps=nsteps, dtype=dtype, seed=seed)
 
 
+def moist_adjoint_bubble(n=256, rh=0.95, rh_core=1.05, A=0.5, R=250.0, xc=500.0, zc=260.0,
+                         dtype="f64", nsteps=400):
+    """Moist variant of the adjoint bubble: the warm bubble of the first workload (+A K,
+    radius R at (xc, zc) on an n x n grid over 1 km) in Earth air with water vapour at
+    relative humidity rh of the background, and at rh_core of saturation at the perturbed
+    temperature inside the bubble (pressure unchanged), so that the first saturation
+    adjustment forms cloud there; cloud and rain start at 0; walls."""
+    w = moist_bubble(n=n, A=A, R=R, xc=xc, zc=zc, rh=rh, nsteps=nsteps, dtype=dtype)
+    vap = w.vapors[0]
+    kappa = (w.gamma_d - 1.0) / w.gamma_d
+    pk = 0.5 * (w.p_bar_face[:-1] + w.p_bar_face[1:])
+    x = _cell_centres(w.nx, w.dx)[None, :]
+    z = _cell_centres(w.nz, w.dz)[:, None]
+    shape = cosine_bubble(A, xc, zc, R)(x, z)
+    T = (300.0 + shape) * (pk[:, None] / 1e5) ** kappa
+    core = shape > 0.0
+    pv = rh_core * _sat_pressure(vap, w.R_d, w.gamma_d, T)
+    P = pk[:, None] * np.ones_like(T)
+    rho_d = (P - pv) / (w.R_d * T)
+    rho_v = pv / ((w.R_d / vap.eps) * T)
+    Y = w.Y.copy()
+    Yc = _assemble(w.nx, 1, w.nz, rho_d[:, None, :], [rho_v[:, None, :]], T[:, None, :],
+                   w.R_d, w.gamma_d, [vap], w.ncond)
+    Y[:, core[:, None, :]] = Yc[:, core[:, None, :]]
+    w = w.with_state(Y)
+    w.name = f"moist_adjoint_bubble_{n}x{n}"
+    return w
+
+
 def ensemble(sizes=(64, 128, 256, 512), per_size=24, seed=BASE_SEED + 4, nsteps=200):
     """Ensemble of 2-D moist bubbles of uneven sizes on 1 km boxes: amplitude ~ U(0.2, 2) K
     and radius ~ U(150, 400) m drawn per member from the seeded stream."""
