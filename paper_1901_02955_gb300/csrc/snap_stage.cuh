@@ -558,6 +558,50 @@ __device__ __forceinline__ void weno5_pair(R a, R b, R c, R d, R e, R eps, R &qm
   qp = (g2 * p0 + g1 * p1 + g0 * p2) * Ar<R>::rcp(Sp);
 }
 
+// weno5_pair<float> for two variables at once on the packed FP32x2 pipe of sm_100-class SMs
+// (one instruction per two lanes of arithmetic: the reconstruction is issue-bound); the
+// reciprocals stay scalar on the special-function unit.
+__device__ __forceinline__ float2 f2c(float x) { return make_float2(x, x); }
+__device__ __forceinline__ float2 f2rcp(float2 x) {
+  return make_float2(__fdividef(1.0f, x.x), __fdividef(1.0f, x.y));
+}
+__device__ __forceinline__ void weno5_pair2(float2 a, float2 b, float2 c, float2 d, float2 e,
+                                            float eps, float2 &qm, float2 &qp) {
+  const float2 k1312 = f2c(13.0f / 12.0f), kq = f2c(0.25f);
+  float2 t = __ffma2_rn(f2c(-2.0f), b, __fadd2_rn(a, c));
+  float2 b0 = __fmul2_rn(__fmul2_rn(k1312, t), t);
+  t = __ffma2_rn(f2c(-4.0f), b, __ffma2_rn(f2c(3.0f), c, a));
+  b0 = __ffma2_rn(__fmul2_rn(kq, t), t, b0);
+  t = __ffma2_rn(f2c(-2.0f), c, __fadd2_rn(b, d));
+  float2 b1 = __fmul2_rn(__fmul2_rn(k1312, t), t);
+  t = __ffma2_rn(f2c(-1.0f), d, b);
+  b1 = __ffma2_rn(__fmul2_rn(kq, t), t, b1);
+  t = __ffma2_rn(f2c(-2.0f), d, __fadd2_rn(c, e));
+  float2 b2 = __fmul2_rn(__fmul2_rn(k1312, t), t);
+  t = __ffma2_rn(f2c(3.0f), c, __ffma2_rn(f2c(-4.0f), d, e));
+  b2 = __ffma2_rn(__fmul2_rn(kq, t), t, b2);
+  const float2 ke = f2c(eps);
+  float2 g0 = f2rcp(__fadd2_rn(ke, b0)), g1 = f2rcp(__fadd2_rn(ke, b1)),
+         g2 = f2rcp(__fadd2_rn(ke, b2));
+  g0 = __fmul2_rn(g0, g0);
+  g1 = __fmul2_rn(g1, g1);
+  g2 = __fmul2_rn(g2, g2);
+  const float2 m0 = __ffma2_rn(f2c(0.1f / 3.0f), a,
+                               __ffma2_rn(f2c(-0.7f / 6.0f), b, __fmul2_rn(f2c(1.1f / 6.0f), c)));
+  const float2 m1 = __ffma2_rn(f2c(-0.1f), b, __ffma2_rn(f2c(0.5f), c, __fmul2_rn(f2c(0.2f), d)));
+  const float2 m2 = __ffma2_rn(f2c(0.1f), c, __ffma2_rn(f2c(0.25f), d, __fmul2_rn(f2c(-0.05f), e)));
+  const float2 p0 = __ffma2_rn(f2c(0.1f / 3.0f), e,
+                               __ffma2_rn(f2c(-0.7f / 6.0f), d, __fmul2_rn(f2c(1.1f / 6.0f), c)));
+  const float2 p1 = __ffma2_rn(f2c(-0.1f), d, __ffma2_rn(f2c(0.5f), c, __fmul2_rn(f2c(0.2f), b)));
+  const float2 p2 = __ffma2_rn(f2c(0.1f), c, __ffma2_rn(f2c(0.25f), b, __fmul2_rn(f2c(-0.05f), a)));
+  const float2 Sm = __ffma2_rn(f2c(0.1f), g0, __ffma2_rn(f2c(0.6f), g1, __fmul2_rn(f2c(0.3f), g2)));
+  const float2 Sp = __ffma2_rn(f2c(0.1f), g2, __ffma2_rn(f2c(0.6f), g1, __fmul2_rn(f2c(0.3f), g0)));
+  const float2 nm = __ffma2_rn(g0, m0, __ffma2_rn(g1, m1, __fmul2_rn(g2, m2)));
+  const float2 np = __ffma2_rn(g2, p0, __ffma2_rn(g1, p1, __fmul2_rn(g0, p2)));
+  qm = __fmul2_rn(nm, f2rcp(Sm));
+  qp = __fmul2_rn(np, f2rcp(Sp));
+}
+
 // CFL rate sum_d (|u_d| + c) / dx_d in the kernel's type (FP32 kernels: FP32; the time step
 // only needs a few digits). The energy entry is stored as rho e - eref.
 template <class R, class L>
@@ -790,14 +834,44 @@ __device__ __forceinline__ void stage_tiles(const StageArgs &a, const int stage,
             const int fl = ((lz + fz) * sy + (ly + fy)) * sx + (lx + fx);  // face c+1/2
             const int fr = (lz * sy + ly) * sx + lx;                        // face c-1/2
             const bool has_l = ld < ed, has_r = ld >= 0;
+            if constexpr (sizeof(R) == 4) {
+              // two variables per packed FP32x2 instruction, the odd one alone
 #pragma unroll
-            for (int v = 0; v < NV; ++v) {
-              const R *q = s_prim + v * B::NBOX + bi;
-              R qm, qp;
-              weno5_pair<R>(q[-2 * stride], q[-stride], q[0], q[stride], q[2 * stride], weps,
-                            qm, qp);
-              if (has_l) s_fl[v * B::NF + fl] = qm;
-              if (has_r) s_fr[v * B::NF + fr] = qp;
+              for (int v = 0; v + 1 < NV; v += 2) {
+                const R *q = s_prim + v * B::NBOX + bi;
+                const R *r2 = q + B::NBOX;
+                float2 qm, qp;
+                weno5_pair2(make_float2(q[-2 * stride], r2[-2 * stride]),
+                            make_float2(q[-stride], r2[-stride]), make_float2(q[0], r2[0]),
+                            make_float2(q[stride], r2[stride]),
+                            make_float2(q[2 * stride], r2[2 * stride]), weps, qm, qp);
+                if (has_l) {
+                  s_fl[v * B::NF + fl] = qm.x;
+                  s_fl[(v + 1) * B::NF + fl] = qm.y;
+                }
+                if (has_r) {
+                  s_fr[v * B::NF + fr] = qp.x;
+                  s_fr[(v + 1) * B::NF + fr] = qp.y;
+                }
+              }
+              if constexpr (NV % 2 == 1) {
+                const R *q = s_prim + (NV - 1) * B::NBOX + bi;
+                R qm, qp;
+                weno5_pair<R>(q[-2 * stride], q[-stride], q[0], q[stride], q[2 * stride],
+                              weps, qm, qp);
+                if (has_l) s_fl[(NV - 1) * B::NF + fl] = qm;
+                if (has_r) s_fr[(NV - 1) * B::NF + fr] = qp;
+              }
+            } else {
+#pragma unroll
+              for (int v = 0; v < NV; ++v) {
+                const R *q = s_prim + v * B::NBOX + bi;
+                R qm, qp;
+                weno5_pair<R>(q[-2 * stride], q[-stride], q[0], q[stride], q[2 * stride],
+                              weps, qm, qp);
+                if (has_l) s_fl[v * B::NF + fl] = qm;
+                if (has_r) s_fr[v * B::NF + fr] = qp;
+              }
             }
           }
         }
