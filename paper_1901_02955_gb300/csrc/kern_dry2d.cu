@@ -5,13 +5,14 @@ namespace snap {
 
 bool find_kernels_dry2d(int f32, int visc, KernelSet *out) {
   using L = Lay<0, 0, false>;
-  using A = TileT<32, 1, 14>;
+  using A = TileT<32, 1, 14, 256, 4>;  // FP32: compiled for 4 CTAs per SM (64 registers)
+  using A64 = TileT<32, 1, 14, 256, 2>;  // FP64: 2 CTAs per SM (128 registers)
   using B = TileT<64, 1, 6>;
   using C = TileT<16, 1, 30>;
   if (f32)
     *out = visc ? Family<float, L>::set<true, A, B, C>() : Family<float, L>::set<false, A, B, C>();
   else
-    *out = visc ? Family<double, L>::set<true, A>() : Family<double, L>::set<false, A>();
+    *out = visc ? Family<double, L>::set<true, A64>() : Family<double, L>::set<false, A64>();
   return true;
 }
 

@@ -79,9 +79,11 @@ template <>
 __device__ __forceinline__ const CstT<double> &cst<double>(const StageArgs &a) { return a.cd; }
 
 // Tile shape: TX x TY x TZ owned cells per CTA of NT threads (TY = 1 in the x-z plane).
-template <int TX_, int TY_, int TZ_, int NT_ = 256>
+// MINB: CTAs per SM the kernel is compiled for (second __launch_bounds__ argument), which caps
+// its registers; 0 leaves the register count to the compiler.
+template <int TX_, int TY_, int TZ_, int NT_ = 256, int MINB_ = 0>
 struct TileT {
-  static constexpr int TX = TX_, TY = TY_, TZ = TZ_, NT = NT_;
+  static constexpr int TX = TX_, TY = TY_, TZ = TZ_, NT = NT_, MINB = MINB_;
 };
 
 template <class T, bool D3>
@@ -512,6 +514,34 @@ __device__ __forceinline__ double block_max(double v, double *red) {
   return v;
 }
 
+__device__ __forceinline__ float block_max_f(float v, float *red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    v = (l < int(blockDim.x >> 5)) ? red[l] : 0.0f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  }
+  return v;
+}
+
+// Asynchronous global -> shared copy of one element (cp.async, completed by cp_async_wait):
+// the stage input Y^n of the owned cells is fetched while the tile is being computed.
+template <class R>
+__device__ __forceinline__ void cp_async_elem(R *smem_dst, const R *gmem_src) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+  if constexpr (sizeof(R) == 4)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem_src) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 // ------------------------------------------------------------------------------------------
 // the fused stage kernel
 // ------------------------------------------------------------------------------------------
@@ -633,7 +663,7 @@ __device__ __forceinline__ R cell_rate_r(const CstT<R> &C, const R *y, R eref, R
   // p = R_d R_m T and T = U / (c_vd C_v), with R_m, C_v here the sums over densities
   const R p = C.gm1 * Rm * Ar<R>::div(U, Cv);
   const R gam = R(1) + C.gm1 * Ar<R>::div(den, num);
-  const R c = Ar<R>::sqrt_(gam * p * ir);
+  const R c = Ar<R>::sqrt_pos(gam * p * ir);
   R r = (fabs(y[L::mom(0)]) * ir + c) * idx + (fabs(y[L::mom(2)]) * ir + c) * idz;
   if constexpr (L::D3) r += (fabs(y[L::mom(1)]) * ir + c) * idy;
   return r;
@@ -646,7 +676,13 @@ struct StageSmem {
   static constexpr size_t visc = VISC ? sizeof(R) * 2 * B::NBOX : 0;
   static constexpr size_t face = sizeof(R) * 2 * L::NV * B::NF;  // left state/flux, right state
   static constexpr size_t red = 32 * sizeof(double);
-  static constexpr size_t total = prim + visc + face + red;
+  static constexpr size_t base = prim + visc + face + red;
+  // Y^n of the owned cells, prefetched by cp.async, when it costs no resident CTA per SM
+  // (228 KB of shared memory per SM, 1 KB reserved per CTA)
+  static constexpr size_t yn_bytes = sizeof(R) * L::NV * B::NCELL;
+  static constexpr bool PREFETCH = 233472 / (base + yn_bytes + 1024) >= 233472 / (base + 1024);
+  static constexpr size_t yn = PREFETCH ? yn_bytes : 0;
+  static constexpr size_t total = base + yn;
 };
 
 // Grid-wide barrier of the persistent step kernel (all CTAs co-resident by a cooperative
@@ -693,6 +729,7 @@ __device__ __forceinline__ void stage_tiles(const StageArgs &a, const int stage,
   R *s_fl = reinterpret_cast<R *>(smem + S::prim + S::visc);  // left states, then fluxes
   R *s_fr = s_fl + NV * B::NF;                                 // right states
   double *s_red = reinterpret_cast<double *>(smem + S::prim + S::visc + S::face);
+  R *s_yn = reinterpret_cast<R *>(smem + S::base);  // used when S::PREFETCH
   const Phys &ph = a.ph;
   const CstT<R> &C = cst<R>(a);
   const R weps = C.weno_eps;
@@ -726,6 +763,21 @@ __device__ __forceinline__ void stage_tiles(const StageArgs &a, const int stage,
     }
 
     // ---- 1. owned cells: load, keep the conserved values, store primitives -------------
+    if constexpr (S::PREFETCH) {
+      if (stage != 0) {
+#pragma unroll
+        for (int m = 0; m < B::CPT; ++m) {
+          const int c = tid + m * NT;
+          const int lx = c % TX, ly = (c / TX) % TY, lz = c / (TX * TY);
+          if (c < B::NCELL && lx < ex && ly < ey && lz < ez) {
+            const long long g = ((long long)(z0 + lz) * ny + (y0 + ly)) * nx + (x0 + lx);
+#pragma unroll
+            for (int v = 0; v < NV; ++v) cp_async_elem<R>(s_yn + v * B::NCELL + c, Yn + v * ncell + g);
+          }
+        }
+        cp_async_commit();
+      }
+    }
     R ys[B::CPT][NV];
 #pragma unroll
     for (int m = 0; m < B::CPT; ++m) {
@@ -933,6 +985,9 @@ __device__ __forceinline__ void stage_tiles(const StageArgs &a, const int stage,
     }
 
     // ---- 4. gravity source, stage combine, saturation adjustment, store ------------------
+    if constexpr (S::PREFETCH) {
+      if (stage != 0) cp_async_wait();  // this thread's own copies of Y^n
+    }
     R rate_max = R(0);
 #pragma unroll
     for (int m = 0; m < B::CPT; ++m) {
@@ -962,7 +1017,7 @@ __device__ __forceinline__ void stage_tiles(const StageArgs &a, const int stage,
           if (stage == 0) {
             yo[v] = s1;
           } else {
-            const R yn = Yn[v * ncell + g];
+            const R yn = S::PREFETCH ? s_yn[v * B::NCELL + c] : Yn[v * ncell + g];
             yo[v] = stage == 1 ? R(0.75) * yn + R(0.25) * s1
                                : yn * R(1.0 / 3.0) + R(2.0 / 3.0) * s1;
           }
@@ -989,7 +1044,11 @@ __device__ __forceinline__ void stage_tiles(const StageArgs &a, const int stage,
       }
     }
     if (stage == 2) {
-      double bm = block_max(double(rate_max), s_red + 1);
+      double bm;
+      if constexpr (sizeof(R) == 4)
+        bm = double(block_max_f(rate_max, reinterpret_cast<float *>(s_red + 1)));
+      else
+        bm = block_max(rate_max, s_red + 1);
       if (tid == 0) atomicMax(D.rate, (unsigned long long)__double_as_longlong(bm));
     }
     __syncthreads();
@@ -998,7 +1057,7 @@ __device__ __forceinline__ void stage_tiles(const StageArgs &a, const int stage,
 
 // One Runge-Kutta stage over all tiles of all domains.
 template <class R, class L, bool VISC, class T>
-__global__ void __launch_bounds__(T::NT) stage_kernel(const StageArgs a) {
+__global__ void __launch_bounds__(T::NT, T::MINB) stage_kernel(const StageArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   stage_tiles<R, L, VISC, T>(a, a.stage, smem);
 }
@@ -1006,7 +1065,7 @@ __global__ void __launch_bounds__(T::NT) stage_kernel(const StageArgs a) {
 // One whole step (three stages) in a single persistent cooperative launch: the CTAs walk the
 // tile queue of every domain per stage and meet at a grid barrier between stages.
 template <class R, class L, bool VISC, class T>
-__global__ void __launch_bounds__(T::NT) step_kernel(const StageArgs a) {
+__global__ void __launch_bounds__(T::NT, T::MINB) step_kernel(const StageArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
 #pragma unroll 1
   for (int st = 0; st < 3; ++st) {
