@@ -301,6 +301,8 @@ static StageArgs args_of(snap_ctx *ctx, int stage) {
   a.max_sweeps = ctx->sweeps_dev;
   a.gsync = ctx->gsync;
   a.dt_override = -1.0;
+  a.buf_s = a.buf_n = nullptr;
+  a.buf_o = nullptr;
   a.ph = ctx->ph;
   // stop tolerance of the adjustment: at least 32 machine epsilons of the arithmetic type
   derive_cst<float>(ctx->ph, 32.0 * 1.1920928955078125e-07, a.cf);
@@ -744,11 +746,16 @@ static int satadj_adjoint(snap_ctx *ctx, const StageArgs &sa, const void *Yout, 
   return SNAP_OK;
 }
 
-// One forward stage; dt > 0 is passed in the launch arguments (the recorded time step).
-static int plain_stage(snap_ctx *ctx, const StageArgs &base, int stage, double dt) {
+// One forward stage; dt > 0 is passed in the launch arguments (the recorded time step). With
+// ys/yn/yo set, the stage reads and writes those states instead of the domain's buffers.
+static int plain_stage(snap_ctx *ctx, const StageArgs &base, int stage, double dt,
+                       const void *ys = nullptr, const void *yn = nullptr, void *yo = nullptr) {
   StageArgs a = base;
   a.stage = stage;
   a.dt_override = dt;
+  a.buf_s = ys;
+  a.buf_n = yn;
+  a.buf_o = yo;
   CK(ctx->ks.var[ctx->tv].stage(a, ctx->grid, ctx->stream));
   return SNAP_OK;
 }
@@ -782,7 +789,9 @@ extern "C" int snap_record(snap_ctx *ctx, int nsteps, int ckpt_every, double dt_
       if (d == 1 && !ctx->three_d) continue;
       long long nf = (long long)(D.nx + (d == 0)) * (D.ny + (d == 1)) * (D.nz + (d == 2));
       ctx->gface_off[d] = off;
-      off += (size_t)nf * ctx->nv * 6 * ctx->word;
+      // per face and stencil slot, the fields padded to a 16-byte vector
+      const int w = 16 / ctx->word, nvp = (ctx->nv + w - 1) / w * w;
+      off += (size_t)nf * nvp * 6 * ctx->word;
     }
     CK(cudaMalloc(&ctx->gface, off));
   }
@@ -796,14 +805,17 @@ extern "C" int snap_record(snap_ctx *ctx, int nsteps, int ckpt_every, double dt_
   }
   for (int n = 0; n < nsteps; ++n) {
     if (store_all) {
-      // three launches per step, each stage's input kept in the record
+      // three launches per step writing straight into the record: the inputs of the stages
+      // of step n are slots 3n, 3n+1, 3n+2; stage 2 writes the next step's slot (the
+      // context's state after the last step)
       const DomDev &D = ctx->dom[0];
       char *slot = (char *)ctx->segbuf + sb * 3 * n;
-      for (int st = 0; st < 3; ++st) {
-        CK(cudaMemcpyAsync(slot + sb * st, D.buf[st], sb, cudaMemcpyDeviceToDevice, ctx->stream));
-        int rc = plain_stage(ctx, base, st, -1.0);
-        if (rc) return rc;
-      }
+      if (n == 0) CK(cudaMemcpyAsync(slot, D.buf[0], sb, cudaMemcpyDeviceToDevice, ctx->stream));
+      void *next = n + 1 < nsteps ? (void *)(slot + 3 * sb) : D.buf[0];
+      int rc = plain_stage(ctx, base, 0, -1.0, slot, slot, slot + sb);
+      if (!rc) rc = plain_stage(ctx, base, 1, -1.0, slot + sb, slot, slot + 2 * sb);
+      if (!rc) rc = plain_stage(ctx, base, 2, -1.0, slot + 2 * sb, slot, next);
+      if (rc) return rc;
     } else {
       if (n % ckpt_every == 0)
         CK(cudaMemcpyAsync((char *)ctx->ckpt + sb * (n / ckpt_every), ctx->dom[0].buf[0], sb,
@@ -893,17 +905,14 @@ extern "C" int snap_step_adjoint(snap_ctx *ctx, int nsteps, const void *lambda_f
   for (int seg = nseg - 1; seg >= 0 && rc == SNAP_OK; --seg) {
     const int n0 = seg * K, n1 = (n0 + K < nsteps) ? n0 + K : nsteps;
     // recompute the segment forward, keeping Y^n and both intermediate stages of each step
-    if (!store_all)
-      CK(cudaMemcpyAsync(D.buf[0], (char *)ctx->ckpt + sb * seg, sb, cudaMemcpyDeviceToDevice, ctx->stream));
     for (int s = n0; s < n1 && rc == SNAP_OK && !store_all; ++s) {
       char *slot = (char *)ctx->segbuf + sb * 3 * (s - n0);
-      CK(cudaMemcpyAsync(slot, D.buf[0], sb, cudaMemcpyDeviceToDevice, ctx->stream));
+      if (s == n0)
+        CK(cudaMemcpyAsync(slot, (char *)ctx->ckpt + sb * seg, sb, cudaMemcpyDeviceToDevice, ctx->stream));
       const double dt = ctx->rec_dt[s];
-      if ((rc = plain_stage(ctx, base, 0, dt))) break;
-      CK(cudaMemcpyAsync(slot + sb, D.buf[1], sb, cudaMemcpyDeviceToDevice, ctx->stream));
-      if ((rc = plain_stage(ctx, base, 1, dt))) break;
-      CK(cudaMemcpyAsync(slot + 2 * sb, D.buf[2], sb, cudaMemcpyDeviceToDevice, ctx->stream));
-      if (s < n1 - 1) rc = plain_stage(ctx, base, 2, dt);
+      if ((rc = plain_stage(ctx, base, 0, dt, slot, slot, slot + sb))) break;
+      if ((rc = plain_stage(ctx, base, 1, dt, slot + sb, slot, slot + 2 * sb))) break;
+      if (s < n1 - 1) rc = plain_stage(ctx, base, 2, dt, slot + 2 * sb, slot, slot + 3 * sb);
     }
     for (int s = n1 - 1; s >= n0 && rc == SNAP_OK; --s) {
       const double dt = ctx->rec_dt[s];

@@ -12,7 +12,7 @@
 //   adj_face_kernel (one launch for the faces of every direction): one thread per face
 //     recomputes the face states from its six-cell stencil, transposes LMARS and WENO5, and
 //     writes the contribution of the face to each of its six stencil cells into
-//     G[d][v][s][face];
+//     G[d][face][s][v] (v padded to a 16-byte vector, so that each slot moves as one access);
 //   adj_cell_kernel: one thread per cell gathers the contributions of every face whose
 //     stencil holds the cell (or a ghost image of it), transposes the primitive map and the
 //     gravity source, and forms the stage combine.
@@ -20,6 +20,31 @@
 #include "snap_stage.cuh"
 
 namespace snap {
+
+// Face contributions are stored per face and stencil slot as NVP values (the field count
+// padded to a multiple of one 16-byte vector: 4 floats or 2 doubles).
+template <class R>
+struct GVec;
+template <>
+struct GVec<float> {
+  using V = float4;
+  static constexpr int W = 4;
+  static __device__ __forceinline__ float get(const V &x, int e) {
+    return e == 0 ? x.x : (e == 1 ? x.y : (e == 2 ? x.z : x.w));
+  }
+  static __device__ __forceinline__ V make(const float *p) { return make_float4(p[0], p[1], p[2], p[3]); }
+};
+template <>
+struct GVec<double> {
+  using V = double2;
+  static constexpr int W = 2;
+  static __device__ __forceinline__ double get(const V &x, int e) { return e == 0 ? x.x : x.y; }
+  static __device__ __forceinline__ V make(const double *p) { return make_double2(p[0], p[1]); }
+};
+template <class R, int NV>
+constexpr int g_stride() {
+  return (NV + GVec<R>::W - 1) / GVec<R>::W * GVec<R>::W;
+}
 
 template <class R>
 __device__ __forceinline__ const CstT<R> &acst(const AdjArgs &a);
@@ -84,6 +109,69 @@ __device__ __forceinline__ R weno5_grad(const R q[5], R eps, R g[5]) {
     for (int k = 0; k < 3; ++k) gj += al[k] * iS * dv[k][j] + cb[k] * db[k][j];
     g[j] = gj;
   }
+  return I;
+}
+
+// weno5_grad<float> of two variables at once on the packed FP32x2 pipe (reciprocals scalar).
+__device__ __forceinline__ float2 weno5_grad2(const float2 q[5], float eps, float2 g[5]) {
+  const float2 k1312 = f2c(13.0f / 12.0f), kq = f2c(0.25f), k136 = f2c(13.0f / 6.0f);
+  const float2 k133 = f2c(-13.0f / 3.0f), kh = f2c(0.5f);
+  float2 b[3], db[3][5], t1, t2;
+  // beta_0 over (q0, q1, q2)
+  t1 = __ffma2_rn(f2c(-2.0f), q[1], __fadd2_rn(q[0], q[2]));
+  t2 = __ffma2_rn(f2c(-4.0f), q[1], __ffma2_rn(f2c(3.0f), q[2], q[0]));
+  b[0] = __ffma2_rn(__fmul2_rn(kq, t2), t2, __fmul2_rn(__fmul2_rn(k1312, t1), t1));
+  db[0][0] = __ffma2_rn(k136, t1, __fmul2_rn(kh, t2));
+  db[0][1] = __ffma2_rn(k133, t1, __fmul2_rn(f2c(-2.0f), t2));
+  db[0][2] = __ffma2_rn(k136, t1, __fmul2_rn(f2c(1.5f), t2));
+  // beta_1 over (q1, q2, q3)
+  t1 = __ffma2_rn(f2c(-2.0f), q[2], __fadd2_rn(q[1], q[3]));
+  t2 = __ffma2_rn(f2c(-1.0f), q[3], q[1]);
+  b[1] = __ffma2_rn(__fmul2_rn(kq, t2), t2, __fmul2_rn(__fmul2_rn(k1312, t1), t1));
+  db[1][1] = __ffma2_rn(k136, t1, __fmul2_rn(kh, t2));
+  db[1][2] = __fmul2_rn(k133, t1);
+  db[1][3] = __ffma2_rn(k136, t1, __fmul2_rn(f2c(-0.5f), t2));
+  // beta_2 over (q2, q3, q4)
+  t1 = __ffma2_rn(f2c(-2.0f), q[3], __fadd2_rn(q[2], q[4]));
+  t2 = __ffma2_rn(f2c(3.0f), q[2], __ffma2_rn(f2c(-4.0f), q[3], q[4]));
+  b[2] = __ffma2_rn(__fmul2_rn(kq, t2), t2, __fmul2_rn(__fmul2_rn(k1312, t1), t1));
+  db[2][2] = __ffma2_rn(k136, t1, __fmul2_rn(f2c(1.5f), t2));
+  db[2][3] = __ffma2_rn(k133, t1, __fmul2_rn(f2c(-2.0f), t2));
+  db[2][4] = __ffma2_rn(k136, t1, __fmul2_rn(kh, t2));
+  // candidates and weights
+  float2 v[3];
+  v[0] = __ffma2_rn(f2c(1.0f / 3.0f), q[0], __ffma2_rn(f2c(-7.0f / 6.0f), q[1], __fmul2_rn(f2c(11.0f / 6.0f), q[2])));
+  v[1] = __ffma2_rn(f2c(-1.0f / 6.0f), q[1], __ffma2_rn(f2c(5.0f / 6.0f), q[2], __fmul2_rn(f2c(1.0f / 3.0f), q[3])));
+  v[2] = __ffma2_rn(f2c(1.0f / 3.0f), q[2], __ffma2_rn(f2c(5.0f / 6.0f), q[3], __fmul2_rn(f2c(-1.0f / 6.0f), q[4])));
+  const float2 ke = f2c(eps);
+  float2 ib[3], al[3];
+  const float dk[3] = {0.1f, 0.6f, 0.3f};
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    ib[k] = f2rcp(__fadd2_rn(ke, b[k]));
+    al[k] = __fmul2_rn(__fmul2_rn(f2c(dk[k]), ib[k]), ib[k]);
+  }
+  const float2 S = __fadd2_rn(__fadd2_rn(al[0], al[1]), al[2]);
+  const float2 iS = f2rcp(S);
+  const float2 I = __fmul2_rn(__ffma2_rn(al[0], v[0], __ffma2_rn(al[1], v[1], __fmul2_rn(al[2], v[2]))), iS);
+  float2 w[3], cb[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    w[k] = __fmul2_rn(al[k], iS);
+    // (v_k - I)/S (-2 alpha_k / (eps + beta_k))
+    cb[k] = __fmul2_rn(__fmul2_rn(__ffma2_rn(f2c(-1.0f), I, v[k]), iS),
+                       __fmul2_rn(__fmul2_rn(f2c(-2.0f), al[k]), ib[k]));
+  }
+  // g_j = sum_k w_k dv_k/dq_j + cb_k dbeta_k/dq_j (zero entries skipped)
+  g[0] = __ffma2_rn(w[0], f2c(1.0f / 3.0f), __fmul2_rn(cb[0], db[0][0]));
+  g[1] = __ffma2_rn(w[0], f2c(-7.0f / 6.0f), __ffma2_rn(w[1], f2c(-1.0f / 6.0f),
+         __ffma2_rn(cb[0], db[0][1], __fmul2_rn(cb[1], db[1][1]))));
+  g[2] = __ffma2_rn(w[0], f2c(11.0f / 6.0f), __ffma2_rn(w[1], f2c(5.0f / 6.0f),
+         __ffma2_rn(w[2], f2c(1.0f / 3.0f), __ffma2_rn(cb[0], db[0][2],
+         __ffma2_rn(cb[1], db[1][2], __fmul2_rn(cb[2], db[2][2]))))));
+  g[3] = __ffma2_rn(w[1], f2c(1.0f / 3.0f), __ffma2_rn(w[2], f2c(5.0f / 6.0f),
+         __ffma2_rn(cb[1], db[1][3], __fmul2_rn(cb[2], db[2][3]))));
+  g[4] = __ffma2_rn(w[2], f2c(-1.0f / 6.0f), __fmul2_rn(cb[2], db[2][4]));
   return I;
 }
 
@@ -281,8 +369,35 @@ __device__ __forceinline__ void adj_face(const AdjArgs &a, const DomDev &D, cons
   }
   R QL[NV], QR[NV], gL[NV][5], gR[NV][5], QLb[NV], QRb[NV];
   const R weps = C.weno_eps;
+  constexpr int NPACK = sizeof(R) == 4 ? NV / 2 * 2 : 0;  // variables done in FP32x2 pairs
+  if constexpr (NPACK > 0) {
 #pragma unroll
-  for (int v = 0; v < NV; ++v) {
+    for (int v = 0; v < NPACK; v += 2) {
+      float2 q[5], g[5], I;
+#pragma unroll
+      for (int s = 0; s < 5; ++s) q[s] = make_float2(X[s][v], X[s][v + 1]);
+      I = weno5_grad2(q, weps, g);
+      QL[v] = I.x;
+      QL[v + 1] = I.y;
+#pragma unroll
+      for (int s = 0; s < 5; ++s) {
+        gL[v][s] = g[s].x;
+        gL[v + 1][s] = g[s].y;
+      }
+#pragma unroll
+      for (int s = 0; s < 5; ++s) q[s] = make_float2(X[5 - s][v], X[5 - s][v + 1]);
+      I = weno5_grad2(q, weps, g);
+      QR[v] = I.x;
+      QR[v + 1] = I.y;
+#pragma unroll
+      for (int s = 0; s < 5; ++s) {
+        gR[v][s] = g[s].x;
+        gR[v + 1][s] = g[s].y;
+      }
+    }
+  }
+#pragma unroll
+  for (int v = NPACK; v < NV; ++v) {
     R q[5];
 #pragma unroll
     for (int s = 0; s < 5; ++s) q[s] = X[s][v];
@@ -290,19 +405,29 @@ __device__ __forceinline__ void adj_face(const AdjArgs &a, const DomDev &D, cons
 #pragma unroll
     for (int s = 0; s < 5; ++s) q[s] = X[5 - s][v];
     QR[v] = weno5_grad<R>(q, weps, gR[v]);
-    QLb[v] = QRb[v] = R(0);
   }
+#pragma unroll
+  for (int v = 0; v < NV; ++v) QLb[v] = QRb[v] = R(0);
   const R pref = fz ? Prof<R>::pf(D, k) : Prof<R>::pc(D, k);
   lmars_adj<R, L>(C, QL, QR, DIR, pref, Fb, QLb, QRb);
+  constexpr int NVP = g_stride<R, NV>(), W = GVec<R>::W;
+  using Vec = typename GVec<R>::V;
+  Vec *Gf = reinterpret_cast<Vec *>(G + f * 6 * NVP);
 #pragma unroll
-  for (int v = 0; v < NV; ++v)
+  for (int s = 0; s < 6; ++s) {
+    R g[NVP];
 #pragma unroll
-    for (int s = 0; s < 6; ++s) {
-      R g = R(0);
-      if (s <= 4) g += QLb[v] * gL[v][s];
-      if (s >= 1) g += QRb[v] * gR[v][5 - s];
-      G[((long long)v * 6 + s) * nf + f] = g;
+    for (int v = 0; v < NVP; ++v) {
+      g[v] = R(0);
+      if (v < NV) {
+        if (s <= 4) g[v] += QLb[v] * gL[v][s];
+        if (s >= 1) g[v] += QRb[v] * gR[v][5 - s];
+      }
     }
+#pragma unroll
+    for (int c = 0; c < NVP / W; ++c) Gf[s * (NVP / W) + c] = GVec<R>::make(g + c * W);
+  }
+  (void)nf;
 }
 
 // One thread per face; the faces of x, then y (3-D), then z.
@@ -337,7 +462,10 @@ __device__ __forceinline__ void gather_image(const AdjArgs &a, const DomDev &D, 
   const int nfx = nx + fx, nfy = ny + fy;
   const long long nf = (long long)nfx * nfy * (nz + fz);
   const int nd = DIR == 0 ? nx : (DIR == 1 ? ny : nz);
-  const R *G = reinterpret_cast<const R *>(a.G[DIR]);
+  constexpr int NVP = g_stride<R, L::NV>(), W = GVec<R>::W;
+  using Vec = typename GVec<R>::V;
+  const Vec *G = reinterpret_cast<const Vec *>(a.G[DIR]);
+  (void)nf;
 #pragma unroll
   for (int s = 0; s < 6; ++s) {
     const int fpos = ipos + 3 - s;  // face whose stencil slot s is this position
@@ -345,9 +473,16 @@ __device__ __forceinline__ void gather_image(const AdjArgs &a, const DomDev &D, 
     const int fi = fx ? fpos : i, fj = fy ? fpos : j, fk = fz ? fpos : k;
     const long long f = ((long long)fk * nfy + fj) * nfx + fi;
 #pragma unroll
-    for (int v = 0; v < L::NV; ++v) {
-      const R g = G[((long long)v * 6 + s) * nf + f];
-      Xb[v] += v == MN ? sg * g : g;
+    for (int c = 0; c < NVP / W; ++c) {
+      const Vec gv = G[(f * 6 + s) * (NVP / W) + c];
+#pragma unroll
+      for (int e = 0; e < W; ++e) {
+        const int v = c * W + e;
+        if (v < L::NV) {
+          const R g = GVec<R>::get(gv, e);
+          Xb[v] += v == MN ? sg * g : g;
+        }
+      }
     }
   }
 }

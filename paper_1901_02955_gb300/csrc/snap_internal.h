@@ -81,6 +81,10 @@ struct StageArgs {
   int *max_sweeps;
   GridSync *gsync;           // persistent step kernel only
   double dt_override;        // > 0: time step of this launch, before any domain setting
+  // single-domain launches only: when set, the stage reads its input from buf_s and Y^n from
+  // buf_n and writes its output to buf_o instead of the domain's buffers
+  const void *buf_s, *buf_n;
+  void *buf_o;
   Phys ph;
   CstT<float> cf;
   CstT<double> cd;
@@ -121,7 +125,7 @@ struct AdjArgs {
   void *lam_n;           // accumulator of the adjoint of the step's initial state
   double a, b, dt;       // stage output = a Y^n + b (Y_s + dt L(Y_s))
   int mode;              // 2: lam_n = a lam_out; 1: lam_n += a lam_out; 0: lam_s = lam_n + ...
-  void *G[3];            // per-direction face contributions [nv][6][nfaces_d]
+  void *G[3];            // per-direction face contributions [nfaces_d][6][nv padded to 16 B]
   Phys ph;
   CstT<float> cf;
   CstT<double> cd;

@@ -745,9 +745,9 @@ __device__ __forceinline__ void stage_tiles(const StageArgs &a, const int stage,
     const int y0 = ((lt / D.tx) % D.ty) * TY;
     const int z0 = (lt / (D.tx * D.ty)) * TZ;
     const int ex = min(TX, nx - x0), ey = min(TY, ny - y0), ez = min(TZ, nz - z0);
-    const R *Ys = reinterpret_cast<const R *>(D.buf[stage]);
-    const R *Yn = reinterpret_cast<const R *>(D.buf[0]);
-    R *Yo = reinterpret_cast<R *>(D.buf[stage == 0 ? 1 : (stage == 1 ? 2 : 0)]);
+    const R *Ys = reinterpret_cast<const R *>(a.buf_s ? a.buf_s : D.buf[stage]);
+    const R *Yn = reinterpret_cast<const R *>(a.buf_n ? a.buf_n : D.buf[0]);
+    R *Yo = reinterpret_cast<R *>(a.buf_o ? a.buf_o : D.buf[stage == 0 ? 1 : (stage == 1 ? 2 : 0)]);
     // the stage's time step, formed once per CTA
     if (tid == 0) {
       double dt;
