@@ -8,7 +8,7 @@
 //
 // Per stage, deterministic (no atomics):
 //   adj_satadj_kernel (moist layouts): one thread per cell maps the adjoint of the adjusted
-//     state to that of the state before the adjustment, in FP64;
+//     state to that of the state before the adjustment (temperature inversion in FP64);
 //   adj_face_kernel (one launch for the faces of every direction): one thread per face
 //     recomputes the face states from its six-cell stencil, transposes LMARS and WENO5, and
 //     writes the contribution of the face to each of its six stencil cells into
@@ -611,54 +611,57 @@ __global__ void __launch_bounds__(128) adj_cell_kernel(const AdjArgs a) {
 // (total of a saturated species), T c_vi - |u|^2/2 (an unsaturated one), T c_ij + mu_ij -
 // |u|^2/2 (other condensates). lam (in place): (dY_out/dY_in)^T lam.
 template <class R, class L>
-__device__ __forceinline__ void satadj_adj_cell(const Phys &ph, const R *y, double eref,
-                                                double *lam) {
+__device__ __forceinline__ void satadj_adj_cell(const Phys &ph, const CstT<R> &C, const R *y,
+                                                double eref, R *lam) {
   constexpr int NV = L::NV, IM0 = L::IM0;
-  double T, p;
-  cell_Tp<R, L>(ph, y, eref, T, p);
-  double rho = 0.0, u2 = 0.0, Cv = double(y[0]);
+  // T from the conserved energy in FP64 (the inversion cancels large terms); the derivative
+  // itself in the kernel's type
+  double Td, pd;
+  cell_Tp<R, L>(ph, y, eref, Td, pd);
+  const R T = R(Td), cvd = C.R_d * C.igm1;
+  R rho = R(0), u2 = R(0), Cv = y[0];
 #pragma unroll
-  for (int s = 0; s < IM0; ++s) rho += double(y[s]);
-  const double ir = 1.0 / rho;
+  for (int s = 0; s < IM0; ++s) rho += y[s];
+  const R ir = Ar<R>::rcp(rho);
 #pragma unroll
-  for (int m = 0; m < L::NMOM; ++m) u2 += (double(y[IM0 + m]) * ir) * (double(y[IM0 + m]) * ir);
+  for (int m = 0; m < L::NMOM; ++m) u2 += (y[IM0 + m] * ir) * (y[IM0 + m] * ir);
 #pragma unroll
   for (int i = 0; i < L::NVAP; ++i) {
-    Cv += ph.sig_v[i] * double(y[1 + i]);
+    Cv += C.sig_v[i] * y[1 + i];
 #pragma unroll
-    for (int j = 0; j < L::NCOND; ++j) Cv += ph.sig_c[i][j] * double(y[L::cond(i, j)]);
+    for (int j = 0; j < L::NCOND; ++j) Cv += C.sig_c[i][j] * y[L::cond(i, j)];
   }
-  Cv *= ph.c_vd;
-  double dF[NV], li[NV];
+  Cv *= cvd;
+  R dF[NV], li[NV];
 #pragma unroll
   for (int v = 0; v < NV; ++v) li[v] = lam[v];
-  dF[0] = T * ph.c_vd - 0.5 * u2;
+  dF[0] = T * cvd - R(0.5) * u2;
 #pragma unroll
-  for (int m = 0; m < L::NMOM; ++m) dF[IM0 + m] = double(y[IM0 + m]) * ir;
-  dF[L::IE] = -1.0;
-  double dFdT = Cv, gT = 0.0;
+  for (int m = 0; m < L::NMOM; ++m) dF[IM0 + m] = y[IM0 + m] * ir;
+  dF[L::IE] = R(-1);
+  R dFdT = Cv, gT = R(0);
 #pragma unroll
   for (int i = 0; i < L::NVAP; ++i) {
     const int vi = 1 + i, ci = L::cond(i, 0);
-    const double c_v = ph.sig_v[i] * ph.c_vd, c_c = ph.sig_c[i][0] * ph.c_vd, mu_c = ph.mu[i][0];
+    const R c_v = C.sig_v[i] * cvd, c_c = C.sig_c[i][0] * cvd, mu_c = C.mu[i][0];
 #pragma unroll
     for (int j = 1; j < L::NCOND; ++j)
-      dF[L::cond(i, j)] = T * ph.sig_c[i][j] * ph.c_vd + ph.mu[i][j] - 0.5 * u2;
+      dF[L::cond(i, j)] = T * C.sig_c[i][j] * cvd + C.mu[i][j] - R(0.5) * u2;
     if (y[ci] > R(0)) {
-      const double t = T / ph.Tref[i];
-      const double ps = ph.pref[i] * exp(ph.beta[i] * (1.0 - 1.0 / t) - ph.delta[i] * log(t));
-      const double rs = ps / (ph.R_v[i] * T);
-      const double drs = rs * ((ph.beta[i] / t - ph.delta[i]) - 1.0) / T;
+      const R t = T * C.inv_Tref[i], it = Ar<R>::rcp(t), iT = Ar<R>::rcp(T);
+      const R ps = C.pref[i] * Ar<R>::exp_(C.beta[i] * (R(1) - it) - C.delta[i] * Ar<R>::log_(t));
+      const R rs = ps * C.eps[i] * C.iR_d * iT;  // p* / (R_i T), R_i = R_d / eps_i
+      const R drs = rs * ((C.beta[i] * it - C.delta[i]) - R(1)) * iT;
       dFdT += drs * (T * (c_v - c_c) - mu_c);
       gT += drs * (lam[vi] - lam[ci]);
-      dF[vi] = dF[ci] = T * c_c + mu_c - 0.5 * u2;
+      dF[vi] = dF[ci] = T * c_c + mu_c - R(0.5) * u2;
       li[vi] = li[ci] = lam[ci];
     } else {
-      dF[vi] = dF[ci] = T * c_v - 0.5 * u2;
+      dF[vi] = dF[ci] = T * c_v - R(0.5) * u2;
       li[vi] = li[ci] = lam[vi];
     }
   }
-  const double coef = -gT / dFdT;
+  const R coef = -gT * Ar<R>::rcp(dFdT);
 #pragma unroll
   for (int v = 0; v < NV; ++v) lam[v] = li[v] + coef * dF[v];
 }
@@ -672,16 +675,15 @@ __global__ void __launch_bounds__(128) adj_satadj_kernel(const AdjArgs a) {
   R *lam = reinterpret_cast<R *>(a.lam_s);
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell;
        c += (long long)gridDim.x * blockDim.x) {
-    R y[L::NV];
-    double l[L::NV];
+    R y[L::NV], l[L::NV];
 #pragma unroll
     for (int v = 0; v < L::NV; ++v) {
       y[v] = Yo[v * ncell + c];
-      l[v] = double(lam[v * ncell + c]);
+      l[v] = lam[v * ncell + c];
     }
-    satadj_adj_cell<R, L>(a.ph, y, D.e_ref[c / plane], l);
+    satadj_adj_cell<R, L>(a.ph, acst<R>(a), y, D.e_ref[c / plane], l);
 #pragma unroll
-    for (int v = 0; v < L::NV; ++v) lam[v * ncell + c] = R(l[v]);
+    for (int v = 0; v < L::NV; ++v) lam[v * ncell + c] = l[v];
   }
 }
 
