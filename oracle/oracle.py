@@ -53,6 +53,9 @@ class _Grid(C.Structure):
         ("satadj", C.c_int), ("satadj_max_iter", C.c_int), ("satadj_tol", C.c_double),
         ("weno_eps", C.c_double),
         ("gravity_energy_pointwise", C.c_int),
+        ("w_term", C.c_double * MAXC),
+        ("kessler", C.c_int), ("kessler_k", C.c_double * 4),
+        ("kessler_max_iter", C.c_int), ("kessler_tol", C.c_double),
     ]
 
 
@@ -92,6 +95,7 @@ def _load():
     lib.orc_rhs_adjoint.argtypes = [G, _D, _D, _D]
     lib.orc_step_adjoint.argtypes = [G, _D, C.c_double, _D, _D]
     lib.orc_satadj_adjoint_cell.argtypes = [G, _D, _D, _D]
+    lib.orc_kessler_cell.argtypes = [G, _D, C.c_double]
     return lib
 
 
@@ -129,6 +133,14 @@ def grid_from_workload(w, satadj: Optional[bool] = None, nu: Optional[float] = N
     g.satadj_max_iter, g.satadj_tol = w.satadj_max_iter, w.satadj_tol
     g.weno_eps = w.weno_eps
     g.gravity_energy_pointwise = int(energy_pointwise)
+    for j, wt in enumerate(getattr(w, "w_term", ())):
+        g.w_term[j] = wt
+    kk = tuple(getattr(w, "kessler_k", ()))
+    g.kessler = int(len(kk) == 4)
+    for r, kv in enumerate(kk):
+        g.kessler_k[r] = kv
+    g.kessler_max_iter = getattr(w, "kessler_max_iter", 30)
+    g.kessler_tol = getattr(w, "kessler_tol", 1e-12)
     return g, keep
 
 
@@ -221,6 +233,12 @@ class Oracle:
         if rc:
             raise RuntimeError(f"orc_rhs_adjoint failed: {rc}")
         return out
+
+    def kessler_cell(self, Yc, dt):
+        """Sec. 3 Kessler scheme on one cell (backward Euler over dt): (Y, iterations)."""
+        Yc = np.array(Yc, dtype=np.float64)
+        it = self.lib.orc_kessler_cell(C.byref(self.grid), _ptr(Yc), dt)
+        return Yc, it
 
     def satadj_adjoint_cell(self, Yout, lam_out):
         """(dYout/dYin)^T lam_out of the saturation adjustment of one cell at its result."""

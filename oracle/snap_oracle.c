@@ -294,6 +294,155 @@ int orc_satadj_cell(const orc_grid *g, double *Y, int max_iter, double tol) {
   return -1;
 }
 
+/* ---------------------------------------------------------------------------------------
+ * Sec. 3: the Kessler scheme, integrated by backward Euler (Eq. x_n+1). For vapour i with
+ * cloud c = (i,1) and precipitation r = (i,2), in mass mixing ratios of the total density
+ * (fixed by the reactions, like rho_d and rho e):
+ *   Phi_v = -k1 (q_v - q*)^+ + k4 q_r (q* - q_v)^+
+ *   Phi_c =  k1 (q_v - q*)^+ - k3 q_c q_r - k2 q_c
+ *   Phi_r = -k4 q_r (q* - q_v)^+ + k3 q_c q_r + k2 q_c
+ * with q* = p*_i(T) / (R_i T rho) the saturation mixing ratio over the cloud.
+ * READINGS: Newton iterations X^m = X^{m-1} + (I/dt - J)^-1 [Phi(X^{m-1}) - (X^{m-1} -
+ * X^n)/dt], with T (hence q*) recomputed from the conserved energy at every iteration, on
+ * one form of the rates at a time (see orc_kessler_cell). The
+ * printed Jacobians hold q* fixed and leave out the derivatives of the evaporation term with
+ * respect to q_r. Here J is the full Jacobian: those derivatives, and q* varying through T,
+ * which the reactions change at fixed rho e and rho (dT/dq_k = -rho (mu_k + c_k T) / C_v with
+ * mu_k, c_k of vapour, cloud or rain, and d(q*)/dT = q* ((beta/t - delta) - 1)/T from App. D).
+ * With q* held, fast condensation (k1 dt >> 1) makes the iteration diverge: the latent heat
+ * of the condensed vapour raises q* by a few times the condensed amount (about 4x for water
+ * near 300 K). The fixed point, the backward Euler solution, is the same. Vapours are treated
+ * one after the other; the iteration stops when |dX| <= tol (q_v + q_c + q_r).
+ * ------------------------------------------------------------------------------------- */
+/* Kessler rates Phi of vapour i at mixing ratios x (density rho fixed), the backward Euler
+ * residual G = Phi - (x - xn)/dt, and (with J != NULL) its Jacobian dG/dx = J - I/dt with J
+ * the full Jacobian of Phi (see the readings above). Y holds the cell and is updated to x. */
+static void kessler_residual(const orc_grid *g, double *Y, int i, double rho, const double x[3],
+                             const double xn[3], double dt, int saturated, double G[3],
+                             double J[3][3], double *sup_out) {
+  const int vi = 1 + i, ci = icond(g, i, 0), ri = icond(g, i, 1);
+  const double k1 = g->kessler_k[0], k2 = g->kessler_k[1], k3 = g->kessler_k[2],
+               k4 = g->kessler_k[3];
+  double X[64], T;
+  Y[vi] = rho * x[0];
+  Y[ci] = rho * x[1];
+  Y[ri] = rho * x[2];
+  orc_cons_to_prim(g, Y, X, &T, NULL);
+  const double qs = orc_sat_pressure(g, i, T) / (R_vap(g, i) * T * rho);
+  const double sup = x[0] - qs;
+  if (sup_out) *sup_out = sup;
+  double phi[3];
+  if (saturated) {
+    phi[0] = -k1 * sup;
+    phi[1] = k1 * sup - k3 * x[1] * x[2] - k2 * x[1];
+    phi[2] = k3 * x[1] * x[2] + k2 * x[1];
+  } else {
+    phi[0] = -k4 * x[2] * sup;
+    phi[1] = -k3 * x[1] * x[2] - k2 * x[1];
+    phi[2] = k4 * x[2] * sup + k3 * x[1] * x[2] + k2 * x[1];
+  }
+  for (int r = 0; r < 3; ++r) G[r] = phi[r] - (x[r] - xn[r]) / dt;
+  if (!J) return;
+  /* d(q*)/dX_k through T at fixed energy */
+  double Cv = c_vd(g) * Y[0];
+  for (int a = 0; a < g->nvap; ++a) {
+    Cv += g->sig_v[a] * c_vd(g) * Y[1 + a];
+    for (int b = 0; b < g->ncond; ++b) Cv += g->sig_c[a][b] * c_vd(g) * Y[icond(g, a, b)];
+  }
+  const double Ri = R_vap(g, i), dc = dc_of(g, i, 0);
+  const double beta = (g->Lref[i][0] + dc * g->Tref[i]) / (Ri * g->Tref[i]);
+  const double delta = dc / Ri, tt = T / g->Tref[i];
+  const double dqs = qs * ((beta / tt - delta) - 1.0) / T;
+  const double dTdq[3] = {-rho * (g->sig_v[i] * c_vd(g) * T) / Cv,
+                          -rho * (mu_of(g, i, 0) + g->sig_c[i][0] * c_vd(g) * T) / Cv,
+                          -rho * (mu_of(g, i, 1) + g->sig_c[i][1] * c_vd(g) * T) / Cv};
+  for (int r = 0; r < 3; ++r)
+    for (int q = 0; q < 3; ++q) J[r][q] = 0.0;
+  /* d sup / dx_q = delta_q0 - dqs dTdq[q] */
+  double dsup[3];
+  for (int q = 0; q < 3; ++q) dsup[q] = (q == 0 ? 1.0 : 0.0) - dqs * dTdq[q];
+  if (saturated) {
+    for (int q = 0; q < 3; ++q) {
+      J[0][q] += -k1 * dsup[q];
+      J[1][q] += k1 * dsup[q];
+    }
+  } else {
+    for (int q = 0; q < 3; ++q) {
+      J[0][q] += -k4 * x[2] * dsup[q];
+      J[2][q] += k4 * x[2] * dsup[q];
+    }
+    J[0][2] += -k4 * sup;
+    J[2][2] += k4 * sup;
+  }
+  J[1][1] += -k2 - k3 * x[2];
+  J[1][2] += -k3 * x[1];
+  J[2][1] += k2 + k3 * x[2];
+  J[2][2] += k3 * x[1];
+  for (int r = 0; r < 3; ++r) J[r][r] -= 1.0 / dt;
+}
+
+/* Newton iterations on one form of the rates (saturated or not), each smooth in X; the
+ * unknowns are (q_v, q_c) with q_r = tot - q_v - q_c. Returns the iteration count (x
+ * converged), or -1; *sup receives q_v - q* at the result. */
+static int kessler_branch(const orc_grid *g, double *Y, int i, double rho, const double xn[3],
+                          double dt, int saturated, double x[3], double *sup) {
+  const double tot = xn[0] + xn[1] + xn[2];
+  x[0] = xn[0];
+  x[1] = xn[1];
+  x[2] = xn[2];
+  for (int m = 1; m <= g->kessler_max_iter; ++m) {
+    double G[3], J[3][3], dx[3];
+    kessler_residual(g, Y, i, rho, x, xn, dt, saturated, G, J, sup);
+    /* Newton step on the first two equations: (dG_r/dq_q - dG_r/dq_r) d = -G_r, r, q < 2 */
+    const double a00 = J[0][0] - J[0][2], a01 = J[0][1] - J[0][2];
+    const double a10 = J[1][0] - J[1][2], a11 = J[1][1] - J[1][2];
+    const double det = a00 * a11 - a01 * a10;
+    dx[0] = (-G[0] * a11 + G[1] * a01) / det;
+    dx[1] = (-G[1] * a00 + G[0] * a10) / det;
+    x[0] += dx[0];
+    x[1] += dx[1];
+    x[2] = tot - x[0] - x[1];
+    if (fabs(dx[0]) + fabs(dx[1]) <= g->kessler_tol * (fabs(x[0]) + fabs(x[1]) + fabs(x[2]))) {
+      kessler_residual(g, Y, i, rho, x, xn, dt, saturated, G, NULL, sup);
+      return m;
+    }
+  }
+  return -1;
+}
+
+int orc_kessler_cell(const orc_grid *g, double *Y, double dt) {
+  const int im0 = im0_of(g);
+  if (!g->kessler || g->nvap == 0 || g->ncond < 2) return 0;
+  double rho = 0.0;
+  for (int s = 0; s < im0; ++s) rho += Y[s];
+  int worst = 0;
+  for (int i = 0; i < g->nvap; ++i) {
+    const int vi = 1 + i, ci = icond(g, i, 0), ri = icond(g, i, 1);
+    const double xn[3] = {Y[vi] / rho, Y[ci] / rho, Y[ri] / rho};
+    /* the rates change form where the vapour crosses saturation: solve with the form of the
+     * initial state, and with the other form if the result lies on the wrong side (the rates
+     * are continuous there, so the backward Euler solution lies on one side or on the edge) */
+    double x[3], sup, sup_n;
+    kessler_residual(g, Y, i, rho, xn, xn, dt, 1, x, NULL, &sup_n);
+    int first = sup_n > 0.0, it = -1, accepted = 0;
+    for (int attempt = 0; attempt < 2 && !accepted; ++attempt) {
+      const int sat = attempt == 0 ? first : !first;
+      it = kessler_branch(g, Y, i, rho, xn, dt, sat, x, &sup);
+      if (it > 0 && (sat ? sup > 0.0 : sup <= 0.0)) accepted = 1;
+    }
+    if (!accepted) {
+      /* the solution sits on the edge: vapour at saturation, the saturated form's result */
+      it = kessler_branch(g, Y, i, rho, xn, dt, 1, x, &sup);
+    }
+    Y[vi] = rho * x[0];
+    Y[ci] = rho * x[1];
+    Y[ri] = rho * x[2];
+    if (it < 0) worst = -1;
+    else if (worst >= 0 && it > worst) worst = it;
+  }
+  return worst;
+}
+
 /* Exact equilibrium of the same cell (test pin): the internal energy U = rho e - K is fixed;
  * at trial temperature T each vapour holds min(total_i, p*_i(T)/(R_i T)) and its cloud the
  * rest; F(T) = C_v(T) T + A(T) - U is strictly increasing, so bisection finds the root. */
@@ -390,6 +539,37 @@ static int wrap_or_mirror(int idx, int n, int bc_lo, int bc_hi, int *flip) {
 
 static double pbar_cell(const orc_grid *g, int k) {
   return 0.5 * (g->p_bar_face[k] + g->p_bar_face[k + 1]);
+}
+
+/* Sec. 2, Eq. d3 and the momentum and energy equations with sedimentation: a condensate
+ * (i,j) with terminal velocity w^t_j carries through a z face the extra fluxes
+ *   mass w^t rho_ij, momentum w^t rho_ij u_m, energy w^t rho_ij e_ij,
+ *   e_ij = c_ij T + |u|^2/2 + mu_ij (Sec. 2).
+ * READINGS: the face values come from the reconstructed state on the side the condensate
+ * comes from (above when w^t < 0); no condensate passes a wall (reflecting boundary), so
+ * precipitation collects in the lowest layer; the frictional heating -sum rho_ij g w^t of the
+ * energy equation is the sedimentation part of -g F_rho in the gravity source of orc_rhs,
+ * whose total-mass flux includes these mass fluxes. */
+static void sedimentation_flux(const orc_grid *g, const double *XL, const double *XR,
+                               double pref, int k, double *F) {
+  const int im0 = im0_of(g), nm = nmom_of(g), nv = orc_nvar(g);
+  if ((k == 0 && g->bc[4] == ORC_REFLECT) || (k == g->nz && g->bc[5] == ORC_REFLECT)) return;
+  for (int j = 0; j < g->ncond; ++j) {
+    const double wt = g->w_term[j];
+    if (wt == 0.0) continue;
+    const double *XS = wt < 0.0 ? XR : XL;
+    double num, den, u2 = 0.0;
+    mix_factors(g, XS, &num, &den);
+    const double T = (pref + XS[nv - 1]) / (XS[0] * g->Rd * den);
+    for (int m = 0; m < nm; ++m) u2 += XS[im0 + m] * XS[im0 + m];
+    for (int i = 0; i < g->nvap; ++i) {
+      const int c = icond(g, i, j);
+      const double ms = wt * XS[0] * XS[c];
+      F[c] += ms;
+      for (int m = 0; m < nm; ++m) F[im0 + m] += ms * XS[im0 + m];
+      F[nv - 1] += ms * (g->sig_c[i][j] * c_vd(g) * T + 0.5 * u2 + mu_of(g, i, j));
+    }
+  }
 }
 
 int orc_rhs(const orc_grid *g, const double *Y, double *dYdt) {
@@ -504,6 +684,7 @@ int orc_rhs(const orc_grid *g, const double *Y, double *dYdt) {
             double heat = 0.5 * (Px[cl] + Px[cr]) * (Tx[cr] - Tx[cl]) / h;
             Ff[nv - 1] -= rf * g->nu * work + rf * cpd * g->nu * heat;
           }
+          if (fz) sedimentation_flux(g, XL, XR, pref, k, Ff);
           long fidx = ((long)k * nfy + j) * nfx + i;
           long nf = (long)nfx * nfy * nfz;
           for (int v = 0; v < nv; ++v) F[v * nf + fidx] = Ff[v];
@@ -636,6 +817,15 @@ int orc_step(const orc_grid *g, double *Y, int nsteps, double dt, double cfl, do
     }
     if (r0 < 0 || r1 < 0 || r2 < 0) worst = -1;
     memcpy(Y, Y1, sizeof(double) * (size_t)n);
+    if (g->kessler && g->nvap > 0 && g->ncond >= 2) {
+      double Yc[64];
+      const long ncell = (long)g->nx * g->ny * g->nz;
+      for (long c = 0; c < ncell; ++c) {
+        for (int v = 0; v < nv; ++v) Yc[v] = Y[v * ncell + c];
+        if (orc_kessler_cell(g, Yc, h) < 0) worst = -1;
+        for (int v = 0; v < nv; ++v) Y[v * ncell + c] = Yc[v];
+      }
+    }
   }
   free(Y1);
   free(Y2);
@@ -871,6 +1061,8 @@ int orc_rhs_adjoint(const orc_grid *g, const double *Y, const double *mu, double
   const int nx = g->nx, ny = g->ny, nz = g->nz, nv = orc_nvar(g), im0 = im0_of(g);
   const int three_d = ny > 1;
   if (g->nu > 0.0) return -3; /* inviscid only */
+  for (int j = 0; j < g->ncond; ++j)
+    if (g->w_term[j] != 0.0) return -3; /* no sedimentation */
   if (nx < 1 || ny < 1 || nz < 3) return -1;
   ext_dims e = {nx + 6, three_d ? ny + 6 : 1, nz + 6, 3, three_d ? 3 : 0, 3};
   const long next = (long)e.nxe * e.nye * e.nze;
@@ -1136,6 +1328,10 @@ int orc_step_adjoint(const orc_grid *g, const double *Yn, double dt, const doubl
   double *Y3 = malloc(sizeof(double) * (size_t)n), *l3 = malloc(sizeof(double) * (size_t)n);
   const int sa = g->satadj && g->nvap > 0 && g->ncond > 0;
   int rc = -2;
+  if (g->kessler) {
+    rc = -3; /* the microphysics is not differentiated */
+    goto done;
+  }
   if (!Y1 || !Y2 || !mu || !Yb || !l2 || !l1 || !Y3 || !l3) goto done;
   if ((rc = orc_stage(g, 0, Yn, Yn, dt, Y1)) < 0) goto done;
   if ((rc = orc_stage(g, 1, Yn, Y1, dt, Y2)) < 0) goto done;

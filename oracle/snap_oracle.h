@@ -50,6 +50,15 @@ typedef struct {
   double satadj_tol;
   double weno_eps;
   int gravity_energy_pointwise; /* 0: -g (F_rho,k-1/2 + F_rho,k+1/2)/2 ; 1: -g (rho w)_k */
+  /* Sec. 2, Eq. d3: terminal velocity of condensate phase j of every vapour (m/s, < 0 falls);
+   * nonzero values add the sedimentation fluxes of mass, momentum and energy in z */
+  double w_term[ORC_MAXC];
+  /* Sec. 3: Kessler microphysics after every step, backward Euler with Newton iterations:
+   * k1 condensation, k2 autoconversion, k3 accretion, k4 evaporation of precipitation */
+  int kessler;
+  double kessler_k[4];
+  int kessler_max_iter;
+  double kessler_tol;
 } orc_grid;
 
 int orc_nvar(const orc_grid *g);
@@ -79,6 +88,12 @@ int orc_satadj_cell(const orc_grid *g, double *Ycell, int max_iter, double tol);
 /* Exact equilibrium by bisection on temperature (test pin for orc_satadj_cell). */
 int orc_satadj_bisect(const orc_grid *g, double *Ycell);
 
+/* Sec. 3 Kessler scheme on one cell, in place: each vapour i with its cloud (i,1) and
+ * precipitation (i,2) advances its mass mixing ratios by one backward Euler step of length
+ * dt (Newton iterations of Eq. x_n+1). Returns the largest iteration count, or -1 when an
+ * iteration did not converge. */
+int orc_kessler_cell(const orc_grid *g, double *Ycell, double dt);
+
 /* ---- whole-grid pieces ---- */
 /* dYdt = L(Y): minus the flux divergence plus the gravity source (and viscous fluxes). */
 int orc_rhs(const orc_grid *g, const double *Y, double *dYdt);
@@ -89,7 +104,8 @@ void orc_rk3_combine(int stage, long n, const double *Yn, const double *Ys, cons
  * Returns the largest sweep count, or -1 if a cell did not converge. */
 int orc_stage(const orc_grid *g, int stage, const double *Yn, const double *Ys, double dt,
               double *Yout);
-/* nsteps full steps in place; dt <= 0 means recompute dt = cfl * min dx/(|u|+c) per step. */
+/* nsteps full steps in place; dt <= 0 means recompute dt = cfl * min dx/(|u|+c) per step.
+ * With g->kessler set, the Kessler scheme follows each step (time splitting). */
 int orc_step(const orc_grid *g, double *Y, int nsteps, double dt, double cfl, double *dt_last);
 double orc_dt_cfl(const orc_grid *g, const double *Y, double cfl);
 /* out[f] = sum of field f times the cell volume (nvar values), out[nvar] = sum of
@@ -98,14 +114,15 @@ void orc_budget(const orc_grid *g, const double *Y, double *out);
 
 /* ---- discrete adjoint (inviscid): transposes of the routines above ---- */
 double orc_weno5_gradient(const double q[5], double eps, double grad[5]);
-/* Ybar = (dL/dY)^T mu at state Y (returns -3 for viscous grids). */
+/* Ybar = (dL/dY)^T mu at state Y (returns -3 for viscous grids or with sedimentation). */
 int orc_rhs_adjoint(const orc_grid *g, const double *Y, const double *mu, double *Ybar);
 /* lam_in = (dYout/dYin)^T lam_out for the saturation adjustment of one cell, evaluated at its
  * converged result Yout (App. D equilibrium; see the definition for the derivation). */
 int orc_satadj_adjoint_cell(const orc_grid *g, const double *Yout, const double *lam_out,
                             double *lam_in);
 /* lam_in = (dY^{n+1}/dY^n)^T lam_out for one step of time step dt from Yn (with the
- * saturation adjustment after every stage when g->satadj is set). */
+ * saturation adjustment after every stage when g->satadj is set; -3 with the Kessler
+ * scheme, which is not differentiated). */
 int orc_step_adjoint(const orc_grid *g, const double *Yn, double dt, const double *lam_out,
                      double *lam_in);
 

@@ -13,7 +13,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "snap_oracle.c")
 PINS = ["tests/test_oracle_weno.py", "tests/test_oracle_lmars.py", "tests/test_oracle_thermo.py",
         "tests/test_oracle_satadj.py", "tests/test_oracle_scheme.py",
-        "tests/test_oracle_adjoint.py"]
+        "tests/test_oracle_adjoint.py", "tests/test_oracle_kessler.py"]
 
 MUTANTS = {
     "weno beta0 curvature coefficient": ("b[0] = 13.0 / 12.0 * t * t;", "b[0] = 13.0 / 6.0 * t * t;"),
@@ -52,6 +52,13 @@ MUTANTS = {
                                                    "Yb[icond(g, i, j)] += Ub * mu_of(g, i, j);"),
     "tracer flux adjoint without dry-air term": ("XSb[t] += wgt * (Fbar[t] - Fbar[0]) * mf;",
                                                  "XSb[t] += wgt * Fbar[t] * mf;"),
+    "kessler autoconversion sign": ("phi[1] = k1 * sup - k3 * x[1] * x[2] - k2 * x[1];",
+                                    "phi[1] = k1 * sup - k3 * x[1] * x[2] + k2 * x[1];"),
+    "kessler evaporation without rain factor": ("    phi[0] = -k4 * x[2] * sup;", "    phi[0] = -k4 * sup;"),
+    "sedimentation from the wrong side": ("const double *XS = wt < 0.0 ? XR : XL;",
+                                          "const double *XS = wt < 0.0 ? XL : XR;"),
+    "sedimentation energy without kinetic part": ("F[nv - 1] += ms * (g->sig_c[i][j] * c_vd(g) * T + 0.5 * u2 + mu_of(g, i, j));",
+                                                  "F[nv - 1] += ms * (g->sig_c[i][j] * c_vd(g) * T + mu_of(g, i, j));"),
 }
 
 

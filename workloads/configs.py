@@ -82,6 +82,13 @@ class Workload:
     weno_eps: float = 1e-6
     dtype: str = "f64"
     seed: int = BASE_SEED
+    # terminal velocity of condensate phase j of every vapour (m/s, negative falls); the
+    # Kessler rates (k1 condensation, k2 autoconversion, k3 accretion, k4 evaporation, 1/s);
+    # an empty kessler_k switches the microphysics off
+    w_term: tuple = ()
+    kessler_k: tuple = ()
+    kessler_max_iter: int = 30
+    kessler_tol: float = 1e-12
 
     @property
     def nvapor(self) -> int:
