@@ -79,6 +79,19 @@ typedef struct snap_grid_desc {
   double satadj_tol;       /* relative stop tolerance on the molar transfer; raised to
                               32 machine epsilons of dtype when smaller */
   double weno_eps;         /* epsilon of the WENO5 weights (e.g. 1e-6) */
+  /* Sec. 2, Eq. d3: terminal velocity of condensate j of every vapour, m/s (< 0 falls); a
+   * nonzero value adds the sedimentation fluxes of mass, momentum and energy at z faces,
+   * taken from the side the condensate comes from; nothing crosses the walls. Needs
+   * n_cond > 0. */
+  double w_term[SNAP_MAX_COND];
+  /* Sec. 3: 1 applies the Kessler scheme after every step by backward Euler (needs n_cond ==
+   * 2: condensate 0 cloud, 1 precipitation): kessler_k = k1 condensation, k2 autoconversion,
+   * k3 accretion, k4 evaporation, 1/s; iterations stop at kessler_tol (raised to 32 machine
+   * epsilons of dtype) or report SNAP_ENOCONV after kessler_max_iter. */
+  int kessler;
+  double kessler_k[4];
+  int kessler_max_iter;
+  double kessler_tol;
 } snap_grid_desc;
 
 /* Domain totals: field sums times the cell volume, and sum of (rho e + rho g z) dV. */

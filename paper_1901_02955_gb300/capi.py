@@ -47,7 +47,10 @@ class GridDesc(C.Structure):
                 ("rho_bar", C.POINTER(C.c_double)), ("p_bar_face", C.POINTER(C.c_double)),
                 ("dtype", C.c_int), ("cfl", C.c_double), ("nu", C.c_double),
                 ("satadj", C.c_int), ("satadj_max_iter", C.c_int), ("satadj_tol", C.c_double),
-                ("weno_eps", C.c_double)]
+                ("weno_eps", C.c_double),
+                ("w_term", C.c_double * MAX_COND),
+                ("kessler", C.c_int), ("kessler_k", C.c_double * 4),
+                ("kessler_max_iter", C.c_int), ("kessler_tol", C.c_double)]
 
 
 class Budget(C.Structure):
@@ -141,6 +144,14 @@ def desc_from_workload(w, dtype: Optional[str] = None, satadj: Optional[bool] = 
     d.satadj = int((len(w.vapors) > 0 and w.ncond > 0) if satadj is None else satadj)
     d.satadj_max_iter, d.satadj_tol = w.satadj_max_iter, w.satadj_tol
     d.weno_eps = w.weno_eps
+    for j, wt in enumerate(getattr(w, "w_term", ())):
+        d.w_term[j] = wt
+    kk = tuple(getattr(w, "kessler_k", ()))
+    d.kessler = int(len(kk) == 4)
+    for r, kv in enumerate(kk):
+        d.kessler_k[r] = kv
+    d.kessler_max_iter = getattr(w, "kessler_max_iter", 30)
+    d.kessler_tol = getattr(w, "kessler_tol", 1e-12)
     return d, keep
 
 

@@ -16,8 +16,8 @@
 namespace snap {
 bool find_kernels_dry2d(int f32, int visc, KernelSet *out);
 bool find_kernels_dry3d(int f32, int visc, KernelSet *out);
-bool find_kernels_moist2d(int f32, int visc, KernelSet *out);
-bool find_kernels_moist3d(int f32, int visc, KernelSet *out);
+bool find_kernels_moist2d(int f32, int visc, int micro, KernelSet *out);
+bool find_kernels_moist3d(int f32, int visc, int micro, KernelSet *out);
 
 bool find_adjoint_kernels_dry2d(int f32, AdjKernels *out);
 bool find_adjoint_kernels_dry3d(int f32, AdjKernels *out);
@@ -29,11 +29,11 @@ bool find_adjoint_kernels(int f32, int nvap, int ncond, int three_d, AdjKernels 
   return false;
 }
 
-bool find_kernels(int f32, int nvap, int ncond, int three_d, int visc, KernelSet *out) {
-  if (nvap == 0 && ncond == 0) return three_d ? find_kernels_dry3d(f32, visc, out)
-                                              : find_kernels_dry2d(f32, visc, out);
-  if (nvap == 1 && ncond == 2 && !three_d) return find_kernels_moist2d(f32, visc, out);
-  if (nvap == 2 && ncond == 2 && three_d) return find_kernels_moist3d(f32, visc, out);
+bool find_kernels(int f32, int nvap, int ncond, int three_d, int visc, int micro, KernelSet *out) {
+  if (nvap == 0 && ncond == 0) return !micro && (three_d ? find_kernels_dry3d(f32, visc, out)
+                                                         : find_kernels_dry2d(f32, visc, out));
+  if (nvap == 1 && ncond == 2 && !three_d) return find_kernels_moist2d(f32, visc, micro, out);
+  if (nvap == 2 && ncond == 2 && three_d) return find_kernels_moist3d(f32, visc, micro, out);
   return false;
 }
 
@@ -198,6 +198,15 @@ static int validate(const snap_grid_desc &d, const snap_grid_desc &d0, int idx, 
   if (d.satadj && (d.n_vapor == 0 || d.n_cond == 0)) return bad("satadj needs vapours with condensates");
   if (d.satadj && d.satadj_max_iter < 1) return bad("satadj_max_iter must be >= 1");
   if (!(d.nu >= 0.0)) return bad("nu must be >= 0");
+  for (int j = 0; j < SNAP_MAX_COND; ++j)
+    if (!isfinite(d.w_term[j]) || (d.w_term[j] != 0.0 && j >= d.n_cond))
+      return bad("w_term must be finite and zero beyond n_cond");
+  if (d.kessler) {
+    if (d.n_vapor < 1 || d.n_cond != 2) return bad("the Kessler scheme needs vapours with cloud and precipitation (n_cond == 2)");
+    if (d.kessler_max_iter < 1) return bad("kessler_max_iter must be >= 1");
+    for (int r = 0; r < 4; ++r)
+      if (!(d.kessler_k[r] >= 0.0)) return bad("Kessler rates must be >= 0");
+  }
   if (!d.rho_bar || !d.p_bar_face) return bad("reference profile pointers are NULL");
   for (int k = 0; k < d.nz; ++k) {
     if (!(d.rho_bar[k] > 0) || !(d.p_bar_face[k] > 0) || !(d.p_bar_face[k + 1] > 0))
@@ -209,7 +218,9 @@ static int validate(const snap_grid_desc &d, const snap_grid_desc &d0, int idx, 
   if (d.dtype != d0.dtype || d.n_vapor != d0.n_vapor || d.n_cond != d0.n_cond ||
       (d.ny > 1) != (d0.ny > 1) || d.gamma_d != d0.gamma_d || d.R_d != d0.R_d ||
       (d.nu > 0) != (d0.nu > 0) || d.nu != d0.nu || d.satadj != d0.satadj ||
-      d.weno_eps != d0.weno_eps)
+      d.weno_eps != d0.weno_eps || d.kessler != d0.kessler ||
+      memcmp(d.kessler_k, d0.kessler_k, sizeof d.kessler_k) != 0 ||
+      memcmp(d.w_term, d0.w_term, sizeof d.w_term) != 0)
     return bad("domains of one context must share dtype, species, gases, dimensionality, "
                "viscosity and scheme options");
   for (int i = 0; i < d.n_vapor; ++i) {
@@ -256,6 +267,15 @@ static void derive_phys(const snap_grid_desc &d, Phys &ph) {
   ph.satadj = d.satadj;
   ph.satadj_max_iter = d.satadj_max_iter;
   ph.satadj_tol = d.satadj_tol;
+  ph.sediment = 0;
+  for (int j = 0; j < kMaxCond; ++j) {
+    ph.w_term[j] = j < d.n_cond ? d.w_term[j] : 0.0;
+    if (ph.w_term[j] != 0.0) ph.sediment = 1;
+  }
+  ph.kessler = d.kessler;
+  ph.kessler_max_iter = d.kessler_max_iter;
+  ph.kessler_tol = d.kessler_tol;
+  for (int r = 0; r < 4; ++r) ph.kessler_k[r] = d.kessler_k[r];
 }
 
 template <class T>
@@ -288,6 +308,10 @@ static void derive_cst(const Phys &ph, double tol_floor, CstT<T> &c) {
       c.mu[i][j] = T(ph.mu[i][j]);
     }
   }
+  for (int j = 0; j < kMaxCond; ++j) c.w_term[j] = T(ph.w_term[j]);
+  for (int r = 0; r < 4; ++r) c.kk[r] = T(ph.kessler_k[r]);
+  c.kessler_tol = T(ph.kessler_tol > tol_floor ? ph.kessler_tol : tol_floor);
+  c.c_vd = T(ph.c_vd);
 }
 
 static StageArgs args_of(snap_ctx *ctx, int stage) {
@@ -336,7 +360,11 @@ extern "C" int snap_init_grid(snap_ctx **out, const snap_grid_desc *d, int n_dom
   ctx->visc = d[0].nu > 0.0;
   ctx->nv = 1 + ctx->nvap + ctx->nvap * ctx->ncond + (ctx->three_d ? 3 : 2) + 1;
   ctx->word = ctx->f32 ? 4 : 8;
-  if (!find_kernels(ctx->f32, ctx->nvap, ctx->ncond, ctx->three_d, ctx->visc, &ctx->ks)) {
+  // the microphysics switch of the descriptor picks kernels with sedimentation and the
+  // Kessler scheme compiled in
+  int micro = d[0].kessler != 0;
+  for (int j = 0; j < SNAP_MAX_COND; ++j) micro |= d[0].w_term[j] != 0.0;
+  if (!find_kernels(ctx->f32, ctx->nvap, ctx->ncond, ctx->three_d, ctx->visc, micro, &ctx->ks)) {
     delete ctx;
     return fail(nullptr, SNAP_ENOTSUP,
                 "snap_init_grid: this library builds dry (any dimension, optional viscosity), "
@@ -345,7 +373,8 @@ extern "C" int snap_init_grid(snap_ctx **out, const snap_grid_desc *d, int n_dom
   }
   derive_phys(d[0], ctx->ph);
   ctx->desc.assign(d, d + n_domains);
-  if (!ctx->visc && n_domains == 1)
+  // the adjoint covers neither the microphysics nor sedimentation
+  if (!ctx->visc && n_domains == 1 && !ctx->ph.kessler && !ctx->ph.sediment)
     ctx->has_adj = find_adjoint_kernels(ctx->f32, ctx->nvap, ctx->ncond, ctx->three_d, &ctx->adj) ? 1 : 0;
   cudaError_t e = cudaSuccess;
   for (int v = 0; v < ctx->ks.nvariants && e == cudaSuccess; ++v) e = ctx->ks.var[v].prepare();

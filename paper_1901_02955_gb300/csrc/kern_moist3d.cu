@@ -3,12 +3,15 @@
 
 namespace snap {
 
-bool find_kernels_moist3d(int f32, int visc, KernelSet *out) {
+bool find_kernels_moist3d(int f32, int visc, int micro, KernelSet *out) {
   using L = Lay<2, 2, true>;
   using A = TileT<8, 8, 4>;
   using B = TileT<16, 8, 2>;
   if (visc) return false;
-  *out = f32 ? Family<float, L>::set<false, A, B>() : Family<double, L>::set<false, A>();
+  if (micro)  // sedimentation and the Kessler scheme compiled in, default tile only
+    *out = f32 ? Family<float, L>::set_micro<A>() : Family<double, L>::set_micro<A>();
+  else
+    *out = f32 ? Family<float, L>::set<false, A, B>() : Family<double, L>::set<false, A>();
   return true;
 }
 

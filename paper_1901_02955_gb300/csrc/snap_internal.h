@@ -25,6 +25,11 @@ struct Phys {
   double nu;
   int satadj, satadj_max_iter;
   double satadj_tol;
+  double w_term[kMaxCond];                 // terminal velocity of condensate j (Eq. d3)
+  int sediment;                            // any w_term != 0
+  int kessler, kessler_max_iter;           // Kessler scheme (Sec. 3) after every step
+  double kessler_k[4];                     // k1 .. k4
+  double kessler_tol;
 };
 
 // The same constants in the arithmetic type of a kernel, derived on the host, so that FP32
@@ -35,6 +40,7 @@ struct CstT {
   T eps[kMaxVap], inv_eps[kMaxVap], ieps_m1[kMaxVap], sig_v[kMaxVap], sigv_m1[kMaxVap];
   T sig_c[kMaxVap][kMaxCond], sigc_m1[kMaxVap][kMaxCond], mu[kMaxVap][kMaxCond];
   T pref[kMaxVap], beta[kMaxVap], delta[kMaxVap], inv_Tref[kMaxVap], sighat_m1[kMaxVap];
+  T w_term[kMaxCond], kk[4], kessler_tol, c_vd;
 };
 
 // One domain as the kernels see it (device memory).
@@ -144,7 +150,7 @@ struct AdjKernels {
 bool find_adjoint_kernels(int f32, int nvap, int ncond, int three_d, AdjKernels *out);
 
 // Returns false when the configuration is not built into this library.
-bool find_kernels(int f32, int nvap, int ncond, int three_d, int visc, KernelSet *out);
+bool find_kernels(int f32, int nvap, int ncond, int three_d, int visc, int micro, KernelSet *out);
 
 // Number of partial rows the budget kernel writes for a domain of ncell cells.
 int budget_blocks(long long ncell);

@@ -514,6 +514,171 @@ __device__ __forceinline__ double block_max(double v, double *red) {
   return v;
 }
 
+// ------------------------------------------------------------------------------------------
+// Sedimentation (Sec. 2, Eq. d3 and the momentum and energy equations with terminal
+// velocities): condensate (i,j) falling at w^t_j carries through a z face the extra fluxes
+// w^t rho_ij (mass), w^t rho_ij u_m (momentum) and w^t rho_ij e_ij with e_ij = c_ij T +
+// |u|^2/2 + mu_ij (energy), from the reconstructed state on the side it comes from (above
+// when w^t < 0). The frictional heating of the energy equation enters through the total
+// mass flux of the gravity-energy source.
+// ------------------------------------------------------------------------------------------
+template <class R, class L>
+__device__ __forceinline__ void sediment_flux(const CstT<R> &C, const R *XL, const R *XR,
+                                              R pref, R *F) {
+#pragma unroll
+  for (int j = 0; j < L::NCOND; ++j) {
+    const R wt = C.w_term[j];
+    if (wt == R(0)) continue;
+    const bool up = wt < R(0);  // falling: the state above the face
+    R XS[L::NV];
+#pragma unroll
+    for (int v = 0; v < L::NV; ++v) XS[v] = up ? XR[v] : XL[v];
+    R num, den, u2 = R(0);
+    mix_factors<R, L>(C, XS, num, den);
+    const R T = (pref + XS[L::IE]) * Ar<R>::rcp(XS[0] * C.R_d * den);
+#pragma unroll
+    for (int m = 0; m < L::NMOM; ++m) u2 += XS[L::IM0 + m] * XS[L::IM0 + m];
+#pragma unroll
+    for (int i = 0; i < L::NVAP; ++i) {
+      const int c = L::cond(i, j);
+      const R ms = wt * XS[0] * XS[c];
+      F[c] += ms;
+#pragma unroll
+      for (int m = 0; m < L::NMOM; ++m) F[L::IM0 + m] += ms * XS[L::IM0 + m];
+      F[L::IE] += ms * (C.sig_c[i][j] * C.c_vd * T + R(0.5) * u2 + C.mu[i][j]);
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// Kessler scheme (Sec. 3) on one cell, backward Euler over dt (Eq. x_n+1), in densities: for
+// vapour i with cloud (i,0) and precipitation (i,1), s = rho_v - rho*(T), rho* = p*/(R_i T),
+//   saturated (s > 0):  F_v = -k1 s, F_c = k1 s - k3 rho_c rho_r / rho - k2 rho_c,
+//                       F_r = k3 rho_c rho_r / rho + k2 rho_c
+//   otherwise:          F_v = -k4 rho_r s / rho, F_c = -k3 rho_c rho_r / rho - k2 rho_c,
+//                       F_r = k4 rho_r s / rho + k3 rho_c rho_r / rho + k2 rho_c
+// (the mass-mixing-ratio rates of Sec. 3 times the fixed total density rho). Newton on
+// G = F(y) - (y - y_n)/dt in (rho_v, rho_c) with rho_r = total - rho_v - rho_c, the full
+// Jacobian (rho* varies with T, which the reactions change at fixed rho e: dT/drho_k =
+// -(mu_k + c_k T)/C_v), one form of the rates at a time: the form of the initial state, then
+// the other if the result lies on the wrong side of saturation, else the saturated form.
+// T is inverted from the energy in FP64. Returns the largest iteration count or -1.
+// ------------------------------------------------------------------------------------------
+template <class R, class L>
+__device__ __forceinline__ void kessler_eval(const Phys &ph, const CstT<R> &C, const R *y,
+                                             double eref, int i, R rho, const R *yn, R dt,
+                                             bool sat, R G[2], R A[2][2], R &s_out) {
+  const int vi = 1 + i, ci = L::cond(i, 0), ri = L::cond(i, 1);
+  double Td, pd;
+  cell_Tp<R, L>(ph, y, eref, Td, pd);
+  const R T = R(Td), iT = Ar<R>::rcp(T), t = T * C.inv_Tref[i], it = Ar<R>::rcp(t);
+  const R rs = C.pref[i] * Ar<R>::exp_(C.beta[i] * (R(1) - it) - C.delta[i] * Ar<R>::log_(t)) *
+               C.eps[i] * C.iR_d * iT;  // p* / (R_i T)
+  const R drs = rs * ((C.beta[i] * it - C.delta[i]) - R(1)) * iT;
+  R Cv = y[0];
+#pragma unroll
+  for (int a = 0; a < L::NVAP; ++a) {
+    Cv += C.sig_v[a] * y[1 + a];
+#pragma unroll
+    for (int b = 0; b < L::NCOND; ++b) Cv += C.sig_c[a][b] * y[L::cond(a, b)];
+  }
+  const R iCv = Ar<R>::rcp(Cv * C.c_vd);
+  // d s / d rho_k for k = vapour, cloud, precipitation (dT/drho_k at fixed energy)
+  const R ds[3] = {R(1) + drs * (C.sig_v[i] * C.c_vd * T) * iCv,
+                   drs * (C.mu[i][0] + C.sig_c[i][0] * C.c_vd * T) * iCv,
+                   drs * (C.mu[i][1] + C.sig_c[i][1] * C.c_vd * T) * iCv};
+  const R k1 = C.kk[0], k2 = C.kk[1], k3 = C.kk[2], k4 = C.kk[3], ir = Ar<R>::rcp(rho);
+  const R yv = y[vi], yc = y[ci], yr = y[ri], s = yv - rs;
+  s_out = s;
+  // Equations: the vapour rate G_v and the vapour-plus-cloud rate G_v + G_c, in which the
+  // stiff condensation term k1 s cancels exactly (with G_v and G_c separately the 2 x 2
+  // determinant would cancel two terms of order k1^2, fatal in FP32 for k1 = 1e9).
+  const R acc = k3 * yc * yr * ir;
+  R Fv, Fvc, Jv[3], Jvc[3];  // rates and their derivatives by (rho_v, rho_c, rho_r)
+  if (sat) {
+    Fv = -k1 * s;
+    Fvc = -acc - k2 * yc;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) Jv[q] = -k1 * ds[q];
+    Jvc[0] = R(0);
+  } else {
+    const R e = k4 * yr * ir;
+    Fv = -e * s;
+    Fvc = -e * s - acc - k2 * yc;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) Jv[q] = -e * ds[q];
+    Jv[2] -= k4 * s * ir;
+    Jvc[0] = Jv[0];
+  }
+  Jvc[1] = (sat ? R(0) : Jv[1]) - k3 * yr * ir - k2;
+  Jvc[2] = (sat ? R(0) : Jv[2]) - k3 * yc * ir;
+  const R idt = Ar<R>::rcp(dt);
+  G[0] = Fv - (yv - yn[0]) * idt;
+  G[1] = Fvc - ((yv - yn[0]) + (yc - yn[1])) * idt;
+  // 2 x 2 Jacobian in (rho_v, rho_c) with rho_r = total - rho_v - rho_c
+  A[0][0] = Jv[0] - Jv[2] - idt;
+  A[0][1] = Jv[1] - Jv[2];
+  A[1][0] = Jvc[0] - Jvc[2] - idt;
+  A[1][1] = Jvc[1] - Jvc[2] - idt;
+}
+
+template <class R, class L>
+__device__ __forceinline__ int kessler_branch(const Phys &ph, const CstT<R> &C, R *y,
+                                              double eref, int i, R rho, const R *yn, R tot,
+                                              R dt, bool sat, R &s) {
+  const int vi = 1 + i, ci = L::cond(i, 0), ri = L::cond(i, 1);
+  y[vi] = yn[0];
+  y[ci] = yn[1];
+  y[ri] = yn[2];
+  for (int m = 1; m <= ph.kessler_max_iter; ++m) {
+    R G[2], A[2][2];
+    kessler_eval<R, L>(ph, C, y, eref, i, rho, yn, dt, sat, G, A, s);
+    const R idet = Ar<R>::rcp(A[0][0] * A[1][1] - A[0][1] * A[1][0]);
+    const R dv = (-G[0] * A[1][1] + G[1] * A[0][1]) * idet;
+    const R dc = (-G[1] * A[0][0] + G[0] * A[1][0]) * idet;
+    y[vi] += dv;
+    y[ci] += dc;
+    y[ri] = tot - y[vi] - y[ci];
+    if (fabs(dv) + fabs(dc) <= C.kessler_tol * (fabs(y[vi]) + fabs(y[ci]) + fabs(y[ri]))) {
+      R Gt[2], At[2][2];
+      kessler_eval<R, L>(ph, C, y, eref, i, rho, yn, dt, sat, Gt, At, s);
+      return m;
+    }
+  }
+  return -1;
+}
+
+template <class R, class L>
+__device__ int kessler_cell(const Phys &ph, const CstT<R> &C, R *y, double eref, R dt) {
+  if constexpr (!(L::NVAP > 0 && L::NCOND >= 2)) {
+    return 0;
+  } else {
+    R rho = R(0);
+#pragma unroll
+    for (int s = 0; s < L::IM0; ++s) rho += y[s];
+    int worst = 0;
+    for (int i = 0; i < L::NVAP; ++i) {
+      const int vi = 1 + i, ci = L::cond(i, 0), ri = L::cond(i, 1);
+      const R yn[3] = {y[vi], y[ci], y[ri]};
+      const R tot = yn[0] + yn[1] + yn[2];
+      R G[2], A[2][2], s0, s;
+      kessler_eval<R, L>(ph, C, y, eref, i, rho, yn, dt, true, G, A, s0);
+      const bool first = s0 > R(0);
+      int it = kessler_branch<R, L>(ph, C, y, eref, i, rho, yn, tot, dt, first, s);
+      if (!(it > 0 && (first ? s > R(0) : s <= R(0)))) {
+        it = kessler_branch<R, L>(ph, C, y, eref, i, rho, yn, tot, dt, !first, s);
+        if (!(it > 0 && (!first ? s > R(0) : s <= R(0))))
+          it = kessler_branch<R, L>(ph, C, y, eref, i, rho, yn, tot, dt, true, s);
+      }
+      if (it < 0)
+        worst = -1;
+      else if (worst >= 0 && it > worst)
+        worst = it;
+    }
+    return worst;
+  }
+}
+
 __device__ __forceinline__ float block_max_f(float v, float *red) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
@@ -715,7 +880,7 @@ __device__ __forceinline__ void grid_barrier(GridSync *gs, unsigned int nblocks,
   __syncthreads();
 }
 
-template <class R, class L, bool VISC, class T>
+template <class R, class L, bool VISC, class T, bool MICRO>
 __device__ __forceinline__ void stage_tiles(const StageArgs &a, const int stage,
                                             unsigned char *smem) {
   using B = Box<T, L::D3>;
@@ -945,6 +1110,12 @@ __device__ __forceinline__ void stage_tiles(const StageArgs &a, const int stage,
           }
           const R pref = fz ? P::pf(D, z0 + iz) : P::pc(D, z0 + iz);
           lmars<R, L>(C, QL, QR, d, pref, F);
+          if constexpr (L::MOIST && MICRO) {
+            // no condensate passes a wall
+            const int kf = z0 + iz;
+            if (fz && ph.sediment && !(kf == 0 && D.bc[4] == 0) && !(kf == nz && D.bc[5] == 0))
+              sediment_flux<R, L>(C, QL, QR, pref, F);
+          }
           if constexpr (VISC) {
             const int bi = B::at(ix + 3, iy + B::HY, iz + 3);  // right cell of the face
             const int bl = bi - stride;
@@ -1031,6 +1202,11 @@ __device__ __forceinline__ void stage_tiles(const StageArgs &a, const int stage,
             else if (it > 2)
               atomicMax(a.max_sweeps, it);
           }
+          // the microphysics follows each step (time splitting), over the step's dt
+          if (MICRO && stage == 2 && ph.kessler) {
+            if (kessler_cell<R, L>(ph, C, yo, D.e_ref[k], dt) < 0)
+              atomicOr(a.flags, (unsigned)kFlagNoConv);
+          }
         }
         R rs = R(0);
 #pragma unroll
@@ -1056,20 +1232,20 @@ __device__ __forceinline__ void stage_tiles(const StageArgs &a, const int stage,
 }
 
 // One Runge-Kutta stage over all tiles of all domains.
-template <class R, class L, bool VISC, class T>
+template <class R, class L, bool VISC, class T, bool MICRO>
 __global__ void __launch_bounds__(T::NT, T::MINB) stage_kernel(const StageArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
-  stage_tiles<R, L, VISC, T>(a, a.stage, smem);
+  stage_tiles<R, L, VISC, T, MICRO>(a, a.stage, smem);
 }
 
 // One whole step (three stages) in a single persistent cooperative launch: the CTAs walk the
 // tile queue of every domain per stage and meet at a grid barrier between stages.
-template <class R, class L, bool VISC, class T>
+template <class R, class L, bool VISC, class T, bool MICRO>
 __global__ void __launch_bounds__(T::NT, T::MINB) step_kernel(const StageArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
 #pragma unroll 1
   for (int st = 0; st < 3; ++st) {
-    stage_tiles<R, L, VISC, T>(a, st, smem);
+    stage_tiles<R, L, VISC, T, MICRO>(a, st, smem);
     if (st < 2) grid_barrier(a.gsync, gridDim.x, a.flags);
   }
 }
@@ -1175,19 +1351,19 @@ __global__ void __launch_bounds__(256) satadj_kernel(const StageArgs a, int dm, 
 // ------------------------------------------------------------------------------------------
 // host launchers of one configuration
 // ------------------------------------------------------------------------------------------
-template <class R, class L, bool VISC, class T>
+template <class R, class L, bool VISC, class T, bool MICRO = false>
 struct Variant {
   using S = StageSmem<R, L, VISC, T>;
   static cudaError_t prepare() {
-    cudaError_t e = cudaFuncSetAttribute(stage_kernel<R, L, VISC, T>,
+    cudaError_t e = cudaFuncSetAttribute(stage_kernel<R, L, VISC, T, MICRO>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          int(S::total));
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(step_kernel<R, L, VISC, T>,
+    return cudaFuncSetAttribute(step_kernel<R, L, VISC, T, MICRO>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, int(S::total));
   }
   static cudaError_t stage(const StageArgs &a, int grid, cudaStream_t s) {
-    stage_kernel<R, L, VISC, T><<<grid, T::NT, S::total, s>>>(a);
+    stage_kernel<R, L, VISC, T, MICRO><<<grid, T::NT, S::total, s>>>(a);
     return cudaGetLastError();
   }
   static int max_resident_blocks() {
@@ -1195,7 +1371,7 @@ struct Variant {
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
     if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
       return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, step_kernel<R, L, VISC, T>, T::NT,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, step_kernel<R, L, VISC, T, MICRO>, T::NT,
                                                       S::total) != cudaSuccess)
       return 0;
     return per * nsm;
@@ -1211,7 +1387,7 @@ struct Variant {
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, step_kernel<R, L, VISC, T>, a);
+    return cudaLaunchKernelEx(&cfg, step_kernel<R, L, VISC, T, MICRO>, a);
   }
   static TileVariant get() {
     TileVariant v;
@@ -1250,6 +1426,18 @@ struct Family {
     KernelSet k;
     k.nvariants = 0;
     TileVariant vs[] = {Variant<R, L, VISC, Ts>::get()...};
+    for (const TileVariant &v : vs) k.var[k.nvariants++] = v;
+    k.rate = &rate;
+    k.budget = &budget;
+    k.satadj = &satadj;
+    return k;
+  }
+  // kernels with the sedimentation fluxes and the Kessler scheme compiled in (inviscid)
+  template <class... Ts>
+  static KernelSet set_micro() {
+    KernelSet k;
+    k.nvariants = 0;
+    TileVariant vs[] = {Variant<R, L, false, Ts, true>::get()...};
     for (const TileVariant &v : vs) k.var[k.nvariants++] = v;
     k.rate = &rate;
     k.budget = &budget;

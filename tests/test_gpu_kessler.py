@@ -1,0 +1,105 @@
+"""Parity of the library's Kessler microphysics (Sec. 3) and sedimentation (Sec. 2, Eq. d3)
+with the oracle, through the C ABI: whole steps of a moist x-z bubble with Earth water and of
+a 3-D Jovian column with water and ammonia, FP64 (1e-12) and FP32 (1e-5) by the per-field
+relative L2 of the parity suite; conservation of dry air and species totals; the
+non-convergence report."""
+import dataclasses
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import Oracle
+
+from test_gpu_parity import TOL, rel_errs, rounded
+
+pytestmark = pytest.mark.gpu
+
+K_EARTH = (1e9, 1e-3, 0.5, 1e-2)
+K_JOVIAN = (1e9, 1e-4, 0.0, 1e-2)  # the paper's Jovian run, with k5 = -20 m/s
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1901_02955_gb300 import build
+    build.build()
+
+
+def with_rain(w, frac, seed=71):
+    """Precipitation of each vapour set to a random fraction (up to frac) of the vapour."""
+    rs = np.random.default_rng(seed)
+    Y = w.Y.copy()
+    nvap, nc = len(w.vapors), w.ncond
+    for i in range(nvap):
+        Y[1 + nvap + i * nc + 1] = Y[1 + i] * rs.uniform(0.0, frac, size=Y[1].shape)
+    return w.with_state(Y)
+
+
+def cases():
+    return {
+        "earth_2d": lambda: dataclasses.replace(
+            with_rain(W.add_random_motion(W.moist_adjoint_bubble(n=24)), 0.1),
+            kessler_k=K_EARTH, w_term=(0.0, -5.0)),
+        "jovian_3d": lambda: dataclasses.replace(
+            with_rain(W.add_random_motion(W.jovian(nx=9, ny=7, nz=24)), 0.05),
+            kessler_k=K_JOVIAN, w_term=(0.0, -20.0)),
+    }
+
+
+def Context(*a, **k):
+    from paper_1901_02955_gb300 import Context as C
+    return C(*a, **k)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("name", list(cases()))
+def test_kessler_steps_match_oracle(name, dtype):
+    w = cases()[name]()
+    Y0 = rounded(w, dtype)
+    o = Oracle(w)
+    dt = o.dt_cfl(Y0)
+    Yo, _, rc = o.step(Y0, 3, dt=dt)
+    assert rc >= 0
+    ctx = Context(w, dtype=dtype)
+    ctx.set_state(Y0)
+    ctx.step(3, dt_fixed=dt)
+    err = rel_errs(ctx.get_state(), Yo, Y0, w)
+    assert np.all(err <= TOL[dtype]), dict(zip(w.field_names(), err))
+
+
+@pytest.mark.parametrize("name", list(cases()))
+def test_kessler_steps_conserve_mass(name):
+    w = cases()[name]()
+    ctx = Context(w, dtype="f64")
+    ctx.set_state(w.Y)
+    b0 = ctx.budget()["total"]
+    ctx.step(5)
+    b1 = ctx.budget()["total"]
+    nvap, nc = len(w.vapors), w.ncond
+    assert b1[0] == pytest.approx(b0[0], rel=1e-13)
+    for i in range(nvap):
+        idx = [1 + i] + [1 + nvap + i * nc + j for j in range(nc)]
+        assert sum(b1[f] for f in idx) == pytest.approx(sum(b0[f] for f in idx), rel=1e-12)
+
+
+def test_kessler_non_convergence_is_reported():
+    from paper_1901_02955_gb300 import SnapError, capi
+    w = dataclasses.replace(cases()["earth_2d"](), kessler_max_iter=1)
+    ctx = Context(w, dtype="f64")
+    ctx.set_state(w.Y)
+    with pytest.raises(SnapError) as e:
+        ctx.step(1)
+    assert e.value.code == capi.ENOCONV
+
+
+def test_adjoint_reports_not_supported_with_microphysics():
+    from paper_1901_02955_gb300 import SnapError, capi
+    w = cases()["earth_2d"]()
+    ctx = Context(w, dtype="f64")
+    ctx.set_state(w.Y)
+    with pytest.raises(SnapError) as e:
+        ctx.record(2, 1)
+    assert e.value.code == capi.ENOTSUP
