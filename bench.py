@@ -241,15 +241,24 @@ def reference_arm(args, rank):
     print(json.dumps(line), flush=True)
 
 
-def extra_workload(args, local):
+def extra_workload(args, local, rank=0, world=1):
     """Measurement line for the 3-D moist column or the moist ensemble (inputs larger than
-    L2, so no flush is needed between steps)."""
+    L2, so no flush is needed between steps). Under torchrun the ensemble's domains are
+    split across the ranks (no exchange between them; strong scaling of the fixed ensemble)
+    and the step time is the slowest rank's; other workloads run on rank 0."""
     import torch
     from paper_1901_02955_gb300 import Context
+    from paper_1901_02955_gb300.ranks import max_over_ranks, shard_domains
     torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    ws = workload("f32", args.workload)
+    ws_all = workload("f32", args.workload)
+    cells_all = sum(w.ncells for w in ws_all)
+    ws = [ws_all[d] for d in shard_domains([w.ncells for w in ws_all], world)[rank]]
     ctx = Context(ws, dtype="f32")
     ctx.set_stream(stream)
     for d, w in enumerate(ws):
@@ -264,14 +273,19 @@ def extra_workload(args, local):
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
     torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
     with Clocks(local) as clk:
         for s_, e_ in ev:
             s_.record(stream)
             ctx.step_async(1)
             e_.record(stream)
         torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
     rc, flags = ctx.check()
-    ms = float(np.mean([s_.elapsed_time(e_) for s_, e_ in ev]))
+    ms = max_over_ranks(float(np.mean([s_.elapsed_time(e_) for s_, e_ in ev])), dist,
+                        torch.device("cuda", local))
     # per-stage launch times
     per = []
     for i in range(max(3, args.steps // 2)):
@@ -289,12 +303,20 @@ def extra_workload(args, local):
     three_d = ws[0].ny > 1
     flops_cell = alg_flops_per_cell_stage(3 if three_d else 2, 3 if three_d else 2, nv)
     tflops = flops_cell * cells / (stage_ms * 1e-3) / 1e12
-    line = {"metric": METRIC, "value": cells * 3 / (ms * 1e-3), "unit": UNIT, "n_gpus": 1,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic",
-            "config": {"workload": args.workload, "cells": cells, "nfields": nv,
-                       "domains": len(ws), "l2": "inputs larger than L2",
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    line = {"metric": METRIC, "value": cells_all * 3 / (ms * 1e-3), "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True,
+            "scaling": "strong" if args.workload.startswith("ensemble_96") else "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "cells": cells_all, "nfields": nv,
+                       "domains": len(ws_all), "domains_rank0": len(ws),
+                       "cells_rank0": cells, "l2": "inputs larger than L2",
+                       "parallelism": f"ensemble domains split over {world} ranks"
+                       if world > 1 else "single GPU",
                        "device_checks": {"rc": rc, "flags": flags},
                        "info": ctx.info(), "autotune": tuned},
             "roofline": {"bound": "alu", "achieved": tflops, "peak": FP32_PEAK_TFLOPS,
@@ -310,6 +332,8 @@ def extra_workload(args, local):
                                  "algorithmic_bytes_per_launch": alg}},
             "gpu_launches": 3 * args.steps, "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
 
 
 def adjoint_workload(args, local):
@@ -380,7 +404,9 @@ def main():
             adjoint_workload(args, local)
         return
     if args.workload != WORKLOAD:
-        if rank == 0:
+        if args.workload.startswith("ensemble_96"):
+            extra_workload(args, local, rank, world)
+        elif rank == 0:
             extra_workload(args, local)
         return
     import torch
