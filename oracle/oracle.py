@@ -56,6 +56,8 @@ class _Grid(C.Structure):
         ("w_term", C.c_double * MAXC),
         ("kessler", C.c_int), ("kessler_k", C.c_double * 4),
         ("kessler_max_iter", C.c_int), ("kessler_tol", C.c_double),
+        ("cool_rate", C.c_double), ("cool_p_lo", C.c_double), ("cool_p_hi", C.c_double),
+        ("sponge_tau0", C.c_double), ("sponge_p0", C.c_double),
     ]
 
 
@@ -141,6 +143,12 @@ def grid_from_workload(w, satadj: Optional[bool] = None, nu: Optional[float] = N
         g.kessler_k[r] = kv
     g.kessler_max_iter = getattr(w, "kessler_max_iter", 30)
     g.kessler_tol = getattr(w, "kessler_tol", 1e-12)
+    cool = tuple(getattr(w, "cooling", ()))  # (rate K/s, p_lo, p_hi)
+    if cool:
+        g.cool_rate, g.cool_p_lo, g.cool_p_hi = cool
+    sponge = tuple(getattr(w, "sponge", ()))  # (tau0 s, p0 Pa)
+    if sponge:
+        g.sponge_tau0, g.sponge_p0 = sponge
     return g, keep
 
 

@@ -705,12 +705,37 @@ int orc_rhs(const orc_grid *g, const double *Y, double *dYdt) {
         }
   }
 
-  /* 4. gravity sources (Eq. mom3 and the energy equation of Sec. 2) */
+  /* 4. gravity sources (Eq. mom3 and the energy equation of Sec. 2), and the forcing of the
+   *    Jovian simulation (Sec. 6):
+   *    cooling: d(rho e)/dt -= C_v Q, C_v = sum_k c_k rho_k, in the levels whose reference
+   *      pressure pbar_k lies in [cool_p_lo, cool_p_hi];
+   *    sponge: d(rho u_h)/dt -= rho u_h / (tau0 (pbar_k/p0)^2) for the horizontal momenta
+   *      where pbar_k < p0; rho e is left unchanged, so the damped kinetic energy turns into
+   *      heat.
+   *    READING: the bands and the sponge time use the fixed reference pressure of the level. */
   const int mw = mom_slot(g, 2);
   for (int k = 0; k < nz; ++k)
     for (int j = 0; j < ny; ++j)
       for (int i = 0; i < nx; ++i) {
         long c = ((long)k * ny + j) * nx + i;
+        const double pk = pbar_cell(g, k);
+        if (g->cool_rate != 0.0 && pk >= g->cool_p_lo && pk <= g->cool_p_hi) {
+          double Cv = c_vd(g) * Y[c];
+          for (int a = 0; a < g->nvap; ++a) {
+            Cv += g->sig_v[a] * c_vd(g) * Y[(long)(1 + a) * ncell + c];
+            for (int b = 0; b < g->ncond; ++b)
+              Cv += g->sig_c[a][b] * c_vd(g) * Y[(long)icond(g, a, b) * ncell + c];
+          }
+          dYdt[(long)(nv - 1) * ncell + c] -= Cv * g->cool_rate;
+        }
+        if (g->sponge_tau0 > 0.0 && pk < g->sponge_p0) {
+          const double r = pk / g->sponge_p0, tau = g->sponge_tau0 * r * r;
+          for (int d = 0; d < 2; ++d) {
+            if (d == 1 && !three_d) continue;
+            const long m = (long)mom_slot(g, d) * ncell + c;
+            dYdt[m] -= Y[m] / tau;
+          }
+        }
         double rho = X[ext_index(&e, k, j, i)];
         dYdt[(long)mw * ncell + c] -= (rho - g->rho_bar[k]) * g->grav;
         if (g->gravity_energy_pointwise) {
@@ -1063,6 +1088,7 @@ int orc_rhs_adjoint(const orc_grid *g, const double *Y, const double *mu, double
   if (g->nu > 0.0) return -3; /* inviscid only */
   for (int j = 0; j < g->ncond; ++j)
     if (g->w_term[j] != 0.0) return -3; /* no sedimentation */
+  if (g->cool_rate != 0.0 || g->sponge_tau0 > 0.0) return -3; /* no forcing */
   if (nx < 1 || ny < 1 || nz < 3) return -1;
   ext_dims e = {nx + 6, three_d ? ny + 6 : 1, nz + 6, 3, three_d ? 3 : 0, 3};
   const long next = (long)e.nxe * e.nye * e.nze;

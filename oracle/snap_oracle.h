@@ -59,6 +59,11 @@ typedef struct {
   double kessler_k[4];
   int kessler_max_iter;
   double kessler_tol;
+  /* Sec. 6 forcing of the Jovian simulation (0 disables each): a body cooling of cool_rate
+   * K/s at constant volume in levels whose reference pressure lies in [cool_p_lo, cool_p_hi];
+   * a sponge relaxing the horizontal momenta at 1/(tau0 (p/p0)^2) where p < p0 */
+  double cool_rate, cool_p_lo, cool_p_hi;
+  double sponge_tau0, sponge_p0;
 } orc_grid;
 
 int orc_nvar(const orc_grid *g);

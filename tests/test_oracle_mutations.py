@@ -13,7 +13,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "snap_oracle.c")
 PINS = ["tests/test_oracle_weno.py", "tests/test_oracle_lmars.py", "tests/test_oracle_thermo.py",
         "tests/test_oracle_satadj.py", "tests/test_oracle_scheme.py",
-        "tests/test_oracle_adjoint.py", "tests/test_oracle_kessler.py"]
+        "tests/test_oracle_adjoint.py", "tests/test_oracle_kessler.py",
+        "tests/test_oracle_forcing.py"]
 
 MUTANTS = {
     "weno beta0 curvature coefficient": ("b[0] = 13.0 / 12.0 * t * t;", "b[0] = 13.0 / 6.0 * t * t;"),
@@ -57,6 +58,10 @@ MUTANTS = {
     "kessler evaporation without rain factor": ("    phi[0] = -k4 * x[2] * sup;", "    phi[0] = -k4 * sup;"),
     "sedimentation from the wrong side": ("const double *XS = wt < 0.0 ? XR : XL;",
                                           "const double *XS = wt < 0.0 ? XL : XR;"),
+    "cooling without condensate heat capacity": ("              Cv += g->sig_c[a][b] * c_vd(g) * Y[(long)icond(g, a, b) * ncell + c];",
+                                                 "              (void)b;"),
+    "sponge time linear in pressure": ("const double r = pk / g->sponge_p0, tau = g->sponge_tau0 * r * r;",
+                                       "const double r = pk / g->sponge_p0, tau = g->sponge_tau0 * r;"),
     "sedimentation energy without kinetic part": ("F[nv - 1] += ms * (g->sig_c[i][j] * c_vd(g) * T + 0.5 * u2 + mu_of(g, i, j));",
                                                   "F[nv - 1] += ms * (g->sig_c[i][j] * c_vd(g) * T + mu_of(g, i, j));"),
 }

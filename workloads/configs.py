@@ -89,6 +89,10 @@ class Workload:
     kessler_k: tuple = ()
     kessler_max_iter: int = 30
     kessler_tol: float = 1e-12
+    # forcing of the Jovian simulation: body cooling (rate K/s, p_lo, p_hi) and sponge
+    # (tau0 s, p0 Pa) by the reference pressure of each level; empty: off
+    cooling: tuple = ()
+    sponge: tuple = ()
 
     @property
     def nvapor(self) -> int:
