@@ -35,8 +35,19 @@ def pbar(w):
     return 0.5 * (w.p_bar_face[:-1] + w.p_bar_face[1:])
 
 
+def with_condensate(w, seed=82):
+    """Cloud and precipitation in every cell, fractions of the vapour."""
+    rs = np.random.default_rng(seed)
+    Y = w.Y.copy()
+    nvap, nc = len(w.vapors), w.ncond
+    for i in range(nvap):
+        for j in range(nc):
+            Y[1 + nvap + i * nc + j] = Y[1 + i] * rs.uniform(0.05, 0.3, size=Y[1].shape)
+    return w.with_state(Y)
+
+
 def test_cooling_tendency_in_the_band_only():
-    w0 = W.add_random_motion(column())
+    w0 = W.add_random_motion(with_condensate(column()))
     pk = pbar(w0)
     lo, hi = np.sort(pk)[6], np.sort(pk)[16]
     w1 = dataclasses.replace(w0, cooling=(Q, lo, hi))
