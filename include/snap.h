@@ -92,6 +92,14 @@ typedef struct snap_grid_desc {
   double kessler_k[4];
   int kessler_max_iter;
   double kessler_tol;
+  /* Sec. 6 forcing of the Jovian simulation, by the reference pressure p_k of each level
+   * (0 disables each): a body cooling of cool_rate K/s at constant volume (rho e loses C_v
+   * cool_rate, C_v the mixture's heat capacity) where cool_p_lo <= p_k <= cool_p_hi; a sponge
+   * relaxing the horizontal momenta at 1/(sponge_tau0 (p_k/sponge_p0)^2) where p_k <
+   * sponge_p0, leaving rho e unchanged. Needs n_vapor > 0 (the library builds the forcing
+   * into its moist kernels). */
+  double cool_rate, cool_p_lo, cool_p_hi;
+  double sponge_tau0, sponge_p0;
 } snap_grid_desc;
 
 /* Domain totals: field sums times the cell volume, and sum of (rho e + rho g z) dV. */

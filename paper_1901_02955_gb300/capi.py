@@ -50,7 +50,9 @@ class GridDesc(C.Structure):
                 ("weno_eps", C.c_double),
                 ("w_term", C.c_double * MAX_COND),
                 ("kessler", C.c_int), ("kessler_k", C.c_double * 4),
-                ("kessler_max_iter", C.c_int), ("kessler_tol", C.c_double)]
+                ("kessler_max_iter", C.c_int), ("kessler_tol", C.c_double),
+                ("cool_rate", C.c_double), ("cool_p_lo", C.c_double), ("cool_p_hi", C.c_double),
+                ("sponge_tau0", C.c_double), ("sponge_p0", C.c_double)]
 
 
 class Budget(C.Structure):
@@ -152,6 +154,12 @@ def desc_from_workload(w, dtype: Optional[str] = None, satadj: Optional[bool] = 
         d.kessler_k[r] = kv
     d.kessler_max_iter = getattr(w, "kessler_max_iter", 30)
     d.kessler_tol = getattr(w, "kessler_tol", 1e-12)
+    cool = tuple(getattr(w, "cooling", ()))
+    if cool:
+        d.cool_rate, d.cool_p_lo, d.cool_p_hi = cool
+    sponge = tuple(getattr(w, "sponge", ()))
+    if sponge:
+        d.sponge_tau0, d.sponge_p0 = sponge
     return d, keep
 
 

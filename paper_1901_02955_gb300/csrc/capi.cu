@@ -201,6 +201,10 @@ static int validate(const snap_grid_desc &d, const snap_grid_desc &d0, int idx, 
   for (int j = 0; j < SNAP_MAX_COND; ++j)
     if (!isfinite(d.w_term[j]) || (d.w_term[j] != 0.0 && j >= d.n_cond))
       return bad("w_term must be finite and zero beyond n_cond");
+  if (!isfinite(d.cool_rate) || !(d.sponge_tau0 >= 0.0) || (d.sponge_tau0 > 0.0 && !(d.sponge_p0 > 0.0)))
+    return bad("cooling rate must be finite, sponge_tau0 >= 0 with sponge_p0 > 0");
+  if ((d.cool_rate != 0.0 || d.sponge_tau0 > 0.0) && d.n_vapor < 1)
+    return bad("the forcing is built for moist contexts (n_vapor > 0)");
   if (d.kessler) {
     if (d.n_vapor < 1 || d.n_cond != 2) return bad("the Kessler scheme needs vapours with cloud and precipitation (n_cond == 2)");
     if (d.kessler_max_iter < 1) return bad("kessler_max_iter must be >= 1");
@@ -220,7 +224,9 @@ static int validate(const snap_grid_desc &d, const snap_grid_desc &d0, int idx, 
       (d.nu > 0) != (d0.nu > 0) || d.nu != d0.nu || d.satadj != d0.satadj ||
       d.weno_eps != d0.weno_eps || d.kessler != d0.kessler ||
       memcmp(d.kessler_k, d0.kessler_k, sizeof d.kessler_k) != 0 ||
-      memcmp(d.w_term, d0.w_term, sizeof d.w_term) != 0)
+      memcmp(d.w_term, d0.w_term, sizeof d.w_term) != 0 || d.cool_rate != d0.cool_rate ||
+      d.cool_p_lo != d0.cool_p_lo || d.cool_p_hi != d0.cool_p_hi ||
+      d.sponge_tau0 != d0.sponge_tau0 || d.sponge_p0 != d0.sponge_p0)
     return bad("domains of one context must share dtype, species, gases, dimensionality, "
                "viscosity and scheme options");
   for (int i = 0; i < d.n_vapor; ++i) {
@@ -276,6 +282,11 @@ static void derive_phys(const snap_grid_desc &d, Phys &ph) {
   ph.kessler_max_iter = d.kessler_max_iter;
   ph.kessler_tol = d.kessler_tol;
   for (int r = 0; r < 4; ++r) ph.kessler_k[r] = d.kessler_k[r];
+  ph.cool_rate = d.cool_rate;
+  ph.cool_p_lo = d.cool_p_lo;
+  ph.cool_p_hi = d.cool_p_hi;
+  ph.sponge_tau0 = d.sponge_tau0;
+  ph.sponge_p0 = d.sponge_p0;
 }
 
 template <class T>
@@ -312,6 +323,11 @@ static void derive_cst(const Phys &ph, double tol_floor, CstT<T> &c) {
   for (int r = 0; r < 4; ++r) c.kk[r] = T(ph.kessler_k[r]);
   c.kessler_tol = T(ph.kessler_tol > tol_floor ? ph.kessler_tol : tol_floor);
   c.c_vd = T(ph.c_vd);
+  c.cool_rate = T(ph.cool_rate);
+  c.cool_p_lo = T(ph.cool_p_lo);
+  c.cool_p_hi = T(ph.cool_p_hi);
+  c.sponge_itau0 = T(ph.sponge_tau0 > 0 ? 1.0 / ph.sponge_tau0 : 0.0);
+  c.sponge_ip0 = T(ph.sponge_p0 > 0 ? 1.0 / ph.sponge_p0 : 0.0);
 }
 
 static StageArgs args_of(snap_ctx *ctx, int stage) {
@@ -360,9 +376,8 @@ extern "C" int snap_init_grid(snap_ctx **out, const snap_grid_desc *d, int n_dom
   ctx->visc = d[0].nu > 0.0;
   ctx->nv = 1 + ctx->nvap + ctx->nvap * ctx->ncond + (ctx->three_d ? 3 : 2) + 1;
   ctx->word = ctx->f32 ? 4 : 8;
-  // the microphysics switch of the descriptor picks kernels with sedimentation and the
-  // Kessler scheme compiled in
-  int micro = d[0].kessler != 0;
+  // microphysics, sedimentation or forcing pick kernels with those terms compiled in
+  int micro = d[0].kessler != 0 || d[0].cool_rate != 0.0 || d[0].sponge_tau0 > 0.0;
   for (int j = 0; j < SNAP_MAX_COND; ++j) micro |= d[0].w_term[j] != 0.0;
   if (!find_kernels(ctx->f32, ctx->nvap, ctx->ncond, ctx->three_d, ctx->visc, micro, &ctx->ks)) {
     delete ctx;
@@ -374,7 +389,7 @@ extern "C" int snap_init_grid(snap_ctx **out, const snap_grid_desc *d, int n_dom
   derive_phys(d[0], ctx->ph);
   ctx->desc.assign(d, d + n_domains);
   // the adjoint covers neither the microphysics nor sedimentation
-  if (!ctx->visc && n_domains == 1 && !ctx->ph.kessler && !ctx->ph.sediment)
+  if (!ctx->visc && n_domains == 1 && !micro)
     ctx->has_adj = find_adjoint_kernels(ctx->f32, ctx->nvap, ctx->ncond, ctx->three_d, &ctx->adj) ? 1 : 0;
   cudaError_t e = cudaSuccess;
   for (int v = 0; v < ctx->ks.nvariants && e == cudaSuccess; ++v) e = ctx->ks.var[v].prepare();

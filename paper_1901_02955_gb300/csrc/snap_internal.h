@@ -30,6 +30,8 @@ struct Phys {
   int kessler, kessler_max_iter;           // Kessler scheme (Sec. 3) after every step
   double kessler_k[4];                     // k1 .. k4
   double kessler_tol;
+  double cool_rate, cool_p_lo, cool_p_hi;  // body cooling (Sec. 6), K/s in [p_lo, p_hi]
+  double sponge_tau0, sponge_p0;           // sponge where p < p0 (Sec. 6)
 };
 
 // The same constants in the arithmetic type of a kernel, derived on the host, so that FP32
@@ -41,6 +43,7 @@ struct CstT {
   T sig_c[kMaxVap][kMaxCond], sigc_m1[kMaxVap][kMaxCond], mu[kMaxVap][kMaxCond];
   T pref[kMaxVap], beta[kMaxVap], delta[kMaxVap], inv_Tref[kMaxVap], sighat_m1[kMaxVap];
   T w_term[kMaxCond], kk[4], kessler_tol, c_vd;
+  T cool_rate, cool_p_lo, cool_p_hi, sponge_itau0, sponge_ip0;
 };
 
 // One domain as the kernels see it (device memory).

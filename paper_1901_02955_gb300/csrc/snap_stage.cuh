@@ -1180,6 +1180,25 @@ __device__ __forceinline__ void stage_tiles(const StageArgs &a, const int stage,
           mt += s_fl[s * B::NF + f1];
         }
         acc[m][L::IE] -= grav * R(0.5) * (mb + mt);
+        if constexpr (MICRO && L::MOIST) {
+          // forcing of the Jovian simulation (Sec. 6) by the level's reference pressure
+          const R pk = P::pc(D, k);
+          if (C.cool_rate != R(0) && pk >= C.cool_p_lo && pk <= C.cool_p_hi) {
+            R Cv = ys[m][0];  // heat capacity at constant volume / c_vd
+#pragma unroll
+            for (int i2 = 0; i2 < L::NVAP; ++i2) {
+              Cv += C.sig_v[i2] * ys[m][1 + i2];
+#pragma unroll
+              for (int j2 = 0; j2 < L::NCOND; ++j2) Cv += C.sig_c[i2][j2] * ys[m][L::cond(i2, j2)];
+            }
+            acc[m][L::IE] -= Cv * C.c_vd * C.cool_rate;
+          }
+          if (C.sponge_itau0 != R(0) && pk * C.sponge_ip0 < R(1)) {
+            const R r = pk * C.sponge_ip0, rate = C.sponge_itau0 * Ar<R>::rcp(r * r);
+            acc[m][L::mom(0)] -= ys[m][L::mom(0)] * rate;
+            if constexpr (L::D3) acc[m][L::mom(1)] -= ys[m][L::mom(1)] * rate;
+          }
+        }
         const long long g = ((long long)k * ny + (y0 + ly)) * nx + (x0 + lx);
         R yo[NV];
 #pragma unroll

@@ -1,8 +1,8 @@
-"""Parity of the library's Kessler microphysics (Sec. 3) and sedimentation (Sec. 2, Eq. d3)
-with the oracle, through the C ABI: whole steps of a moist x-z bubble with Earth water and of
-a 3-D Jovian column with water and ammonia, FP64 (1e-12) and FP32 (1e-5) by the per-field
-relative L2 of the parity suite; conservation of dry air and species totals; the
-non-convergence report."""
+"""Parity of the library's Kessler microphysics (Sec. 3), sedimentation (Sec. 2, Eq. d3) and
+the Jovian forcing (Sec. 6: body cooling, sponge) with the oracle, through the C ABI: whole
+steps of a moist x-z bubble with Earth water and of a 3-D Jovian column with water and
+ammonia, FP64 (1e-12) and FP32 (1e-5) by the per-field relative L2 of the parity suite;
+conservation of dry air and species totals; the non-convergence report."""
 import dataclasses
 
 import numpy as np
@@ -46,7 +46,18 @@ def cases():
         "jovian_3d": lambda: dataclasses.replace(
             with_rain(W.add_random_motion(W.jovian(nx=9, ny=7, nz=24)), 0.05),
             kessler_k=K_JOVIAN, w_term=(0.0, -20.0)),
+        # the Jovian forcing (Sec. 6): cooling 100x the paper's 1 K/day in a middle band and a
+        # sponge in the upper levels, with the microphysics
+        "jovian_forced": lambda: forced(dataclasses.replace(
+            with_rain(W.add_random_motion(W.jovian(nx=9, ny=7, nz=24)), 0.05),
+            kessler_k=K_JOVIAN, w_term=(0.0, -20.0))),
     }
+
+
+def forced(w):
+    pk = np.sort(0.5 * (w.p_bar_face[:-1] + w.p_bar_face[1:]))
+    return dataclasses.replace(w, cooling=(100.0 / 86400.0, pk[6], pk[16]),
+                               sponge=(1e4, pk[8]))
 
 
 def Context(*a, **k):
