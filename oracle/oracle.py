@@ -98,6 +98,7 @@ def _load():
     lib.orc_step_adjoint.argtypes = [G, _D, C.c_double, _D, _D]
     lib.orc_satadj_adjoint_cell.argtypes = [G, _D, _D, _D]
     lib.orc_kessler_cell.argtypes = [G, _D, C.c_double]
+    lib.orc_theta_e.argtypes = [G, _D, _D]
     return lib
 
 
@@ -240,6 +241,15 @@ class Oracle:
         rc = self.lib.orc_rhs_adjoint(C.byref(self.grid), _ptr(Y), _ptr(mu), _ptr(out))
         if rc:
             raise RuntimeError(f"orc_rhs_adjoint failed: {rc}")
+        return out
+
+    def theta_e(self, Y):
+        """Equivalent potential temperature of every cell (App. A, Eq. theta_e)."""
+        Y = np.ascontiguousarray(Y, dtype=np.float64).reshape(self.shape)
+        out = np.zeros(self.shape[1:])
+        rc = self.lib.orc_theta_e(C.byref(self.grid), _ptr(Y), _ptr(out))
+        if rc:
+            raise RuntimeError(f"orc_theta_e failed: {rc}")
         return out
 
     def kessler_cell(self, Yc, dt):

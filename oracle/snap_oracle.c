@@ -443,6 +443,31 @@ int orc_kessler_cell(const orc_grid *g, double *Y, double dt) {
   return worst;
 }
 
+/* App. A, Eq. theta_e: theta_e = T (p0/p_d)^(R_d q_d / c) exp(L q_v / (c T)), c = c_pd q_d +
+ * c_l q_t, with the mass fractions q of the total density, q_t = q_v + q_cloud, p_d the
+ * partial pressure of dry air, L = L^r - (c_l - c_pv)(T - T^r) the latent heat at T (Eq.
+ * latent) and c_l the cloud's heat capacity. */
+int orc_theta_e(const orc_grid *g, const double *Y, double *theta_e) {
+  if (g->nvap != 1 || g->ncond < 1) return -3;
+  const int nv = orc_nvar(g), im0 = im0_of(g);
+  const long ncell = (long)g->nx * g->ny * g->nz;
+  const double cpd = g->gamma_d * c_vd(g), cl = g->sig_c[0][0] * c_vd(g);
+  const double dc = dc_of(g, 0, 0);
+  double Yc[64], X[64], T;
+  for (long c = 0; c < ncell; ++c) {
+    for (int v = 0; v < nv; ++v) Yc[v] = Y[v * ncell + c];
+    orc_cons_to_prim(g, Yc, X, &T, NULL);
+    double rho = 0.0;
+    for (int s = 0; s < im0; ++s) rho += Yc[s];
+    const double qd = Yc[0] / rho, qv = Yc[1] / rho, qt = (Yc[1] + Yc[icond(g, 0, 0)]) / rho;
+    const double pd = Yc[0] * g->Rd * T;
+    const double L = g->Lref[0][0] - dc * (T - g->Tref[0]);
+    const double cc = cpd * qd + cl * qt;
+    theta_e[c] = T * pow(1e5 / pd, g->Rd * qd / cc) * exp(L * qv / (cc * T));
+  }
+  return 0;
+}
+
 /* Exact equilibrium of the same cell (test pin): the internal energy U = rho e - K is fixed;
  * at trial temperature T each vapour holds min(total_i, p*_i(T)/(R_i T)) and its cloud the
  * rest; F(T) = C_v(T) T + A(T) - U is strictly increasing, so bisection finds the root. */

@@ -99,6 +99,11 @@ int orc_satadj_bisect(const orc_grid *g, double *Ycell);
  * iteration did not converge. */
 int orc_kessler_cell(const orc_grid *g, double *Ycell, double dt);
 
+/* App. A, Eq. theta_e (Emanuel's 4.5.11): equivalent potential temperature of each cell of a
+ * state with one vapour, whose first condensate is the cloud (precipitation is not part of
+ * q_t), p0 = 1e5 Pa. Returns -3 unless the grid has exactly one vapour. */
+int orc_theta_e(const orc_grid *g, const double *Y, double *theta_e);
+
 /* ---- whole-grid pieces ---- */
 /* dYdt = L(Y): minus the flux divergence plus the gravity source (and viscous fluxes). */
 int orc_rhs(const orc_grid *g, const double *Y, double *dYdt);

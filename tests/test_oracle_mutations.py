@@ -14,7 +14,7 @@ SRC = os.path.join(ROOT, "oracle", "snap_oracle.c")
 PINS = ["tests/test_oracle_weno.py", "tests/test_oracle_lmars.py", "tests/test_oracle_thermo.py",
         "tests/test_oracle_satadj.py", "tests/test_oracle_scheme.py",
         "tests/test_oracle_adjoint.py", "tests/test_oracle_kessler.py",
-        "tests/test_oracle_forcing.py"]
+        "tests/test_oracle_forcing.py", "tests/test_oracle_theta_e.py"]
 
 MUTANTS = {
     "weno beta0 curvature coefficient": ("b[0] = 13.0 / 12.0 * t * t;", "b[0] = 13.0 / 6.0 * t * t;"),
@@ -58,6 +58,10 @@ MUTANTS = {
     "kessler evaporation without rain factor": ("    phi[0] = -k4 * x[2] * sup;", "    phi[0] = -k4 * sup;"),
     "sedimentation from the wrong side": ("const double *XS = wt < 0.0 ? XR : XL;",
                                           "const double *XS = wt < 0.0 ? XL : XR;"),
+    "theta_e latent heat at the reference temperature": ("const double L = g->Lref[0][0] - dc * (T - g->Tref[0]);",
+                                                          "const double L = g->Lref[0][0];"),
+    "theta_e exponent without the cloud heat capacity": ("const double cc = cpd * qd + cl * qt;",
+                                                         "const double cc = cpd * qd + cl * qv;"),
     "cooling without condensate heat capacity": ("              Cv += g->sig_c[a][b] * c_vd(g) * Y[(long)icond(g, a, b) * ncell + c];",
                                                  "              (void)b;"),
     "sponge time linear in pressure": ("const double r = pk / g->sponge_p0, tau = g->sponge_tau0 * r * r;",

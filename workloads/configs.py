@@ -442,6 +442,113 @@ def moist_adjoint_bubble(n=256, rh=0.95, rh_core=1.05, A=0.5, R=250.0, xc=500.0,
     return w
 
 
+def _moist_adiabat(T0, p0, r_t, R_d, gamma_d, vap, p_top, n=40000):
+    """Reversible saturated moist adiabat of Appendix A (Eq. mgrad): ln T against ln p for air
+    carrying one condensing species with total water r_t per unit mass of dry air, integrated
+    by classical RK4 in ln p from (T0, p0) up to p_top. Vapour is at saturation over the
+    condensate (the App. D Clausius-Clapeyron integral), cloud the rest of r_t; where r_t is
+    below saturation the latent terms vanish (the dry gradient of Eq. dgrad). Returns
+    (ln p ascending, T) for interpolation."""
+    c_vd = R_d / (gamma_d - 1.0)
+    c_pd = gamma_d * c_vd
+    R_v = R_d / vap.eps
+    c_pv = vap.sigma_v * c_vd + R_v
+    c_l = vap.cond[0].sigma_v * c_vd
+    dc = c_l - c_pv  # Eq. latent
+    beta = (vap.cond[0].L_ref + dc * vap.T_ref) / (R_v * vap.T_ref)
+    delta = dc / R_v
+
+    def slope(lnp, T):
+        p = np.exp(lnp)
+        t = T / vap.T_ref
+        es = vap.p_ref * np.exp(beta * (1.0 - 1.0 / t) - delta * np.log(t))
+        r_s = vap.eps * es / (p - es)
+        r_v = min(r_s, r_t)
+        r_c = r_t - r_v
+        a = r_v / vap.eps
+        lam = (vap.cond[0].L_ref - dc * (T - vap.T_ref)) / (R_v * T) if r_s < r_t else 0.0
+        num = (1.0 + a) * (1.0 + a * lam)
+        den = c_pd / R_d * (1.0 + r_v * c_pv / c_pd + r_c * c_l / c_pd) + a * lam * lam + (a * lam) ** 2
+        return T * num / den  # dT / d ln p
+
+    lnp = np.linspace(np.log(p0), np.log(p_top), n)
+    h = lnp[1] - lnp[0]
+    T = np.empty(n)
+    T[0] = T0
+    for m in range(n - 1):
+        x, y = lnp[m], T[m]
+        k1 = slope(x, y)
+        k2 = slope(x + h / 2, y + h / 2 * k1)
+        k3 = slope(x + h / 2, y + h / 2 * k2)
+        k4 = slope(x + h, y + h * k3)
+        T[m + 1] = y + h / 6 * (k1 + 2 * k2 + 2 * k3 + k4)
+    return lnp[::-1].copy(), T[::-1].copy()
+
+
+def _saturated_parcel(T, p, r_t, R_d, gamma_d, vap):
+    """Densities (rho_d, rho_v, rho_c) of air at (T, p) with total water r_t per unit dry
+    air, the vapour at saturation over the condensate or all of r_t if that is less."""
+    c_vd = R_d / (gamma_d - 1.0)
+    R_v = R_d / vap.eps
+    es = _sat_pressure(vap, R_d, gamma_d, T)
+    r_s = vap.eps * es / (p - es)
+    e = np.where(r_s < r_t, es, p * r_t / (vap.eps + r_t))
+    rho_d = (p - e) / (R_d * T)
+    rho_v = e / (R_v * T)
+    rho_c = np.maximum(r_t * rho_d - rho_v, 0.0)
+    del c_vd
+    return rho_d, rho_v, rho_c
+
+
+def bryan_moist_bubble(nx=200, nz=100, Lx=20e3, Lz=10e3, T_s=289.85, p_s=1e5, r_t=0.020,
+                       A=2.0, R=2000.0, xc=10e3, zc=2000.0, dtype="f64", nsteps=5000):
+    """Bryan moist bubble (Sec. 5, after Bryan & Fritsch 2002): a saturated environment on
+    the reversible moist adiabat from 289.85 K and 1 bar, total water fixed at all levels,
+    20 km x 10 km at 100 m; a bubble warmer by A cos^2(pi L/2) (L the distance from its
+    centre over R) at fixed pressure, saturated at its own temperature (more vapour, less
+    cloud); Earth air and water (cloud and rain slots, rain 0); walls. The background is
+    discretely hydrostatic and neutral to moist convection."""
+    R_d, gamma_d, g = 287.0, 1.4, 9.81
+    vap = earth_water(R_d, gamma_d)
+    dx, dz = Lx / nx, Lz / nz
+    lnp, Tad = _moist_adiabat(T_s, p_s, r_t, R_d, gamma_d, vap, p_top=0.2 * p_s)
+
+    def T_of(p):
+        return np.interp(np.log(p), lnp, Tad)
+
+    def rho_of(k, p):
+        rd, rv, rc = _saturated_parcel(T_of(p), p, r_t, R_d, gamma_d, vap)
+        return float(rd + rv + rc)
+
+    rho_bar, pf = _hydrostatic_column(nz, dz, g, p_s, False, rho_of)
+    pk = 0.5 * (pf[:-1] + pf[1:])
+    x = _cell_centres(nx, dx)[None, :]
+    z = _cell_centres(nz, dz)[:, None]
+    T = T_of(pk)[:, None] + cosine_bubble(A, xc, zc, R)(x, z)
+    P = pk[:, None] * np.ones_like(T)
+    rd, rv, rc = _saturated_parcel(T, P, r_t, R_d, gamma_d, vap)
+    Y = _assemble_condensed(nx, 1, nz, rd[:, None, :], rv[:, None, :], rc[:, None, :],
+                            T[:, None, :], R_d, gamma_d, vap)
+    return Workload(name=f"bryan_moist_bubble_{nx}x{nz}", nx=nx, ny=1, nz=nz, dx=dx, dy=dx,
+                    dz=dz, bc=(REFLECT,) * 6, grav=g, gamma_d=gamma_d, R_d=R_d, vapors=[vap],
+                    ncond=2, rho_bar=rho_bar, p_bar_face=pf, Y=Y, nsteps=nsteps, dtype=dtype)
+
+
+def _assemble_condensed(nx, ny, nz, rho_d, rho_v, rho_c, T, R_d, gamma_d, vap):
+    """Conserved state at rest of dry air, one vapour and its cloud (rain 0): rho e =
+    (c_vd rho_d + c_v rho_v + c_l rho_c) T + mu_c rho_c, mu_c = -(L^r + (c_l - c_pv) T^r)
+    (Sec. 2, Eqs. energy and muij)."""
+    c_vd = R_d / (gamma_d - 1.0)
+    c_pv = vap.sigma_v * c_vd + R_d / vap.eps
+    c_l = vap.cond[0].sigma_v * c_vd
+    mu_c = -(vap.cond[0].L_ref + (c_l - c_pv) * vap.T_ref)
+    nmom = 3 if ny > 1 else 2
+    Y = np.zeros((1 + 1 + 2 + nmom + 1, nz, ny, nx))
+    Y[0], Y[1], Y[2] = rho_d, rho_v, rho_c
+    Y[-1] = (c_vd * rho_d + vap.sigma_v * c_vd * rho_v + c_l * rho_c) * T + mu_c * rho_c
+    return Y
+
+
 def ensemble(sizes=(64, 128, 256, 512), per_size=24, seed=BASE_SEED + 4, nsteps=200):
     """Ensemble of 2-D moist bubbles of uneven sizes on 1 km boxes: amplitude ~ U(0.2, 2) K
     and radius ~ U(150, 400) m drawn per member from the seeded stream."""
