@@ -40,7 +40,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--workload", default=WORKLOAD,
                    choices=[WORKLOAD, "jovian_256x256x128", "jovian_256x256x128_kessler",
-                            "ensemble_96", "ensemble_96_autotuned", "adjoint_256x256"],
+                            "ensemble_96", "ensemble_96_autotuned", "adjoint_256x256",
+                            "bryan_1000s"],
                    help="the default is the headline workload; the others print an extra "
                         "measurement line of the same form (3-D moist column, the same with "
                         "Kessler microphysics and falling precipitation, moist ensemble) or "
@@ -336,6 +337,48 @@ def extra_workload(args, local, rank=0, world=1):
         dist.destroy_process_group()
 
 
+def bryan_workload(args, local):
+    """The Bryan moist bubble (Sec. 5) run to 1000 s at 100 m on the GPU, FP64 and FP32, with
+    the CFL time step: the largest equivalent-potential-temperature anomaly (against the
+    initial state's edge column, the unperturbed background) and the throughput. The paper
+    reports 4.4 K at 1000 s (Bryan & Fritsch's reference solution: 4.09 K)."""
+    import torch
+    import workloads as W
+    from paper_1901_02955_gb300 import Context
+    torch.cuda.set_device(local)
+    w = W.bryan_moist_bubble()
+    out = {}
+    for dt_name in ("f64", "f32"):
+        ctx = Context(w, dtype=dt_name)
+        ctx.set_state(w.Y)
+        bg = ctx.theta_e()[:, :, :1]
+        t, n = 0.0, 0
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        while t < 1000.0 - 1e-9:
+            dt = min(ctx.compute_dt(), 1000.0 - t)
+            ctx.step(1, dt_fixed=dt)
+            t += dt
+            n += 1
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        te = ctx.theta_e()
+        Y = ctx.get_state()
+        out[dt_name] = {"max_theta_e_anomaly_K": float((te - bg).max()),
+                        "min_theta_e_anomaly_K": float((te - bg).min()),
+                        "max_w_m_s": float((Y[5] / Y[:4].sum(axis=0)).max()),
+                        "steps": n, "wall_s": wall,
+                        "cell_updates_per_s": w.ncells * 3 * n / wall}
+        ctx.close()
+    line = {"metric": "max equivalent potential temperature anomaly at 1000 s", "unit": "K",
+            "value": out["f64"]["max_theta_e_anomaly_K"], "higher_is_better": None,
+            "n_gpus": 1, "vs_baseline": None, "data": "synthetic",
+            "config": {"workload": "bryan_moist_bubble_200x100", "t_end_s": 1000.0,
+                       "paper_value_K": 4.4, "note": "wall clock includes one host "
+                       "round trip per step for the CFL time step", "results": out}}
+    print(json.dumps(line), flush=True)
+
+
 def adjoint_workload(args, local):
     """Forward and discrete-adjoint cost of the 2-D warm bubble at 256 x 256 and of its moist
     variant (cloud forming in the core), 400 steps with a checkpoint every 20 steps or with
@@ -402,6 +445,10 @@ def main():
     if args.workload == "adjoint_256x256":
         if rank == 0:
             adjoint_workload(args, local)
+        return
+    if args.workload == "bryan_1000s":
+        if rank == 0:
+            bryan_workload(args, local)
         return
     if args.workload != WORKLOAD:
         if args.workload.startswith("ensemble_96"):

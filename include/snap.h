@@ -197,6 +197,15 @@ int snap_record(snap_ctx *ctx, int nsteps, int ckpt_every, double dt_fixed);
 int snap_step_adjoint(snap_ctx *ctx, int nsteps, const void *lambda_final, void *lambda_init,
                       int dtype, void *stream);
 
+/* Equivalent potential temperature (App. A, Eq. theta_e) of every cell of one domain's
+ * current state, for a context with one vapour whose first condensate is the cloud (q_t =
+ * vapour + cloud; precipitation excluded), p0 = 1e5 Pa: theta_e = T (p0/p_d)^(R_d q_d / c)
+ * exp(L q_v / (c T)), c = c_pd q_d + c_l q_t. out receives nx*ny*nz doubles in the state's
+ * cell order, in device memory (on_device = 1) or host memory. Evaluated in FP64 whatever the
+ * context's dtype. A diagnostic (the step does not use it); synchronous. SNAP_ENOTSUP for
+ * other species tables. */
+int snap_theta_e(snap_ctx *ctx, int domain, double *out, int on_device);
+
 /* Order all following work of the context on this cudaStream_t. NULL selects the CUDA legacy
  * default stream (the handle of torch's default stream); a new context starts on a
  * non-blocking stream of its own. */

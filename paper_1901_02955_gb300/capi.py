@@ -28,7 +28,7 @@ EXPORTS = ["snap_init_grid", "snap_set_state", "snap_get_state", "snap_step", "s
            "snap_compute_dt", "snap_saturation_adjust", "snap_record", "snap_step_adjoint",
            "snap_set_stream",
            "snap_use_graph", "snap_set_tile_variant", "snap_use_persistent", "snap_autotune",
-           "snap_get_info", "snap_buffer_pointer", "snap_budget_noalloc",
+           "snap_get_info", "snap_buffer_pointer", "snap_budget_noalloc", "snap_theta_e",
            "snap_free", "snap_last_error", "snap_status_string"]
 
 
@@ -111,6 +111,7 @@ def load(path: Optional[str] = None) -> C.CDLL:
     lib.snap_budget_noalloc.argtypes = [P, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                                         C.c_int, C.c_double, C.c_double, C.c_double,
                                         C.c_double, P, P]
+    lib.snap_theta_e.argtypes = [P, C.c_int, C.POINTER(C.c_double), C.c_int]
     lib.snap_free.argtypes = [P]
     lib.snap_free.restype = None
     lib.snap_last_error.argtypes = [P]
@@ -240,6 +241,15 @@ class Context:
         n = b.nfields
         return {"total": np.array(b.total[:n]), "energy_with_potential": b.energy_with_potential,
                 "dt_last": b.dt_last, "flags": b.flags, "satadj_max_sweeps": b.satadj_max_sweeps}
+
+    def theta_e(self, domain=0):
+        """Equivalent potential temperature of every cell (snap_theta_e), FP64 numpy array
+        shaped (nz, ny, nx)."""
+        w = self.workloads[domain]
+        out = np.empty((w.nz, w.ny, w.nx), dtype=np.float64)
+        self._check(self.lib.snap_theta_e(self._ptr, domain,
+                                          out.ctypes.data_as(C.POINTER(C.c_double)), 0))
+        return out
 
     def compute_dt(self, domain=0):
         dt = C.c_double(0.0)

@@ -995,6 +995,26 @@ extern "C" int snap_step_adjoint(snap_ctx *ctx, int nsteps, const void *lambda_f
   return rc;
 }
 
+extern "C" int snap_theta_e(snap_ctx *ctx, int domain, double *out, int on_device) {
+  if (!ctx) return fail(nullptr, SNAP_EINVAL, "snap_theta_e: NULL context");
+  if (domain < 0 || domain >= ctx->ndom || !out) return fail(ctx, SNAP_EINVAL, "snap_theta_e: bad arguments");
+  if (ctx->nvap != 1 || ctx->ncond < 1)
+    return fail(ctx, SNAP_ENOTSUP, "snap_theta_e: defined for one vapour with a cloud");
+  const DomDev &D = ctx->dom[domain];
+  double *dst = out;
+  if (!on_device) {
+    CK(cudaMalloc(&dst, sizeof(double) * D.ncell));
+  }
+  cudaError_t e = launch_theta_e(ctx->doms_dev, domain, D.ncell, ctx->ph, ctx->f32, ctx->nv,
+                                 ctx->three_d ? 3 : 2, dst, ctx->stream);
+  if (e == cudaSuccess && !on_device)
+    e = cudaMemcpyAsync(out, dst, sizeof(double) * D.ncell, cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (!on_device) cudaFree(dst);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "snap_theta_e");
+  return SNAP_OK;
+}
+
 extern "C" int snap_set_stream(snap_ctx *ctx, void *stream) {
   if (!ctx) return fail(nullptr, SNAP_EINVAL, "snap_set_stream: NULL context");
   ctx->stream = (cudaStream_t)stream;  // NULL: the legacy default stream

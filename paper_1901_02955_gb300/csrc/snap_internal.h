@@ -149,6 +149,10 @@ struct AdjKernels {
   cudaError_t (*satadj)(const AdjArgs &, long long ncell, cudaStream_t);
 };
 
+// Equivalent potential temperature of one domain's state (diag.cu), FP64 into out[ncell].
+cudaError_t launch_theta_e(const DomDev *doms_dev, int dm, long long ncell, const Phys &ph,
+                           int f32, int nv, int nmom, double *out, cudaStream_t s);
+
 // Adjoint kernels of the inviscid single-domain layouts; false when not built.
 bool find_adjoint_kernels(int f32, int nvap, int ncond, int three_d, AdjKernels *out);
 
