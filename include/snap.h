@@ -214,8 +214,11 @@ int snap_set_stream(snap_ctx *ctx, void *stream);
 /* 1 (default): snap_step replays one captured CUDA graph per step; 0: plain launches. */
 int snap_use_graph(snap_ctx *ctx, int enable);
 
-/* Select one of the tile shapes built for the context's layout (0 is the default; count in
- * snap_info.n_tile_variants). Domains are re-tiled; results do not depend on the shape. */
+/* Select one of the tile shapes built for the context's layout (count in
+ * snap_info.n_tile_variants; the active one in snap_info.tile_variant). A new context starts
+ * on the first shape, in the order built, whose tiles over all domains are at least the
+ * device's SM count, else on the shape with the most tiles, so that a small grid still
+ * spreads over every SM. Domains are re-tiled; results do not depend on the shape. */
 int snap_set_tile_variant(snap_ctx *ctx, int variant);
 
 /* 1: each step is one persistent cooperative launch whose CTAs (all co-resident) walk the tile

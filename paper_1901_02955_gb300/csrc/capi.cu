@@ -357,6 +357,32 @@ static int refresh_rate(snap_ctx *ctx, int dm, cudaStream_t s) {
   return SNAP_OK;
 }
 
+static int apply_variant(snap_ctx *ctx, int v);
+
+// Default tile shape: the first variant (in the order built, the fastest on large grids) whose
+// tiles over all domains fill every SM at least once; else the one with the most tiles.
+static int default_variant(const snap_ctx *ctx) {
+  int dev = 0, nsm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return 0;
+  int best = 0;
+  long long best_tiles = -1;
+  for (int v = 0; v < ctx->ks.nvariants; ++v) {
+    const int *tl = ctx->ks.var[v].tile;
+    long long t = 0;
+    for (const DomDev &D : ctx->dom)
+      t += (long long)((D.nx + tl[0] - 1) / tl[0]) * ((D.ny + tl[1] - 1) / tl[1]) *
+           ((D.nz + tl[2] - 1) / tl[2]);
+    if (t >= nsm) return v;
+    if (t > best_tiles) {
+      best_tiles = t;
+      best = v;
+    }
+  }
+  return best;
+}
+
 extern "C" int snap_init_grid(snap_ctx **out, const snap_grid_desc *d, int n_domains) {
   snap_ctx *ctx = nullptr;
   if (!out || !d || n_domains < 1) return fail(nullptr, SNAP_EINVAL, "snap_init_grid: bad arguments");
@@ -523,6 +549,14 @@ extern "C" int snap_init_grid(snap_ctx **out, const snap_grid_desc *d, int n_dom
   {
     int mrb = ctx->ks.var[0].max_resident_blocks();
     ctx->grid_persistent = mrb < ctx->ntiles ? mrb : ctx->ntiles;
+  }
+  if (const int v = default_variant(ctx)) {
+    if ((ret = apply_variant(ctx, v)) != SNAP_OK) {
+      g_init_error = "snap_init_grid: " + ctx->err;
+      release(ctx);
+      delete ctx;
+      return ret;
+    }
   }
   *out = ctx;
   return SNAP_OK;

@@ -65,6 +65,39 @@ def test_persistent_step_on_3d_and_dry_layouts():
             assert all(np.array_equal(a, b) for a, b in zip(out, ref)), v
 
 
+def test_dry_fp64_tile_variants_agree_bitwise():
+    """The FP64 dry x-z family has two tile shapes (32 x 28 and 32 x 14): both, in both launch
+    modes, on a grid that leaves ragged tiles in x and z."""
+    ws = [W.add_random_motion(W.density_current(nx=70, nz=37, dtype="f64"))]
+    ref, info = run(ws, "f64")
+    assert info["n_tile_variants"] == 2
+    for v in range(2):
+        for persistent in (False, True):
+            out, _ = run(ws, "f64", v, persistent)
+            assert np.array_equal(out[0], ref[0]), (v, persistent)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+@pytest.mark.parametrize("n", [(1024, 256), (256, 256), (40, 40)])
+def test_default_tile_fills_the_sms(dtype, n):
+    """A new context starts on the first tile shape whose tiles cover every SM at least once,
+    else on the shape with the most tiles."""
+    import torch
+    from paper_1901_02955_gb300 import Context
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    w = W.density_current(nx=n[0], nz=n[1], dtype=dtype)
+    ctx = Context(w, dtype=dtype)
+    chosen = ctx.info()["tile_variant"]
+    tiles = []
+    for v in range(ctx.info()["n_tile_variants"]):
+        ctx.set_tile_variant(v)
+        tiles.append(ctx.info()["tiles_total"])
+    ctx.close()
+    full = [v for v, t in enumerate(tiles) if t >= nsm]
+    expect = full[0] if full else int(np.argmax(tiles))
+    assert chosen == expect, (tiles, chosen)
+
+
 def test_autotune_keeps_state_and_picks_a_mode():
     from paper_1901_02955_gb300 import Context
     ws = members()
