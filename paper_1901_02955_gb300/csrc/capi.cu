@@ -105,6 +105,8 @@ struct snap_ctx {
   void *lam = nullptr;        // four adjoint vectors
   void *gface = nullptr;      // per-direction face contributions
   size_t gface_off[3] = {0, 0, 0};
+  void *adjw = nullptr;       // FP64 adjoint: primitives and per-direction window results
+  size_t adjw_off[4] = {0, 0, 0, 0};
   // device memory
   void *arena = nullptr;
   DomDev *doms_dev = nullptr;
@@ -162,6 +164,7 @@ static void release(snap_ctx *ctx) {
   cudaFree(ctx->dt_hist);
   cudaFree(ctx->lam);
   cudaFree(ctx->gface);
+  cudaFree(ctx->adjw);
   cudaFree(ctx->prof_dev);
   cudaFree(ctx->proff_dev);
   cudaFree(ctx->rate_dev);
@@ -873,6 +876,19 @@ extern "C" int snap_record(snap_ctx *ctx, int nsteps, int ckpt_every, double dt_
     }
     CK(cudaMalloc(&ctx->gface, off));
   }
+  if (!ctx->adjw && !ctx->f32) {
+    // primitives [nv][ncell], then per direction 12 nv values per window centre (the cells
+    // -1 .. n_d along the direction)
+    const DomDev &D = ctx->dom[0];
+    size_t off = (size_t)D.ncell * ctx->nv * 8;
+    for (int d = 0; d < 3; ++d) {
+      ctx->adjw_off[d + 1] = off;
+      if (d == 1 && !ctx->three_d) continue;
+      const long long nc = (long long)(D.nx + 2 * (d == 0)) * (D.ny + 2 * (d == 1)) * (D.nz + 2 * (d == 2));
+      off += (size_t)nc * 12 * ctx->nv * 8;
+    }
+    CK(cudaMalloc(&ctx->adjw, off));
+  }
   ctx->rec_dt.assign(nsteps, 0.0);
   ctx->ckpt_every = ckpt_every;
   const int keep = ctx->use_graph;
@@ -933,6 +949,13 @@ static int adjoint_stage(snap_ctx *ctx, const StageArgs &sa, const void *Ys, con
   A.cf = sa.cf;
   A.cd = sa.cd;
   const DomDev &D = ctx->dom[0];
+  A.nx = D.nx;
+  A.ny = D.ny;
+  A.nz = D.nz;
+  if (ctx->adjw) {
+    A.X = ctx->adjw;
+    for (int d = 0; d < 3; ++d) A.W[d] = (char *)ctx->adjw + ctx->adjw_off[d + 1];
+  }
   long long ntot = 0;
   for (int d = 0; d < 3; ++d) {
     A.G[d] = (char *)ctx->gface + ctx->gface_off[d];

@@ -9,10 +9,14 @@
 // Per stage, deterministic (no atomics):
 //   adj_satadj_kernel (moist layouts): one thread per cell maps the adjoint of the adjusted
 //     state to that of the state before the adjustment (temperature inversion in FP64);
-//   adj_face_kernel (one launch for the faces of every direction): one thread per face
+//   adj_face_kernel (FP32; one launch for the faces of every direction): one thread per face
 //     recomputes the face states from its six-cell stencil, transposes LMARS and WENO5, and
 //     writes the contribution of the face to each of its six stencil cells into
 //     G[d][face][s][v] (v padded to a 16-byte vector, so that each slot moves as one access);
+//   FP64 instead: adj_prim_kernel (primitives of every cell once), adj_weno_kernel (every
+//     five-cell window once: both face states it yields and their gradients, sharing the
+//     smoothness indicators) and adj_face_w_kernel (LMARS transposed from the stored states,
+//     the same G) -- about a third less work on the slow FP64 pipe;
 //   adj_cell_kernel: one thread per cell gathers the contributions of every face whose
 //     stencil holds the cell (or a ghost image of it), transposes the primitive map and the
 //     gravity source, and forms the stage combine.
@@ -173,6 +177,81 @@ __device__ __forceinline__ float2 weno5_grad2(const float2 q[5], float eps, floa
          __ffma2_rn(cb[1], db[1][3], __fmul2_rn(cb[2], db[2][3]))));
   g[4] = __ffma2_rn(w[2], f2c(-1.0f / 6.0f), __fmul2_rn(cb[2], db[2][4]));
   return I;
+}
+
+// Both WENO5 states that the five-cell window q[0..4] (cells c-2 .. c+2 along a direction)
+// produces, with their gradients (FP64 adjoint): QL, the left state of face c+1/2 (the window
+// in order), and QR, the right state of face c-1/2 (the window reversed). gL[t] = dQL/dq[t]
+// and gR[t] = dQR/dq[4-t], the gradient in the reversed window's own order as weno5_grad
+// returns it. The mirrored window visits the same three sub-stencils in reverse order, so the
+// smoothness indicators and their derivatives are formed once; the linear weights swap ends
+// (0.3, 0.6, 0.1 over the sub-stencils in the window's order). The normalised Jiang-Shu
+// weights of both states, and 1/(eps + beta_k) in the indicator terms of the gradients, come
+// from one reciprocal through a common denominator: with e_k = eps + beta_k, m_k the product
+// of the other two e and P = e0 e1 e2, alpha_k = d_k m_k^2 / P^2 and 1/e_k = m_k / P.
+template <class R>
+__device__ __forceinline__ void weno5_pair_grad(const R q[5], R eps, R &QL, R &QR, R gL[5],
+                                                R gR[5]) {
+  // sub-stencils A = (q0, q1, q2), B = (q1, q2, q3), C = (q2, q3, q4)
+  const R tA = q[0] - R(2) * q[1] + q[2], sA = q[0] - R(4) * q[1] + R(3) * q[2];
+  const R tB = q[1] - R(2) * q[2] + q[3], sB = q[1] - q[3];
+  const R tC = q[2] - R(2) * q[3] + q[4], sC = R(3) * q[2] - R(4) * q[3] + q[4];
+  const R e0 = eps + (R(13.0 / 12.0) * tA * tA + R(0.25) * sA * sA);
+  const R e1 = eps + (R(13.0 / 12.0) * tB * tB + R(0.25) * sB * sB);
+  const R e2 = eps + (R(13.0 / 12.0) * tC * tC + R(0.25) * sC * sC);
+  // d beta / d q over each sub-stencil's own three cells
+  const R dA0 = R(13.0 / 6.0) * tA + R(0.5) * sA, dA1 = R(-13.0 / 3.0) * tA - R(2) * sA;
+  const R dA2 = R(13.0 / 6.0) * tA + R(1.5) * sA;
+  const R dB1 = R(13.0 / 6.0) * tB + R(0.5) * sB, dB2 = R(-13.0 / 3.0) * tB;
+  const R dB3 = R(13.0 / 6.0) * tB - R(0.5) * sB;
+  const R dC2 = R(13.0 / 6.0) * tC + R(1.5) * sC, dC3 = R(-13.0 / 3.0) * tC - R(2) * sC;
+  const R dC4 = R(13.0 / 6.0) * tC + R(0.5) * sC;
+  const R m0 = e1 * e2, m1 = e0 * e2, m2 = e0 * e1, P = e0 * m0;
+  const R s0 = m0 * m0, s1 = m1 * m1, s2 = m2 * m2;
+  const R nL0 = R(0.1) * s0, nL1 = R(0.6) * s1, nL2 = R(0.3) * s2;
+  const R nR0 = R(0.3) * s0, nR1 = R(0.6) * s1, nR2 = R(0.1) * s2;
+  const R AL = nL0 + nL1 + nL2, AR = nR0 + nR1 + nR2;
+  R iAL, iAR, iP;
+  const R Z = R(1) / (AL * AR * P);
+  if (Z > R(0) && Z < R(INFINITY)) {
+    iAL = AR * P * Z;
+    iAR = AL * P * Z;
+    iP = AL * AR * Z;
+  } else {  // the triple product left the exponent range (a tiny eps): one division each
+    iAL = R(1) / AL;
+    iAR = R(1) / AR;
+    iP = R(1) / P;
+  }
+  const R wL0 = nL0 * iAL, wL1 = nL1 * iAL, wL2 = nL2 * iAL;
+  const R wR0 = nR0 * iAR, wR1 = nR1 * iAR, wR2 = nR2 * iAR;
+  // candidates: the left state's on A, B, C and the right state's on the same sub-stencils
+  const R vL0 = q[0] * R(1.0 / 3.0) - R(7.0 / 6.0) * q[1] + R(11.0 / 6.0) * q[2];
+  const R vL1 = -q[1] * R(1.0 / 6.0) + R(5.0 / 6.0) * q[2] + q[3] * R(1.0 / 3.0);
+  const R vL2 = q[2] * R(1.0 / 3.0) + R(5.0 / 6.0) * q[3] - q[4] * R(1.0 / 6.0);
+  const R vR0 = q[2] * R(1.0 / 3.0) + R(5.0 / 6.0) * q[1] - q[0] * R(1.0 / 6.0);
+  const R vR1 = -q[3] * R(1.0 / 6.0) + R(5.0 / 6.0) * q[2] + q[1] * R(1.0 / 3.0);
+  const R vR2 = q[4] * R(1.0 / 3.0) - R(7.0 / 6.0) * q[3] + R(11.0 / 6.0) * q[2];
+  QL = wL0 * vL0 + wL1 * vL1 + wL2 * vL2;
+  QR = wR0 * vR0 + wR1 * vR1 + wR2 * vR2;
+  // indicator terms: (v_k - Q) dw_k/dbeta_k = -2 (v_k - Q) w_k / e_k
+  const R m2iP = R(-2) * iP;
+  const R cL0 = (vL0 - QL) * wL0 * m0 * m2iP, cL1 = (vL1 - QL) * wL1 * m1 * m2iP;
+  const R cL2 = (vL2 - QL) * wL2 * m2 * m2iP;
+  const R cR0 = (vR0 - QR) * wR0 * m0 * m2iP, cR1 = (vR1 - QR) * wR1 * m1 * m2iP;
+  const R cR2 = (vR2 - QR) * wR2 * m2 * m2iP;
+  gL[0] = wL0 * R(1.0 / 3.0) + cL0 * dA0;
+  gL[1] = wL0 * R(-7.0 / 6.0) + wL1 * R(-1.0 / 6.0) + cL0 * dA1 + cL1 * dB1;
+  gL[2] = wL0 * R(11.0 / 6.0) + wL1 * R(5.0 / 6.0) + wL2 * R(1.0 / 3.0) + cL0 * dA2 +
+          cL1 * dB2 + cL2 * dC2;
+  gL[3] = wL1 * R(1.0 / 3.0) + wL2 * R(5.0 / 6.0) + cL1 * dB3 + cL2 * dC3;
+  gL[4] = wL2 * R(-1.0 / 6.0) + cL2 * dC4;
+  // dQR/dq[t], stored at gR[4 - t]
+  gR[4] = wR0 * R(-1.0 / 6.0) + cR0 * dA0;
+  gR[3] = wR0 * R(5.0 / 6.0) + wR1 * R(1.0 / 3.0) + cR0 * dA1 + cR1 * dB1;
+  gR[2] = wR0 * R(1.0 / 3.0) + wR1 * R(5.0 / 6.0) + wR2 * R(11.0 / 6.0) + cR0 * dA2 +
+          cR1 * dB2 + cR2 * dC2;
+  gR[1] = wR1 * R(-1.0 / 6.0) + wR2 * R(-7.0 / 6.0) + cR1 * dB3 + cR2 * dC3;
+  gR[0] = wR2 * R(1.0 / 3.0) + cR2 * dC4;
 }
 
 // Transpose of mix_factors<>: adds the adjoint of (num, den) to the tracer entries of Xb.
@@ -451,6 +530,191 @@ __global__ void __launch_bounds__(128) adj_face_kernel(const AdjArgs a) {
   }
 }
 
+// ---- FP64 path: window-centred WENO transpose ------------------------------------------
+// On the FP64 pipe the face kernel above is bound by arithmetic, most of it the two WENO5
+// gradients of each face, whose windows (centred on the two cells beside the face) are each
+// evaluated twice over the grid, and six primitive conversions per face. The FP64 adjoint
+// splits the work: adj_prim_kernel converts every cell once; adj_weno_kernel evaluates every
+// window once (both of its states, weno5_pair_grad); adj_face_w_kernel transposes LMARS at
+// each face from the stored states and writes the same G as adj_face_kernel.
+
+// Window centres of direction DIR: the cells -1 .. n_d along DIR (a ghost centre at each end
+// holds the window of a boundary face's outer state), all cells across.
+template <int DIR>
+__device__ __forceinline__ long long n_centres(const DomDev &D) {
+  return (long long)(D.nx + 2 * (DIR == 0)) * (D.ny + 2 * (DIR == 1)) * (D.nz + 2 * (DIR == 2));
+}
+
+template <class R, class L>
+__global__ void __launch_bounds__(128) adj_prim_kernel(const AdjArgs a) {
+  constexpr int NV = L::NV;
+  const DomDev &D = a.doms[0];
+  const CstT<R> &C = acst<R>(a);
+  const long long ncell = D.ncell, plane = (long long)D.nx * D.ny;
+  const R *Ys = reinterpret_cast<const R *>(a.Ys);
+  R *X = reinterpret_cast<R *>(a.X);
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell;
+       c += (long long)gridDim.x * blockDim.x) {
+    R y[NV], x[NV], pt, Tt;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) y[v] = Ys[v * ncell + c];
+    cons_to_prim<R, L>(a.ph, C, D, int(c / plane), y, x, pt, Tt);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) X[v * ncell + c] = x[v];
+  }
+}
+
+// Window centre e of direction DIR: reads the primitives of cells pos-2 .. pos+2 (ghosts
+// mirrored, the normal velocity negated, or wrapped) and writes, per field v, at W[q][e]:
+// q = v the left state of face pos+1/2, NV + v the right state of face pos-1/2, 2 NV + t NV + v
+// the left state's gradient gL[t], 7 NV + t NV + v the right state's gR[t].
+template <class R, class L, int DIR>
+__device__ __forceinline__ void adj_window(const AdjArgs &a, const DomDev &D, long long e) {
+  constexpr int NV = L::NV, MN = L::mom(DIR);
+  constexpr int fx = DIR == 0, fy = DIR == 1, fz = DIR == 2;
+  const int nx = D.nx, ny = D.ny;
+  const int ex = nx + 2 * fx, ey = ny + 2 * fy;
+  const int i = int(e % ex), j = int((e / ex) % ey), k = int(e / ((long long)ex * ey));
+  const int pos = (DIR == 0 ? i : (DIR == 1 ? j : k)) - 1;
+  const int nd = DIR == 0 ? nx : (DIR == 1 ? ny : D.nz);
+  const int bclo = D.bc[2 * DIR], bchi = D.bc[2 * DIR + 1];
+  const long long ncell = D.ncell, nc = n_centres<DIR>(D);
+  const R *X = reinterpret_cast<const R *>(a.X);
+  R *W = reinterpret_cast<R *>(a.W[DIR]);
+  long long cs[5];
+  bool fl[5];
+#pragma unroll
+  for (int t = 0; t < 5; ++t) {
+    const int p = map_index(pos - 2 + t, nd, bclo, bchi, fl[t]);
+    const int ci = fx ? p : i, cj = fy ? p : j, ck = fz ? p : k;
+    cs[t] = ((long long)ck * ny + cj) * nx + ci;
+  }
+  const R weps = acst<R>(a).weno_eps;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    R q[5], QL, QR, gL[5], gR[5];
+#pragma unroll
+    for (int t = 0; t < 5; ++t) {
+      const R x = X[v * ncell + cs[t]];
+      q[t] = (v == MN && fl[t]) ? -x : x;
+    }
+    weno5_pair_grad<R>(q, weps, QL, QR, gL, gR);
+    W[v * nc + e] = QL;
+    W[(NV + v) * nc + e] = QR;
+#pragma unroll
+    for (int t = 0; t < 5; ++t) {
+      W[(2 * NV + t * NV + v) * nc + e] = gL[t];
+      W[(7 * NV + t * NV + v) * nc + e] = gR[t];
+    }
+  }
+}
+
+template <class R, class L>
+__global__ void __launch_bounds__(128) adj_weno_kernel(const AdjArgs a) {
+  const DomDev &D = a.doms[0];
+  const long long n0 = n_centres<0>(D), n1 = L::D3 ? n_centres<1>(D) : 0ll;
+  const long long ntot = n0 + n1 + n_centres<2>(D);
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < ntot;
+       e += (long long)gridDim.x * blockDim.x) {
+    if (e < n0) {
+      adj_window<R, L, 0>(a, D, e);
+    } else if (L::D3 && e < n0 + n1) {
+      if constexpr (L::D3) adj_window<R, L, 1>(a, D, e - n0);
+    } else {
+      adj_window<R, L, 2>(a, D, e - n0 - n1);
+    }
+  }
+}
+
+// Face f of direction DIR from the stored window results: the left state comes from the
+// window centred on cell pos-1, the right state from the one centred on cell pos.
+template <class R, class L, int DIR>
+__device__ __forceinline__ void adj_face_w(const AdjArgs &a, const DomDev &D, const CstT<R> &C,
+                                           long long f) {
+  constexpr int NV = L::NV;
+  constexpr int fx = DIR == 0, fy = DIR == 1, fz = DIR == 2;
+  const int nx = D.nx, ny = D.ny, nz = D.nz;
+  const long long ncell = D.ncell, nc = n_centres<DIR>(D);
+  const int nfx = nx + fx, nfy = ny + fy;
+  const R *lo = reinterpret_cast<const R *>(a.lam_out);
+  const R *Wd = reinterpret_cast<const R *>(a.W[DIR]);
+  R *G = reinterpret_cast<R *>(a.G[DIR]);
+  const R bdt = R(a.b * a.dt), ih = Prof<R>::ih(D, DIR);
+  const int nd = DIR == 0 ? nx : (DIR == 1 ? ny : nz);
+  const int i = int(f % nfx), j = int((f / nfx) % nfy), k = int(f / ((long long)nfx * nfy));
+  const int pos = DIR == 0 ? i : (DIR == 1 ? j : k);
+  R Fb[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) Fb[v] = R(0);
+  R Fbz = R(0);
+  if (pos > 0) {
+    const long long c = ((long long)(k - fz) * ny + (j - fy)) * nx + (i - fx);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) Fb[v] -= bdt * lo[v * ncell + c] * ih;
+    if (fz) Fbz -= R(0.5) * Prof<R>::grav(D) * bdt * lo[L::IE * ncell + c];
+  }
+  if (pos < nd) {
+    const long long c = ((long long)k * ny + j) * nx + i;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) Fb[v] += bdt * lo[v * ncell + c] * ih;
+    if (fz) Fbz -= R(0.5) * Prof<R>::grav(D) * bdt * lo[L::IE * ncell + c];
+  }
+  if (fz) {
+#pragma unroll
+    for (int s = 0; s < L::IM0; ++s) Fb[s] += Fbz;
+  }
+  // centre index of the window on cell pos-1; the one on cell pos is a stride further
+  const int ex = nx + 2 * fx, ey = ny + 2 * fy;
+  const long long eL = ((long long)k * ey + j) * ex + i;
+  const long long eR = eL + (DIR == 0 ? 1ll : (DIR == 1 ? (long long)ex : (long long)ex * ey));
+  R QL[NV], QR[NV], QLb[NV], QRb[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    QL[v] = Wd[v * nc + eL];
+    QR[v] = Wd[(NV + v) * nc + eR];
+    QLb[v] = QRb[v] = R(0);
+  }
+  const R pref = fz ? Prof<R>::pf(D, k) : Prof<R>::pc(D, k);
+  lmars_adj<R, L>(C, QL, QR, DIR, pref, Fb, QLb, QRb);
+  constexpr int NVP = g_stride<R, NV>(), W = GVec<R>::W;
+  using Vec = typename GVec<R>::V;
+  Vec *Gf = reinterpret_cast<Vec *>(G + f * 6 * NVP);
+#pragma unroll
+  for (int s = 0; s < 6; ++s) {
+    R g[NVP];
+#pragma unroll
+    for (int v = 0; v < NVP; ++v) {
+      g[v] = R(0);
+      if (v < NV) {
+        if (s <= 4) g[v] += QLb[v] * Wd[(2 * NV + s * NV + v) * nc + eL];
+        if (s >= 1) g[v] += QRb[v] * Wd[(7 * NV + (5 - s) * NV + v) * nc + eR];
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < NVP / W; ++c) Gf[s * (NVP / W) + c] = GVec<R>::make(g + c * W);
+  }
+}
+
+template <class R, class L>
+__global__ void __launch_bounds__(128) adj_face_w_kernel(const AdjArgs a) {
+  const DomDev &D = a.doms[0];
+  const CstT<R> &C = acst<R>(a);
+  const int nx = D.nx, ny = D.ny, nz = D.nz;
+  const long long n0 = (long long)(nx + 1) * ny * nz;
+  const long long n1 = L::D3 ? (long long)nx * (ny + 1) * nz : 0ll;
+  const long long ntot = n0 + n1 + (long long)nx * ny * (nz + 1);
+  for (long long gf = blockIdx.x * (long long)blockDim.x + threadIdx.x; gf < ntot;
+       gf += (long long)gridDim.x * blockDim.x) {
+    if (gf < n0) {
+      adj_face_w<R, L, 0>(a, D, C, gf);
+    } else if (L::D3 && gf < n0 + n1) {
+      if constexpr (L::D3) adj_face_w<R, L, 1>(a, D, C, gf - n0);
+    } else {
+      adj_face_w<R, L, 2>(a, D, C, gf - n0 - n1);
+    }
+  }
+}
+
 // Adds to Xb the contributions of the faces of direction DIR whose stencil slot holds the
 // position ipos along DIR (the cell itself or a ghost image of it), with the normal velocity
 // entry multiplied by sg (-1 for a mirror image).
@@ -689,9 +953,24 @@ __global__ void __launch_bounds__(128) adj_satadj_kernel(const AdjArgs a) {
 
 template <class R, class L>
 struct AdjFamily {
+  // FP32: one face launch (latency-bound at the sizes an adjoint runs); FP64: primitives,
+  // windows, then faces (see adj_weno_kernel)
   static cudaError_t face(const AdjArgs &a, long long nfaces, cudaStream_t s) {
-    long long g = (nfaces + 127) / 128;
-    adj_face_kernel<R, L><<<int(g < 9728 ? g : 9728), 128, 0, s>>>(a);
+    if constexpr (sizeof(R) == 8) {
+      const long long ncell = (long long)a.nx * a.ny * a.nz;
+      const long long ncent = (long long)(a.nx + 2) * a.ny * a.nz +
+                              (L::D3 ? (long long)a.nx * (a.ny + 2) * a.nz : 0ll) +
+                              (long long)a.nx * a.ny * (a.nz + 2);
+      long long g = (ncell + 127) / 128;
+      adj_prim_kernel<R, L><<<int(g < 9728 ? g : 9728), 128, 0, s>>>(a);
+      g = (ncent + 127) / 128;
+      adj_weno_kernel<R, L><<<int(g < 9728 ? g : 9728), 128, 0, s>>>(a);
+      g = (nfaces + 127) / 128;
+      adj_face_w_kernel<R, L><<<int(g < 9728 ? g : 9728), 128, 0, s>>>(a);
+    } else {
+      long long g = (nfaces + 127) / 128;
+      adj_face_kernel<R, L><<<int(g < 9728 ? g : 9728), 128, 0, s>>>(a);
+    }
     return cudaGetLastError();
   }
   static cudaError_t cell(const AdjArgs &a, long long ncell, cudaStream_t s) {

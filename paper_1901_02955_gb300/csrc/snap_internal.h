@@ -135,6 +135,11 @@ struct AdjArgs {
   double a, b, dt;       // stage output = a Y^n + b (Y_s + dt L(Y_s))
   int mode;              // 2: lam_n = a lam_out; 1: lam_n += a lam_out; 0: lam_s = lam_n + ...
   void *G[3];            // per-direction face contributions [nfaces_d][6][nv padded to 16 B]
+  // FP64 adjoint only: primitives of every cell of Ys [nv][ncell], and per direction the face
+  // states and WENO gradients of every window centre [12 nv][ncentres_d] (see adj_weno_kernel)
+  void *X;
+  void *W[3];
+  int nx, ny, nz;        // domain size (host copy, for the launch shapes)
   Phys ph;
   CstT<float> cf;
   CstT<double> cd;
