@@ -20,7 +20,7 @@ constexpr int kThreads = 256;
 constexpr int kMaxBlocks = 1024;                    // partial rows
 constexpr int kMaxOut = SNAP_MAX_FIELDS + 1;        // field totals + energy with potential
 // 1024 x 25 doubles = 200 KiB, held by every device that loads this library until exit.
-__device__ __align__(256) double g_budget_scratch[kMaxBlocks * kMaxOut];
+static __device__ __align__(256) double g_budget_scratch[kMaxBlocks * kMaxOut];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mutex;
