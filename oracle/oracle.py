@@ -58,6 +58,7 @@ class _Grid(C.Structure):
         ("kessler_max_iter", C.c_int), ("kessler_tol", C.c_double),
         ("cool_rate", C.c_double), ("cool_p_lo", C.c_double), ("cool_p_hi", C.c_double),
         ("sponge_tau0", C.c_double), ("sponge_p0", C.c_double),
+        ("T_bottom", C.c_double),
     ]
 
 
@@ -150,6 +151,7 @@ def grid_from_workload(w, satadj: Optional[bool] = None, nu: Optional[float] = N
     sponge = tuple(getattr(w, "sponge", ()))  # (tau0 s, p0 Pa)
     if sponge:
         g.sponge_tau0, g.sponge_p0 = sponge
+    g.T_bottom = float(getattr(w, "T_bottom", 0.0))
     return g, keep
 
 

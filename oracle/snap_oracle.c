@@ -537,7 +537,15 @@ int orc_satadj_bisect(const orc_grid *g, double *Y) {
  *    values, the momentum flux -rho_f nu du/dn and the energy flux
  *    -rho_f nu u_f . du/dn - rho_f c_pd nu Pi_f dtheta/dn, where theta = T / Pi and
  *    Pi = (p / 1e5 Pa)^(R_d/c_pd) (App. C, Eq. theta, dry); the subscript f is the mean of
- *    the two cells. Ghost cells mirror theta, so no heat crosses a reflecting wall.
+ *    the two cells. Ghost cells mirror theta, so no heat crosses a wall, except below a
+ *    fixed bottom temperature (Sec. 6), whose ghosts hold theta = T_bottom / Pi; a no-slip
+ *    wall's ghosts carry the reversed tangential velocity, so the wall exerts a stress.
+ *  - Lower boundary of the Jovian simulation (Sec. 6; READING): a no-slip wall and a fixed
+ *    temperature are set in the ghost cells below z = 0, which mirror pressure, composition
+ *    and (negated) velocity and hold T_bottom, their density scaled by T / T_bottom at that
+ *    pressure. The mirrored pressure and normal velocity keep u* = 0 at the wall, so no mass
+ *    or energy is advected through it; in an inviscid run the fixed temperature only enters
+ *    the reconstruction next to the wall, with viscosity it drives the heat flux above.
  * ------------------------------------------------------------------------------------- */
 typedef struct {
   int nxe, nye, nze, ox, oy, oz;
@@ -566,19 +574,30 @@ static double pbar_cell(const orc_grid *g, int k) {
   return 0.5 * (g->p_bar_face[k] + g->p_bar_face[k + 1]);
 }
 
+/* Velocities of a ghost cell that mirrors a cell across a wall normal to direction d: a
+ * free-slip wall negates the normal velocity only, a no-slip wall every component (Sec. 6,
+ * the no-slip lower boundary of the Jovian simulation). */
+static void wall_ghost(const orc_grid *g, double *X, long next, long dst, int d, int bc) {
+  if (bc == ORC_NOSLIP) {
+    for (int m = 0; m < nmom_of(g); ++m) X[(long)(im0_of(g) + m) * next + dst] *= -1.0;
+  } else {
+    X[(long)mom_slot(g, d) * next + dst] *= -1.0;
+  }
+}
+
 /* Sec. 2, Eq. d3 and the momentum and energy equations with sedimentation: a condensate
  * (i,j) with terminal velocity w^t_j carries through a z face the extra fluxes
  *   mass w^t rho_ij, momentum w^t rho_ij u_m, energy w^t rho_ij e_ij,
  *   e_ij = c_ij T + |u|^2/2 + mu_ij (Sec. 2).
  * READINGS: the face values come from the reconstructed state on the side the condensate
- * comes from (above when w^t < 0); no condensate passes a wall (reflecting boundary), so
+ * comes from (above when w^t < 0); no condensate passes a wall (free-slip or no-slip), so
  * precipitation collects in the lowest layer; the frictional heating -sum rho_ij g w^t of the
  * energy equation is the sedimentation part of -g F_rho in the gravity source of orc_rhs,
  * whose total-mass flux includes these mass fluxes. */
 static void sedimentation_flux(const orc_grid *g, const double *XL, const double *XR,
                                double pref, int k, double *F) {
   const int im0 = im0_of(g), nm = nmom_of(g), nv = orc_nvar(g);
-  if ((k == 0 && g->bc[4] == ORC_REFLECT) || (k == g->nz && g->bc[5] == ORC_REFLECT)) return;
+  if ((k == 0 && g->bc[4] != ORC_PERIODIC) || (k == g->nz && g->bc[5] != ORC_PERIODIC)) return;
   for (int j = 0; j < g->ncond; ++j) {
     const double wt = g->w_term[j];
     if (wt == 0.0) continue;
@@ -601,9 +620,10 @@ int orc_rhs(const orc_grid *g, const double *Y, double *dYdt) {
   const int nx = g->nx, ny = g->ny, nz = g->nz, nv = orc_nvar(g), im0 = im0_of(g);
   const int three_d = ny > 1;
   if (nx < 1 || ny < 1 || nz < 3) return -1;
-  if (g->bc[4] != ORC_REFLECT || g->bc[5] != ORC_REFLECT) return -1;
-  if ((g->bc[0] == ORC_REFLECT || g->bc[1] == ORC_REFLECT) && nx < 3) return -1;
-  if (three_d && (g->bc[2] == ORC_REFLECT || g->bc[3] == ORC_REFLECT) && ny < 3) return -1;
+  if (g->bc[4] == ORC_PERIODIC || g->bc[5] == ORC_PERIODIC) return -1; /* z: walls */
+  if ((g->bc[0] != ORC_PERIODIC || g->bc[1] != ORC_PERIODIC) && nx < 3) return -1;
+  if (three_d && (g->bc[2] != ORC_PERIODIC || g->bc[3] != ORC_PERIODIC) && ny < 3) return -1;
+  if (!(g->T_bottom >= 0.0)) return -1;
   ext_dims e = {nx + 6, three_d ? ny + 6 : 1, nz + 6, 3, three_d ? 3 : 0, 3};
   const long next = (long)e.nxe * e.nye * e.nze;
   const long ncell = (long)nx * ny * nz;
@@ -645,7 +665,7 @@ int orc_rhs(const orc_grid *g, const double *Y, double *dYdt) {
         for (int v = 0; v < nv; ++v) X[v * next + dst] = X[v * next + src];
         Tx[dst] = Tx[src];
         Px[dst] = Px[src];
-        if (flip) X[(long)mom_slot(g, 0) * next + dst] *= -1.0;
+        if (flip) wall_ghost(g, X, next, dst, 0, g->bc[gi < 0 ? 0 : 1]);
       }
   if (three_d)
     for (int k = 0; k < nz; ++k)
@@ -657,7 +677,7 @@ int orc_rhs(const orc_grid *g, const double *Y, double *dYdt) {
           for (int v = 0; v < nv; ++v) X[v * next + dst] = X[v * next + src];
           Tx[dst] = Tx[src];
           Px[dst] = Px[src];
-          if (flip) X[(long)mom_slot(g, 1) * next + dst] *= -1.0;
+          if (flip) wall_ghost(g, X, next, dst, 1, g->bc[gj < 0 ? 2 : 3]);
         }
   for (int gk = -3; gk < nz + 3; ++gk)
     for (int j = 0; j < ny; ++j)
@@ -668,7 +688,14 @@ int orc_rhs(const orc_grid *g, const double *Y, double *dYdt) {
         for (int v = 0; v < nv; ++v) X[v * next + dst] = X[v * next + src];
         Tx[dst] = Tx[src];
         Px[dst] = Px[src];
-        if (flip) X[(long)mom_slot(g, 2) * next + dst] *= -1.0;
+        if (flip) wall_ghost(g, X, next, dst, 2, g->bc[gk < 0 ? 4 : 5]);
+        if (gk < 0 && g->T_bottom > 0.0) {
+          /* Sec. 6 lower boundary: the ghost holds T_bottom at the mirrored pressure and
+           * composition, so its density is the mirrored one times T / T_bottom */
+          const double T = Tx[src] * Px[src];
+          X[dst] *= T / g->T_bottom;
+          Tx[dst] = g->T_bottom / Px[src];
+        }
       }
 
   for (long v = 0; v < nv * ncell; ++v) dYdt[v] = 0.0;
@@ -1114,6 +1141,9 @@ int orc_rhs_adjoint(const orc_grid *g, const double *Y, const double *mu, double
   for (int j = 0; j < g->ncond; ++j)
     if (g->w_term[j] != 0.0) return -3; /* no sedimentation */
   if (g->cool_rate != 0.0 || g->sponge_tau0 > 0.0) return -3; /* no forcing */
+  for (int s = 0; s < 6; ++s)
+    if (g->bc[s] == ORC_NOSLIP) return -3; /* free-slip or periodic sides only */
+  if (g->T_bottom > 0.0) return -3;       /* no fixed bottom temperature */
   if (nx < 1 || ny < 1 || nz < 3) return -1;
   ext_dims e = {nx + 6, three_d ? ny + 6 : 1, nz + 6, 3, three_d ? 3 : 0, 3};
   const long next = (long)e.nxe * e.nye * e.nze;

@@ -28,7 +28,10 @@ extern "C" {
 #define ORC_MAXV 4
 #define ORC_MAXC 2
 
-enum { ORC_REFLECT = 0, ORC_PERIODIC = 1 };
+/* Boundary of one side: a free-slip wall (ghosts mirror the state, normal velocity negated),
+ * periodic, or a no-slip wall (ghosts mirror the state with every velocity component
+ * negated). */
+enum { ORC_REFLECT = 0, ORC_PERIODIC = 1, ORC_NOSLIP = 2 };
 
 typedef struct {
   int nx, ny, nz;               /* ny == 1: x-z plane with no y direction */
@@ -64,6 +67,9 @@ typedef struct {
    * a sponge relaxing the horizontal momenta at 1/(tau0 (p/p0)^2) where p < p0 */
   double cool_rate, cool_p_lo, cool_p_hi;
   double sponge_tau0, sponge_p0;
+  /* Sec. 6 lower boundary: > 0 holds the ghost cells below z = 0 at this temperature (K),
+   * with the pressure, composition and velocities of the cells they mirror (0: off) */
+  double T_bottom;
 } orc_grid;
 
 int orc_nvar(const orc_grid *g);
@@ -124,7 +130,8 @@ void orc_budget(const orc_grid *g, const double *Y, double *out);
 
 /* ---- discrete adjoint (inviscid): transposes of the routines above ---- */
 double orc_weno5_gradient(const double q[5], double eps, double grad[5]);
-/* Ybar = (dL/dY)^T mu at state Y (returns -3 for viscous grids or with sedimentation). */
+/* Ybar = (dL/dY)^T mu at state Y (returns -3 for viscous grids, with sedimentation, forcing,
+ * a no-slip wall or a fixed bottom temperature). */
 int orc_rhs_adjoint(const orc_grid *g, const double *Y, const double *mu, double *Ybar);
 /* lam_in = (dYout/dYin)^T lam_out for the saturation adjustment of one cell, evaluated at its
  * converged result Yout (App. D equilibrium; see the definition for the derivation). */

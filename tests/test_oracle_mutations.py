@@ -14,7 +14,8 @@ SRC = os.path.join(ROOT, "oracle", "snap_oracle.c")
 PINS = ["tests/test_oracle_weno.py", "tests/test_oracle_lmars.py", "tests/test_oracle_thermo.py",
         "tests/test_oracle_satadj.py", "tests/test_oracle_scheme.py",
         "tests/test_oracle_adjoint.py", "tests/test_oracle_kessler.py",
-        "tests/test_oracle_forcing.py", "tests/test_oracle_theta_e.py"]
+        "tests/test_oracle_forcing.py", "tests/test_oracle_theta_e.py",
+        "tests/test_oracle_bottom.py"]
 
 MUTANTS = {
     "weno beta0 curvature coefficient": ("b[0] = 13.0 / 12.0 * t * t;", "b[0] = 13.0 / 6.0 * t * t;"),
@@ -66,6 +67,14 @@ MUTANTS = {
                                                  "              (void)b;"),
     "sponge time linear in pressure": ("const double r = pk / g->sponge_p0, tau = g->sponge_tau0 * r * r;",
                                        "const double r = pk / g->sponge_p0, tau = g->sponge_tau0 * r;"),
+    "no-slip ghost negates the normal velocity only": (
+        "  if (bc == ORC_NOSLIP) {\n    for (int m = 0; m < nmom_of(g); ++m)",
+        "  if (bc == -1) {\n    for (int m = 0; m < nmom_of(g); ++m)"),
+    "bottom ghost density scaled the wrong way": ("X[dst] *= T / g->T_bottom;", "X[dst] *= g->T_bottom / T;"),
+    "bottom ghost keeps the mirrored temperature": ("Tx[dst] = g->T_bottom / Px[src];", "Tx[dst] = Tx[src];"),
+    "sedimentation through the no-slip floor": (
+        "if ((k == 0 && g->bc[4] != ORC_PERIODIC) || (k == g->nz && g->bc[5] != ORC_PERIODIC)) return;",
+        "if ((k == 0 && g->bc[4] == ORC_REFLECT) || (k == g->nz && g->bc[5] == ORC_REFLECT)) return;"),
     "sedimentation energy without kinetic part": ("F[nv - 1] += ms * (g->sig_c[i][j] * c_vd(g) * T + 0.5 * u2 + mu_of(g, i, j));",
                                                   "F[nv - 1] += ms * (g->sig_c[i][j] * c_vd(g) * T + mu_of(g, i, j));"),
 }

@@ -34,8 +34,9 @@ from . import rng
 
 RHAT = 8.3144598  # universal gas constant, J/(mol K) (App. A, symbol table)
 
-REFLECT = 0
+REFLECT = 0   # free-slip wall
 PERIODIC = 1
+NOSLIP = 2    # wall whose ghost cells reverse every velocity component
 
 BASE_SEED = 190102955
 
@@ -65,7 +66,7 @@ class Workload:
     dx: float
     dy: float
     dz: float
-    bc: tuple  # (x-, x+, y-, y+, z-, z+), REFLECT or PERIODIC
+    bc: tuple  # (x-, x+, y-, y+, z-, z+), REFLECT, PERIODIC or NOSLIP
     grav: float
     gamma_d: float
     R_d: float
@@ -93,6 +94,9 @@ class Workload:
     # (tau0 s, p0 Pa) by the reference pressure of each level; empty: off
     cooling: tuple = ()
     sponge: tuple = ()
+    # lower boundary of the Jovian simulation: temperature held by the ghost cells below the
+    # bottom wall, K (0: off)
+    T_bottom: float = 0.0
 
     @property
     def nvapor(self) -> int:
