@@ -40,6 +40,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--workload", default=WORKLOAD,
                    choices=[WORKLOAD, "jovian_256x256x128", "jovian_256x256x128_kessler",
+                            "jovian_rce_256x256x128",
                             "ensemble_96", "ensemble_96_autotuned", "adjoint_256x256",
                             "bryan_1000s"],
                    help="the default is the headline workload; the others print an extra "
@@ -67,6 +68,10 @@ def workload(dtype, name=WORKLOAD):
         import dataclasses
         return [dataclasses.replace(W.jovian(dtype=dtype), kessler_k=(1e9, 1e-4, 0.0, 1e-2),
                                     w_term=(0.0, -20.0))]
+    if name == "jovian_rce_256x256x128":
+        # the radiative-convective setup of Sec. 6: microphysics, falling precipitation,
+        # cooling, sponge, and the no-slip floor at a fixed temperature
+        return [W.jovian_rce(dtype=dtype)]
     if name.startswith("ensemble_96"):
         return W.ensemble()
     return W.density_current(dtype=dtype)

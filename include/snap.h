@@ -41,7 +41,11 @@ typedef enum snap_status {
   SNAP_ENOTSUP = -7     /* combination of options not built into this library */
 } snap_status;
 
-enum { SNAP_REFLECT = 0, SNAP_PERIODIC = 1 };
+/* Boundary of one side of a domain. SNAP_REFLECT: free-slip wall (ghost cells mirror the
+ * state with the normal velocity negated). SNAP_PERIODIC: wrap (both opposite sides).
+ * SNAP_NOSLIP: no-slip wall (ghost cells mirror the state with every velocity component
+ * negated; Sec. 6 puts one at the bottom of the Jovian simulation). */
+enum { SNAP_REFLECT = 0, SNAP_PERIODIC = 1, SNAP_NOSLIP = 2 };
 enum { SNAP_F64 = 0, SNAP_F32 = 1 };
 
 /* One condensable vapour i and its condensates (i,j); j = 0 is the cloud that exchanges mass
@@ -59,8 +63,9 @@ typedef struct snap_species {
 typedef struct snap_grid_desc {
   int nx, ny, nz;          /* cells; ny == 1: x-z plane. Each active extent >= 3 */
   double dx, dy, dz;       /* cell sizes, m (dy ignored when ny == 1) */
-  int bc[6];               /* x-, x+, y-, y+, z-, z+ : SNAP_REFLECT or SNAP_PERIODIC; z must
-                              reflect; a periodic side needs its opposite side periodic */
+  int bc[6];               /* x-, x+, y-, y+, z-, z+ : SNAP_REFLECT, SNAP_PERIODIC or
+                              SNAP_NOSLIP; z must be walls; a periodic side needs its
+                              opposite side periodic */
   double grav;             /* gravitational acceleration, m/s^2 (along -z) */
   double gamma_d;          /* c_p,d / c_v,d of the dry gas */
   double R_d;              /* dry-gas constant, J/(kg K) */
@@ -100,6 +105,12 @@ typedef struct snap_grid_desc {
    * into its moist kernels). */
   double cool_rate, cool_p_lo, cool_p_hi;
   double sponge_tau0, sponge_p0;
+  /* Sec. 6 lower boundary (fixed temperature): > 0 holds the ghost cells below the bottom
+   * wall at T_bottom (K). They keep the mirrored pressure, composition and velocities, so
+   * their densities are the mirrored ones times T / T_bottom. Nothing is advected through
+   * the wall (u* = 0 there); inviscid, the ghosts only enter the reconstruction next to the
+   * wall; with viscosity the wall face carries the heat flux -rho c_p nu dT/dz. 0: off. */
+  double T_bottom;
 } snap_grid_desc;
 
 /* Domain totals: field sums times the cell volume, and sum of (rho e + rho g z) dV. */
@@ -179,7 +190,8 @@ int snap_saturation_adjust(snap_ctx *ctx, int domain);
  *     the adjoint recomputes nothing.
  * Also allocates four adjoint vectors and the per-face work arrays of the adjoint. The
  * adjoint is built for a single inviscid domain, dry (x-z or 3-D) or with one vapour and two
- * condensates in the x-z plane; SNAP_ENOTSUP for any other context. */
+ * condensates in the x-z plane, with free-slip or periodic sides and no fixed bottom
+ * temperature; SNAP_ENOTSUP for any other context. */
 int snap_record(snap_ctx *ctx, int nsteps, int ckpt_every, double dt_fixed);
 
 /* Discrete adjoint of the recorded run: lambda_init = (dY_N / dY_0)^T lambda_final, with

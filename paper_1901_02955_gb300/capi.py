@@ -19,7 +19,7 @@ MAX_COND = 2
 MAX_FIELDS = 24
 
 OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, ENOCONV, ETIMEOUT, ENOTSUP = 0, -1, -2, -3, -4, -5, -6, -7
-REFLECT, PERIODIC = 0, 1
+REFLECT, PERIODIC, NOSLIP = 0, 1, 2
 F64, F32 = 0, 1
 
 # every function declared in include/snap.h
@@ -52,7 +52,8 @@ class GridDesc(C.Structure):
                 ("kessler", C.c_int), ("kessler_k", C.c_double * 4),
                 ("kessler_max_iter", C.c_int), ("kessler_tol", C.c_double),
                 ("cool_rate", C.c_double), ("cool_p_lo", C.c_double), ("cool_p_hi", C.c_double),
-                ("sponge_tau0", C.c_double), ("sponge_p0", C.c_double)]
+                ("sponge_tau0", C.c_double), ("sponge_p0", C.c_double),
+                ("T_bottom", C.c_double)]
 
 
 class Budget(C.Structure):
@@ -161,6 +162,7 @@ def desc_from_workload(w, dtype: Optional[str] = None, satadj: Optional[bool] = 
     sponge = tuple(getattr(w, "sponge", ()))
     if sponge:
         d.sponge_tau0, d.sponge_p0 = sponge
+    d.T_bottom = float(getattr(w, "T_bottom", 0.0))
     return d, keep
 
 

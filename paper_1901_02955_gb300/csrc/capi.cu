@@ -13,6 +13,10 @@
 #include "../../include/snap.h"
 #include "snap_internal.h"
 
+static_assert(snap::kBcReflect == SNAP_REFLECT && snap::kBcPeriodic == SNAP_PERIODIC &&
+                  snap::kBcNoSlip == SNAP_NOSLIP,
+              "boundary kinds of the kernels and of the C interface differ");
+
 namespace snap {
 bool find_kernels_dry2d(int f32, int visc, KernelSet *out);
 bool find_kernels_dry3d(int f32, int visc, KernelSet *out);
@@ -187,8 +191,10 @@ static int validate(const snap_grid_desc &d, const snap_grid_desc &d0, int idx, 
   if (d.nx < 3 || d.nz < 3 || d.ny < 1 || d.ny == 2) return bad("need nx >= 3, nz >= 3, ny == 1 or ny >= 3");
   if (!(d.dx > 0) || !(d.dz > 0) || (d.ny > 1 && !(d.dy > 0))) return bad("cell sizes must be positive");
   for (int s = 0; s < 6; ++s)
-    if (d.bc[s] != SNAP_REFLECT && d.bc[s] != SNAP_PERIODIC) return bad("bc must be REFLECT or PERIODIC");
-  if (d.bc[4] != SNAP_REFLECT || d.bc[5] != SNAP_REFLECT) return bad("the z boundaries must reflect");
+    if (d.bc[s] != SNAP_REFLECT && d.bc[s] != SNAP_PERIODIC && d.bc[s] != SNAP_NOSLIP)
+      return bad("bc must be REFLECT, PERIODIC or NOSLIP");
+  if (d.bc[4] == SNAP_PERIODIC || d.bc[5] == SNAP_PERIODIC) return bad("the z boundaries must be walls");
+  if (!isfinite(d.T_bottom) || !(d.T_bottom >= 0.0)) return bad("T_bottom must be finite and >= 0");
   if ((d.bc[0] == SNAP_PERIODIC) != (d.bc[1] == SNAP_PERIODIC)) return bad("periodic x needs both x sides periodic");
   if ((d.bc[2] == SNAP_PERIODIC) != (d.bc[3] == SNAP_PERIODIC)) return bad("periodic y needs both y sides periodic");
   if (!(d.gamma_d > 1.0) || !(d.R_d > 0.0)) return bad("gamma_d > 1 and R_d > 0 required");
@@ -417,8 +423,11 @@ extern "C" int snap_init_grid(snap_ctx **out, const snap_grid_desc *d, int n_dom
   }
   derive_phys(d[0], ctx->ph);
   ctx->desc.assign(d, d + n_domains);
-  // the adjoint covers neither the microphysics nor sedimentation
-  if (!ctx->visc && n_domains == 1 && !micro)
+  // the adjoint covers neither the microphysics nor sedimentation, nor no-slip walls or a
+  // fixed bottom temperature
+  bool plain_walls = d[0].T_bottom == 0.0;
+  for (int s = 0; s < 6; ++s) plain_walls = plain_walls && d[0].bc[s] != SNAP_NOSLIP;
+  if (!ctx->visc && n_domains == 1 && !micro && plain_walls)
     ctx->has_adj = find_adjoint_kernels(ctx->f32, ctx->nvap, ctx->ncond, ctx->three_d, &ctx->adj) ? 1 : 0;
   cudaError_t e = cudaSuccess;
   for (int v = 0; v < ctx->ks.nvariants && e == cudaSuccess; ++v) e = ctx->ks.var[v].prepare();
@@ -461,6 +470,7 @@ extern "C" int snap_init_grid(snap_ctx **out, const snap_grid_desc *d, int n_dom
     D.grav = g.grav;
     D.cfl = g.cfl;
     D.dt_fixed = -1.0;
+    D.T_bot = g.T_bottom;
     D.ncell = (long long)nc;
     (void)bytes;
   }
@@ -844,7 +854,7 @@ static int plain_stage(snap_ctx *ctx, const StageArgs &base, int stage, double d
 extern "C" int snap_record(snap_ctx *ctx, int nsteps, int ckpt_every, double dt_fixed) {
   if (!ctx) return fail(nullptr, SNAP_EINVAL, "snap_record: NULL context");
   if (!ctx->has_adj)
-    return fail(ctx, SNAP_ENOTSUP, "snap_record: the adjoint is built for one inviscid domain, dry or with one vapour (x-z)");
+    return fail(ctx, SNAP_ENOTSUP, "snap_record: the adjoint is built for one inviscid domain, dry or with one vapour (x-z), free-slip or periodic sides, no fixed bottom temperature");
   if (nsteps < 1 || ckpt_every < 0)
     return fail(ctx, SNAP_EINVAL, "snap_record: nsteps must be >= 1 and ckpt_every >= 0");
   const size_t sb = state_bytes_dom0(ctx);
@@ -972,7 +982,7 @@ extern "C" int snap_step_adjoint(snap_ctx *ctx, int nsteps, const void *lambda_f
                                  void *lambda_init, int dtype, void *stream) {
   if (!ctx) return fail(nullptr, SNAP_EINVAL, "snap_step_adjoint: NULL context");
   if (!ctx->has_adj)
-    return fail(ctx, SNAP_ENOTSUP, "snap_step_adjoint: the adjoint is built for one inviscid domain, dry or with one vapour (x-z)");
+    return fail(ctx, SNAP_ENOTSUP, "snap_step_adjoint: the adjoint is built for one inviscid domain, dry or with one vapour (x-z), free-slip or periodic sides, no fixed bottom temperature");
   if (!lambda_final || !lambda_init || (dtype != SNAP_F64 && dtype != SNAP_F32))
     return fail(ctx, SNAP_EINVAL, "snap_step_adjoint: bad pointers or dtype");
   if (ctx->rec_steps < 1 || nsteps != ctx->rec_steps)

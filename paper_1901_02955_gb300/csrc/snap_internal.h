@@ -47,6 +47,9 @@ struct CstT {
 };
 
 // One domain as the kernels see it (device memory).
+// Side boundary kinds (the values of SNAP_REFLECT, SNAP_PERIODIC, SNAP_NOSLIP).
+enum BcKind : int { kBcReflect = 0, kBcPeriodic = 1, kBcNoSlip = 2 };
+
 struct DomDev {
   int nx, ny, nz;
   int tx, ty, tz;            // tiles per direction
@@ -72,6 +75,7 @@ struct DomDev {
   unsigned long long *rate;  // CFL rate max as double bits (non-negative doubles order as
                              // unsigned integers)
   double *dt_step;           // time step of the current step
+  double T_bot;              // > 0: temperature of the ghost cells below the bottom wall
 };
 
 // State of the grid-wide barrier of the persistent step kernel (device memory).

@@ -995,6 +995,8 @@ __device__ __forceinline__ void stage_tiles(const StageArgs &a, const int stage,
         }
         if (!ok) continue;
         int gx = x0 + bx - 3, gy = y0 + by - B::HY, gz = z0 + bz - 3;
+        // the side this ghost lies beyond (x-, x+, y-, y+, z-, z+)
+        const int side = 2 * dirn + ((dirn == 0 ? gx : (dirn == 1 ? gy : gz)) < 0 ? 0 : 1);
         bool flip = false;
         if (dirn == 0) gx = map_index(gx, nx, D.bc[0], D.bc[1], flip);
         if (dirn == 1) gy = map_index(gy, ny, D.bc[2], D.bc[3], flip);
@@ -1004,7 +1006,23 @@ __device__ __forceinline__ void stage_tiles(const StageArgs &a, const int stage,
 #pragma unroll
         for (int v = 0; v < NV; ++v) y[v] = Ys[v * ncell + g];
         cons_to_prim<R, L>(ph, C, D, gz, y, x, pt, Tt);
-        if (flip) x[L::mom(dirn)] = -x[L::mom(dirn)];
+        if (flip) {
+          // a wall: free-slip negates the normal velocity, no-slip every component
+          if (D.bc[side] == kBcNoSlip) {
+#pragma unroll
+            for (int m = 0; m < L::NMOM; ++m) x[L::IM0 + m] = -x[L::IM0 + m];
+          } else {
+            x[L::mom(dirn)] = -x[L::mom(dirn)];
+          }
+          // Sec. 6 lower boundary: the ghost holds T_bot at the mirrored pressure and
+          // composition, so its density is p / (R_d den T_bot) (App. B: p = rho R_d den T,
+          // den the mixing factor), the mirrored density times T / T_bot
+          if (side == 4 && D.T_bot > 0.0) {
+            R num, den;
+            mix_factors<R, L>(C, x, num, den);
+            x[0] = pt * C.iR_d * Ar<R>::rcp(den * R(D.T_bot));
+          }
+        }
         const int bi = B::at(bx, by, bz);
 #pragma unroll
         for (int v = 0; v < NV; ++v) s_prim[v * B::NBOX + bi] = x[v];
@@ -1113,7 +1131,8 @@ __device__ __forceinline__ void stage_tiles(const StageArgs &a, const int stage,
           if constexpr (L::MOIST && MICRO) {
             // no condensate passes a wall
             const int kf = z0 + iz;
-            if (fz && ph.sediment && !(kf == 0 && D.bc[4] == 0) && !(kf == nz && D.bc[5] == 0))
+            if (fz && ph.sediment && !(kf == 0 && D.bc[4] != kBcPeriodic) &&
+                !(kf == nz && D.bc[5] != kBcPeriodic))
               sediment_flux<R, L>(C, QL, QR, pref, F);
           }
           if constexpr (VISC) {

@@ -67,3 +67,51 @@ def test_invalid_descriptor_rejected_on_host(lib):
     d, keep = capi.desc_from_workload(w)
     d.bc[4] = capi.PERIODIC
     assert L.snap_init_grid(ctypes.byref(p), ctypes.byref(d), 1) == capi.EINVAL
+
+
+def test_descriptor_layout_matches_the_header(tmp_path):
+    """The ctypes mirrors of snap_grid_desc and snap_species have the C layout: a small C
+    program compiled against include/snap.h prints the size and field offsets."""
+    import shutil
+    import subprocess
+    from paper_1901_02955_gb300 import capi
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    cuda_inc = os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "include")
+    fields = [f for f, _ in capi.GridDesc._fields_]
+    prog = tmp_path / "layout.c"
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "snap.h"', "int main(void) {",
+             '  printf("%zu %zu\\n", sizeof(snap_grid_desc), sizeof(snap_species));']
+    for f in fields:
+        lines.append(f'  printf("%zu\\n", offsetof(snap_grid_desc, {f}));')
+    lines.append("  return 0;\n}\n")
+    prog.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.check_call([cc, "-I", os.path.join(ROOT, "include"), "-I", cuda_inc, str(prog),
+                           "-o", str(exe)])
+    out = subprocess.check_output([str(exe)], text=True).split()
+    assert int(out[0]) == ctypes.sizeof(capi.GridDesc)
+    assert int(out[1]) == ctypes.sizeof(capi.Species)
+    for f, off in zip(fields, out[2:]):
+        assert int(off) == getattr(capi.GridDesc, f).offset, f
+
+
+def test_noslip_and_bottom_temperature_are_validated(lib):
+    import workloads as W
+    from paper_1901_02955_gb300 import capi
+    L = capi.load()
+    p = ctypes.c_void_p()
+    w = W.warm_bubble(n=8)
+    d, keep = capi.desc_from_workload(w)
+    d.bc[4] = capi.PERIODIC
+    d.bc[5] = capi.PERIODIC
+    assert L.snap_init_grid(ctypes.byref(p), ctypes.byref(d), 1) == capi.EINVAL
+    assert b"walls" in L.snap_last_error(None)
+    d, keep = capi.desc_from_workload(w)
+    d.bc[0] = 7
+    assert L.snap_init_grid(ctypes.byref(p), ctypes.byref(d), 1) == capi.EINVAL
+    d, keep = capi.desc_from_workload(w)
+    d.T_bottom = -1.0
+    assert L.snap_init_grid(ctypes.byref(p), ctypes.byref(d), 1) == capi.EINVAL
+    assert b"T_bottom" in L.snap_last_error(None)

@@ -338,13 +338,13 @@ def dry_bubble_3d(nx=32, ny=24, nz=20, L=1000.0, A=0.5, R=250.0, nsteps=10, dtyp
 
 
 def jovian(nx=256, ny=256, nz=128, Lx=100e3, Ly=100e3, Lz=150e3, nsteps=500, dtype="f32",
-           seed=BASE_SEED + 3, noise_K=0.1, q_deep=(0.040, 0.0027)):
+           seed=BASE_SEED + 3, noise_K=0.1, q_deep=(0.040, 0.0027), p_top=1e5):
     """3-D moist Jovian-like column (Sec. 6): H2/He gas with mu = 2.3 g/mol, c_p = 3.5 R;
-    dry adiabat theta = 166 K referenced at 1 bar at the top face; H2O and NH3 vapour with
-    deep mass mixing ratios 40 and 2.7 g/kg capped at saturation; no condensate initially;
-    seeded white-noise temperature perturbation (sigma 0.1 K); periodic x/y, walls in z.
-    The grid spacing is Lx/nx etc., so a crop (smaller nx, ny at the same spacing) is made
-    by scaling Lx, Ly with nx, ny."""
+    dry adiabat theta = 166 K referenced at 1 bar, the top face at p_top (1 bar by default);
+    H2O and NH3 vapour with deep mass mixing ratios 40 and 2.7 g/kg capped at saturation; no
+    condensate initially; seeded white-noise temperature perturbation (sigma 0.1 K);
+    periodic x/y, walls in z. The grid spacing is Lx/nx etc., so a crop (smaller nx, ny at
+    the same spacing) is made by scaling Lx, Ly with nx, ny."""
     R_d = RHAT / 2.3e-3
     gamma_d = 1.4
     g = 24.79
@@ -365,7 +365,7 @@ def jovian(nx=256, ny=256, nz=128, Lx=100e3, Ly=100e3, Lz=150e3, nsteps=500, dty
         rd, rv = _gas_densities(p, T, R_d, gamma_d, vapors, x_fn)
         return float(rd + sum(rv))
 
-    rho_bar, pf = _hydrostatic_column(nz, dz, g, p0, True, rho_of)
+    rho_bar, pf = _hydrostatic_column(nz, dz, g, p_top, True, rho_of)
     pk = 0.5 * (pf[:-1] + pf[1:])
     Tbar = T_of(pk)
     dT = noise_K * rng.normal(seed, nx * ny * nz).reshape(nz, ny, nx)
@@ -377,6 +377,26 @@ def jovian(nx=256, ny=256, nz=128, Lx=100e3, Ly=100e3, Lz=150e3, nsteps=500, dty
                     bc=(PERIODIC, PERIODIC, PERIODIC, PERIODIC, REFLECT, REFLECT), grav=g,
                     gamma_d=gamma_d, R_d=R_d, vapors=vapors, ncond=2, rho_bar=rho_bar,
                     p_bar_face=pf, Y=Y, nsteps=nsteps, dtype=dtype, seed=seed)
+
+
+def jovian_rce(nx=256, ny=256, nz=128, Lx=100e3, Ly=100e3, Lz=332e3, p_top=1e4, nsteps=500,
+               dtype="f32", seed=BASE_SEED + 6, noise_K=0.1, cool_K_per_day=1.0):
+    """The Jovian radiative-convective setup of Sec. 6 on the column above: the top face at
+    0.1 bar and 332 km of depth put the bottom near 200 bar and 750 K on the dry adiabat
+    (the paper holds 800 K at 200 bar). Kessler microphysics with the paper's constants and
+    precipitation falling at 20 m/s; a body cooling of cool_K_per_day between 2 and 0.2 bar;
+    a sponge above 0.2 bar relaxing the horizontal winds on 1e4 s (p/p0)^2; a no-slip bottom
+    wall whose ghost cells hold the bottom level's initial horizontal-mean temperature (the
+    fixed-temperature lower boundary). Periodic x and y, a free-slip top."""
+    w = jovian(nx=nx, ny=ny, nz=nz, Lx=Lx, Ly=Ly, Lz=Lz, nsteps=nsteps, dtype=dtype,
+               seed=seed, noise_K=noise_K, p_top=p_top)
+    pk0 = 0.5 * (w.p_bar_face[0] + w.p_bar_face[1])
+    T_bot = 166.0 * (pk0 / 1e5) ** ((w.gamma_d - 1.0) / w.gamma_d)
+    return dataclasses.replace(
+        w, name=f"jovian_rce_{nx}x{ny}x{nz}",
+        bc=(PERIODIC, PERIODIC, PERIODIC, PERIODIC, NOSLIP, REFLECT),
+        kessler_k=(1e9, 1e-4, 0.0, 1e-2), w_term=(0.0, -20.0),
+        cooling=(cool_K_per_day / 86400.0, 2e4, 2e5), sponge=(1e4, 2e4), T_bottom=float(T_bot))
 
 
 def moist_bubble(n=64, L=1000.0, A=0.5, R=250.0, xc=500.0, zc=450.0, rh=0.9, nsteps=200,
