@@ -82,7 +82,9 @@ typedef struct snap_grid_desc {
   int satadj;              /* 1: saturation adjustment after every stage (needs n_cond > 0) */
   int satadj_max_iter;     /* sweep limit of the adjustment (e.g. 20) */
   double satadj_tol;       /* relative stop tolerance on the molar transfer; raised to
-                              32 machine epsilons of dtype when smaller */
+                              32 machine epsilons of dtype when smaller, and for each vapour
+                              to 4 (|a| + 2) epsilons, a the exponent of its saturation
+                              pressure (the precision dtype holds that pressure to) */
   double weno_eps;         /* epsilon of the WENO5 weights (e.g. 1e-6) */
   /* Sec. 2, Eq. d3: terminal velocity of condensate j of every vapour, m/s (< 0 falls); a
    * nonzero value adds the sedimentation fluxes of mass, momentum and energy at z faces,
@@ -91,8 +93,8 @@ typedef struct snap_grid_desc {
   double w_term[SNAP_MAX_COND];
   /* Sec. 3: 1 applies the Kessler scheme after every step by backward Euler (needs n_cond ==
    * 2: condensate 0 cloud, 1 precipitation): kessler_k = k1 condensation, k2 autoconversion,
-   * k3 accretion, k4 evaporation, 1/s; iterations stop at kessler_tol (raised to 32 machine
-   * epsilons of dtype) or report SNAP_ENOCONV after kessler_max_iter. */
+   * k3 accretion, k4 evaporation, 1/s; iterations stop at kessler_tol (raised as satadj_tol
+   * is) or report SNAP_ENOCONV after kessler_max_iter. */
   int kessler;
   double kessler_k[4];
   int kessler_max_iter;

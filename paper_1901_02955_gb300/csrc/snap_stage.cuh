@@ -32,6 +32,7 @@ struct Ar<float> {
   static __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
   static __device__ __forceinline__ float exp_(float x) { return expf(x); }
   static __device__ __forceinline__ float log_(float x) { return logf(x); }
+  static __device__ __forceinline__ float log1p_(float x) { return log1pf(x); }
   static __device__ __forceinline__ float pow_(float x, float y) { return powf(x, y); }
   // exp2(y log2 x) on the special-function unit: a few ulp when |y log2 x| is small, as for
   // the Exner function (p / 1e5)^(R/c_p) near 1 bar
@@ -47,6 +48,7 @@ struct Ar<double> {
   static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
   static __device__ __forceinline__ double exp_(double x) { return exp(x); }
   static __device__ __forceinline__ double log_(double x) { return log(x); }
+  static __device__ __forceinline__ double log1p_(double x) { return log1p(x); }
   static __device__ __forceinline__ double pow_(double x, double y) { return pow(x, y); }
   static __device__ __forceinline__ double pow_small(double x, double y) { return pow(x, y); }
   static __device__ __forceinline__ double sqrt_pos(double x) { return sqrt(x); }
@@ -436,8 +438,11 @@ __device__ int satadj_cell(const Phys &ph, const CstT<R> &C, R *y, double eref, 
         R gsum = gas * iN - qv;
         R t = T * C.inv_Tref[i];
         // p* = p^r exp[beta (1 - 1/t) - delta ln t] with 1 - 1/t = (T - T^r) / T
-        R ps = C.pref[i] *
-               Ar<R>::exp_(C.beta[i] * dTr * Ar<R>::rcp(T) - C.delta[i] * Ar<R>::log_(t));
+        const R arg = C.beta[i] * dTr * Ar<R>::rcp(T) - C.delta[i] * Ar<R>::log_(t);
+        R ps = C.pref[i] * Ar<R>::exp_(arg);
+        // the arithmetic type holds p* only to ~(|arg| + 2) eps relative (the exponent's own
+        // rounding), so the transfer cannot settle below that: the stop test allows 4 times it
+        const R tol = fmax(C.satadj_tol, R(4) * (fabs(arg) + R(2)) * R(Ar<R>::eps));
         R s = Ar<R>::div(ps, p);
         R dq;
         if (s >= R(1)) {
@@ -464,7 +469,7 @@ __device__ int satadj_cell(const Phys &ph, const CstT<R> &C, R *y, double eref, 
           y[L::cond(i, 0)] += drho;
           stale = true;
         }
-        if (fabs(dq) > C.satadj_tol * (qv + qc)) conv = false;
+        if (fabs(dq) > tol * (qv + qc)) conv = false;
       }
       if (conv) return sweep;
     }
@@ -567,13 +572,20 @@ __device__ __forceinline__ void sediment_flux(const CstT<R> &C, const R *XL, con
 template <class R, class L>
 __device__ __forceinline__ void kessler_eval(const Phys &ph, const CstT<R> &C, const R *y,
                                              double eref, int i, R rho, const R *yn, R dt,
-                                             bool sat, R G[2], R A[2][2], R &s_out) {
+                                             bool sat, R G[2], R A[2][2], R &s_out,
+                                             R &tol_out) {
   const int vi = 1 + i, ci = L::cond(i, 0), ri = L::cond(i, 1);
   double Td, pd;
   cell_Tp<R, L>(ph, y, eref, Td, pd);
   const R T = R(Td), iT = Ar<R>::rcp(T), t = T * C.inv_Tref[i], it = Ar<R>::rcp(t);
-  const R rs = C.pref[i] * Ar<R>::exp_(C.beta[i] * (R(1) - it) - C.delta[i] * Ar<R>::log_(t)) *
-               C.eps[i] * C.iR_d * iT;  // p* / (R_i T)
+  // T - T^r kept accurate (from the FP64 temperature): rho*(T) is steep, d ln rho*/d ln T ~
+  // beta / t ~ 20 near water's triple point, so T rounded to FP32 alone would put ~1e-6
+  // relative noise into s = rho_v - rho* -- the size of the FP32 Newton stop tolerance
+  const R dTr = R(Td - ph.Tref[i]);
+  const R arg = C.beta[i] * dTr * iT - C.delta[i] * Ar<R>::log1p_(dTr * C.inv_Tref[i]);
+  const R rs = C.pref[i] * Ar<R>::exp_(arg) * C.eps[i] * C.iR_d * iT;  // p* / (R_i T)
+  // rho* is held only to ~(|arg| + 2) eps relative: the Newton stop test allows 4 times it
+  tol_out = fmax(C.kessler_tol, R(4) * (fabs(arg) + R(2)) * R(Ar<R>::eps));
   const R drs = rs * ((C.beta[i] * it - C.delta[i]) - R(1)) * iT;
   R Cv = y[0];
 #pragma unroll
@@ -631,17 +643,17 @@ __device__ __forceinline__ int kessler_branch(const Phys &ph, const CstT<R> &C, 
   y[ci] = yn[1];
   y[ri] = yn[2];
   for (int m = 1; m <= ph.kessler_max_iter; ++m) {
-    R G[2], A[2][2];
-    kessler_eval<R, L>(ph, C, y, eref, i, rho, yn, dt, sat, G, A, s);
+    R G[2], A[2][2], tol;
+    kessler_eval<R, L>(ph, C, y, eref, i, rho, yn, dt, sat, G, A, s, tol);
     const R idet = Ar<R>::rcp(A[0][0] * A[1][1] - A[0][1] * A[1][0]);
     const R dv = (-G[0] * A[1][1] + G[1] * A[0][1]) * idet;
     const R dc = (-G[1] * A[0][0] + G[0] * A[1][0]) * idet;
     y[vi] += dv;
     y[ci] += dc;
     y[ri] = tot - y[vi] - y[ci];
-    if (fabs(dv) + fabs(dc) <= C.kessler_tol * (fabs(y[vi]) + fabs(y[ci]) + fabs(y[ri]))) {
-      R Gt[2], At[2][2];
-      kessler_eval<R, L>(ph, C, y, eref, i, rho, yn, dt, sat, Gt, At, s);
+    if (fabs(dv) + fabs(dc) <= tol * (fabs(y[vi]) + fabs(y[ci]) + fabs(y[ri]))) {
+      R Gt[2], At[2][2], tt;
+      kessler_eval<R, L>(ph, C, y, eref, i, rho, yn, dt, sat, Gt, At, s, tt);
       return m;
     }
   }
@@ -661,8 +673,8 @@ __device__ int kessler_cell(const Phys &ph, const CstT<R> &C, R *y, double eref,
       const int vi = 1 + i, ci = L::cond(i, 0), ri = L::cond(i, 1);
       const R yn[3] = {y[vi], y[ci], y[ri]};
       const R tot = yn[0] + yn[1] + yn[2];
-      R G[2], A[2][2], s0, s;
-      kessler_eval<R, L>(ph, C, y, eref, i, rho, yn, dt, true, G, A, s0);
+      R G[2], A[2][2], s0, s, tol0;
+      kessler_eval<R, L>(ph, C, y, eref, i, rho, yn, dt, true, G, A, s0, tol0);
       const bool first = s0 > R(0);
       int it = kessler_branch<R, L>(ph, C, y, eref, i, rho, yn, tot, dt, first, s);
       if (!(it > 0 && (first ? s > R(0) : s <= R(0)))) {
