@@ -102,6 +102,28 @@ struct Box {
   static __device__ __forceinline__ int at(int bx, int by, int bz) {
     return (bz * BY + by) * BX + bx;
   }
+  // Storage of the primitives in shared memory. x-z: the whole box. 3-D: only the cross the
+  // stencils use -- x-lines through the owned y, z range with both x halos (contiguous, so
+  // x stencils have unit stride), then the y halos of the owned x, z range, then the z halos
+  // of the owned x, y range -- about half the box, which lets a third CTA fit on an SM.
+  // Ragged tiles put their far halos inside the owned index range; the fill and the reads use
+  // the same map, so a location is never claimed twice.
+  static constexpr int NXB = BX * T::TY * T::TZ;
+  static constexpr int NYH = D3 ? T::TX * 6 * T::TZ : 0;
+  static constexpr int NZH = T::TX * T::TY * 6;
+  static constexpr int NSTORE = D3 ? NXB + NYH + NZH : NBOX;
+  static __device__ __forceinline__ int idx(int bx, int by, int bz) {
+    if constexpr (!D3) {
+      return at(bx, by, bz);
+    } else {
+      const int oy = by - 3, oz = bz - 3;
+      if ((unsigned)oy < (unsigned)T::TY && (unsigned)oz < (unsigned)T::TZ)
+        return (oz * T::TY + oy) * BX + bx;
+      if ((unsigned)oz < (unsigned)T::TZ)  // y halo: by in 0..2 or TY+3..TY+5
+        return NXB + (oz * 6 + (by < 3 ? by : by - T::TY)) * T::TX + (bx - 3);
+      return NXB + NYH + ((bz < 3 ? bz : bz - T::TZ) * T::TY + oy) * T::TX + (bx - 3);
+    }
+  }
 };
 
 // Per-level reference values in the kernel's type: FP32 kernels read FP32 copies, FP64
@@ -849,8 +871,8 @@ __device__ __forceinline__ R cell_rate_r(const CstT<R> &C, const R *y, R eref, R
 template <class R, class L, bool VISC, class T>
 struct StageSmem {
   using B = Box<T, L::D3>;
-  static constexpr size_t prim = sizeof(R) * L::NV * B::NBOX;
-  static constexpr size_t visc = VISC ? sizeof(R) * 2 * B::NBOX : 0;
+  static constexpr size_t prim = sizeof(R) * L::NV * B::NSTORE;
+  static constexpr size_t visc = VISC ? sizeof(R) * 2 * B::NSTORE : 0;
   static constexpr size_t face = sizeof(R) * 2 * L::NV * B::NF;  // left state/flux, right state
   static constexpr size_t red = 32 * sizeof(double);
   static constexpr size_t base = prim + visc + face + red;
@@ -902,7 +924,7 @@ __device__ __forceinline__ void stage_tiles(const StageArgs &a, const int stage,
   constexpr int TX = T::TX, TY = T::TY, TZ = T::TZ, NT = T::NT;
   R *s_prim = reinterpret_cast<R *>(smem);
   R *s_th = reinterpret_cast<R *>(smem + S::prim);
-  R *s_pi = s_th + (VISC ? B::NBOX : 0);
+  R *s_pi = s_th + (VISC ? B::NSTORE : 0);
   R *s_fl = reinterpret_cast<R *>(smem + S::prim + S::visc);  // left states, then fluxes
   R *s_fr = s_fl + NV * B::NF;                                 // right states
   double *s_red = reinterpret_cast<double *>(smem + S::prim + S::visc + S::face);
@@ -967,9 +989,9 @@ __device__ __forceinline__ void stage_tiles(const StageArgs &a, const int stage,
         for (int v = 0; v < NV; ++v) ys[m][v] = Ys[v * ncell + g];
         R x[NV], pt, Tt;
         cons_to_prim<R, L>(ph, C, D, k, ys[m], x, pt, Tt);
-        const int bi = B::at(lx + 3, ly + B::HY, lz + 3);
+        const int bi = B::idx(lx + 3, ly + B::HY, lz + 3);
 #pragma unroll
-        for (int v = 0; v < NV; ++v) s_prim[v * B::NBOX + bi] = x[v];
+        for (int v = 0; v < NV; ++v) s_prim[v * B::NSTORE + bi] = x[v];
         if constexpr (VISC) {
           const R Pi = Ar<R>::pow_small(pt * R(1e-5), C.kappa);
           s_th[bi] = pt * Ar<R>::rcp(x[0] * Pi) * C.iR_d;
@@ -1035,9 +1057,9 @@ __device__ __forceinline__ void stage_tiles(const StageArgs &a, const int stage,
             x[0] = pt * C.iR_d * Ar<R>::rcp(den * R(D.T_bot));
           }
         }
-        const int bi = B::at(bx, by, bz);
+        const int bi = B::idx(bx, by, bz);
 #pragma unroll
-        for (int v = 0; v < NV; ++v) s_prim[v * B::NBOX + bi] = x[v];
+        for (int v = 0; v < NV; ++v) s_prim[v * B::NSTORE + bi] = x[v];
         if constexpr (VISC) {
           const R Pi = Ar<R>::pow_small(pt * R(1e-5), C.kappa);
           s_th[bi] = pt * Ar<R>::rcp(x[0] * Pi) * C.iR_d;
@@ -1077,7 +1099,18 @@ __device__ __forceinline__ void stage_tiles(const StageArgs &a, const int stage,
           lz -= fz;
           const int ld = fx ? lx : (fy ? ly : lz);
           if (it < nrec && ld <= ed && lx < ex + fx && ly < ey + fy && lz < ez + fz) {
-            const int bi = B::at(lx + 3, ly + B::HY, lz + 3);
+            // the five cells of the window along d: a fixed stride in the x-z box and along the
+            // 3-D x-lines; mapped one by one where a 3-D y or z window leaves the x-lines
+            int o[5];
+            if (L::D3 && !fx) {
+#pragma unroll
+              for (int k = 0; k < 5; ++k)
+                o[k] = B::idx(lx + 3, ly + B::HY + fy * (k - 2), lz + 3 + fz * (k - 2));
+            } else {
+              const int bi = B::idx(lx + 3, ly + B::HY, lz + 3);
+#pragma unroll
+              for (int k = 0; k < 5; ++k) o[k] = bi + (k - 2) * stride;
+            }
             const int fl = ((lz + fz) * sy + (ly + fy)) * sx + (lx + fx);  // face c+1/2
             const int fr = (lz * sy + ly) * sx + lx;                        // face c-1/2
             const bool has_l = ld < ed, has_r = ld >= 0;
@@ -1085,13 +1118,12 @@ __device__ __forceinline__ void stage_tiles(const StageArgs &a, const int stage,
               // two variables per packed FP32x2 instruction, the odd one alone
 #pragma unroll
               for (int v = 0; v + 1 < NV; v += 2) {
-                const R *q = s_prim + v * B::NBOX + bi;
-                const R *r2 = q + B::NBOX;
+                const R *q = s_prim + v * B::NSTORE;
+                const R *r2 = q + B::NSTORE;
                 float2 qm, qp;
-                weno5_pair2(make_float2(q[-2 * stride], r2[-2 * stride]),
-                            make_float2(q[-stride], r2[-stride]), make_float2(q[0], r2[0]),
-                            make_float2(q[stride], r2[stride]),
-                            make_float2(q[2 * stride], r2[2 * stride]), weps, qm, qp);
+                weno5_pair2(make_float2(q[o[0]], r2[o[0]]), make_float2(q[o[1]], r2[o[1]]),
+                            make_float2(q[o[2]], r2[o[2]]), make_float2(q[o[3]], r2[o[3]]),
+                            make_float2(q[o[4]], r2[o[4]]), weps, qm, qp);
                 if (has_l) {
                   s_fl[v * B::NF + fl] = qm.x;
                   s_fl[(v + 1) * B::NF + fl] = qm.y;
@@ -1102,20 +1134,18 @@ __device__ __forceinline__ void stage_tiles(const StageArgs &a, const int stage,
                 }
               }
               if constexpr (NV % 2 == 1) {
-                const R *q = s_prim + (NV - 1) * B::NBOX + bi;
+                const R *q = s_prim + (NV - 1) * B::NSTORE;
                 R qm, qp;
-                weno5_pair<R>(q[-2 * stride], q[-stride], q[0], q[stride], q[2 * stride],
-                              weps, qm, qp);
+                weno5_pair<R>(q[o[0]], q[o[1]], q[o[2]], q[o[3]], q[o[4]], weps, qm, qp);
                 if (has_l) s_fl[(NV - 1) * B::NF + fl] = qm;
                 if (has_r) s_fr[(NV - 1) * B::NF + fr] = qp;
               }
             } else {
 #pragma unroll
               for (int v = 0; v < NV; ++v) {
-                const R *q = s_prim + v * B::NBOX + bi;
+                const R *q = s_prim + v * B::NSTORE;
                 R qm, qp;
-                weno5_pair<R>(q[-2 * stride], q[-stride], q[0], q[stride], q[2 * stride],
-                              weps, qm, qp);
+                weno5_pair<R>(q[o[0]], q[o[1]], q[o[2]], q[o[3]], q[o[4]], weps, qm, qp);
                 if (has_l) s_fl[v * B::NF + fl] = qm;
                 if (has_r) s_fr[v * B::NF + fr] = qp;
               }
@@ -1148,15 +1178,15 @@ __device__ __forceinline__ void stage_tiles(const StageArgs &a, const int stage,
               sediment_flux<R, L>(C, QL, QR, pref, F);
           }
           if constexpr (VISC) {
-            const int bi = B::at(ix + 3, iy + B::HY, iz + 3);  // right cell of the face
-            const int bl = bi - stride;
+            const int bi = B::idx(ix + 3, iy + B::HY, iz + 3);  // right cell of the face
+            const int bl = B::idx(ix + 3 - fx, iy + B::HY - fy, iz + 3 - fz);
             const R rf = R(0.5) * (s_prim[bl] + s_prim[bi]);
             const R ih = P::ih(D, d), nu = C.nu;
             R work = R(0);
 #pragma unroll
             for (int mm = 0; mm < L::NMOM; ++mm) {
-              const R ul = s_prim[(L::IM0 + mm) * B::NBOX + bl];
-              const R ur = s_prim[(L::IM0 + mm) * B::NBOX + bi];
+              const R ul = s_prim[(L::IM0 + mm) * B::NSTORE + bl];
+              const R ur = s_prim[(L::IM0 + mm) * B::NSTORE + bi];
               const R grad = (ur - ul) * ih;
               F[L::IM0 + mm] -= rf * nu * grad;
               work += R(0.5) * (ul + ur) * grad;
@@ -1197,7 +1227,6 @@ __device__ __forceinline__ void stage_tiles(const StageArgs &a, const int stage,
       const int lx = c % TX, ly = (c / TX) % TY, lz = c / (TX * TY);
       if (c < B::NCELL && lx < ex && ly < ey && lz < ez) {
         const int k = z0 + lz;
-        const int bi = B::at(lx + 3, ly + B::HY, lz + 3);
         const R grav = P::grav(D);
         // vertical momentum: -(rho - rho_bar) g (Eq. mom3 with the reference balance removed)
         acc[m][L::mom(2)] -= P::template drho<L>(D, k, ys[m]) * grav;
