@@ -99,7 +99,7 @@ struct Box {
   static constexpr int NF = NFX > NFZ ? (NFX > NFY ? NFX : NFY) : (NFZ > NFY ? NFZ : NFY);
   static constexpr int NCELL = T::TX * T::TY * T::TZ;
   static constexpr int CPT = (NCELL + T::NT - 1) / T::NT;  // owned cells per thread
-  static __device__ __forceinline__ int at(int bx, int by, int bz) {
+  static __host__ __device__ __forceinline__ int at(int bx, int by, int bz) {
     return (bz * BY + by) * BX + bx;
   }
   // Storage of the primitives in shared memory. x-z: the whole box. 3-D: only the cross the
@@ -112,7 +112,7 @@ struct Box {
   static constexpr int NYH = D3 ? T::TX * 6 * T::TZ : 0;
   static constexpr int NZH = T::TX * T::TY * 6;
   static constexpr int NSTORE = D3 ? NXB + NYH + NZH : NBOX;
-  static __device__ __forceinline__ int idx(int bx, int by, int bz) {
+  static __host__ __device__ __forceinline__ int idx(int bx, int by, int bz) {
     if constexpr (!D3) {
       return at(bx, by, bz);
     } else {
