@@ -137,14 +137,17 @@ int snap_init_grid(snap_ctx **out, const snap_grid_desc *d, int n_domains);
 
 /* Copy the conserved state of one domain in. Y has the layout above with element type
  * dtype (SNAP_F64 or SNAP_F32, converted to the context's dtype); on_device != 0 means Y is a
- * device pointer (e.g. a torch CUDA tensor), else host memory (pinned memory is copied
- * asynchronously). stream: a cudaStream_t to order the copy on, or NULL for the context's.
- * The CFL rate of the new state is recomputed. */
+ * device pointer (e.g. a torch CUDA tensor), else host memory: page-locked (pinned) memory
+ * is read by the conversion kernel itself through its device mapping, asynchronously (keep
+ * it unchanged until the stream has passed the call); pageable memory is staged. stream: a
+ * cudaStream_t to order the copy on, or NULL for the context's. The CFL rate of the new
+ * state is recomputed. */
 int snap_set_state(snap_ctx *ctx, int domain, const void *Y, int dtype, int on_device,
                    void *stream);
 
 /* Copy the current conserved state of one domain out (same layout and conventions). Host
- * destinations are written when the call returns. */
+ * destinations (pinned ones written directly by the conversion kernel) are complete when
+ * the call returns. */
 int snap_get_state(snap_ctx *ctx, int domain, void *Y_out, int dtype, int on_device,
                    void *stream);
 

@@ -609,6 +609,18 @@ static cudaStream_t pick(snap_ctx *ctx, void *stream) {
   return stream ? (cudaStream_t)stream : ctx->stream;  // NULL: the context's current stream
 }
 
+// Device address of page-locked host memory (a pinned buffer is mapped into the device's
+// address space): the conversion kernel then reads or writes it directly over the host link,
+// with no staging copy. nullptr for pageable memory.
+static void *mapped_host(const void *p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) == cudaSuccess && a.type == cudaMemoryTypeHost &&
+      a.devicePointer)
+    return a.devicePointer;
+  cudaGetLastError();
+  return nullptr;
+}
+
 extern "C" int snap_set_state(snap_ctx *ctx, int domain, const void *Y, int dtype, int on_device,
                               void *stream) {
   if (!ctx) return fail(nullptr, SNAP_EINVAL, "snap_set_state: NULL context");
@@ -621,8 +633,12 @@ extern "C" int snap_set_state(snap_ctx *ctx, int domain, const void *Y, int dtyp
   const size_t sw = src_f32 ? 4 : 8;
   const void *src = Y;
   if (!on_device) {
-    CK(cudaMemcpyAsync(ctx->staging, Y, n * sw, cudaMemcpyHostToDevice, s));
-    src = ctx->staging;
+    if (const void *m = mapped_host(Y)) {
+      src = m;
+    } else {
+      CK(cudaMemcpyAsync(ctx->staging, Y, n * sw, cudaMemcpyHostToDevice, s));
+      src = ctx->staging;
+    }
   }
   CK(launch_state_copy(src, src_f32, D.buf[0], ctx->f32, ctx->nv, D.ncell,
                        (long long)D.nx * D.ny, D.e_ref, 1, s));
@@ -639,11 +655,12 @@ extern "C" int snap_get_state(snap_ctx *ctx, int domain, void *Y_out, int dtype,
   const long long n = D.ncell * ctx->nv;
   const int dst_f32 = dtype == SNAP_F32;
   const size_t dw = dst_f32 ? 4 : 8;
-  void *dst = on_device ? Y_out : ctx->staging;
+  void *mapped = on_device ? nullptr : mapped_host(Y_out);
+  void *dst = on_device ? Y_out : (mapped ? mapped : ctx->staging);
   CK(launch_state_copy(D.buf[0], ctx->f32, dst, dst_f32, ctx->nv, D.ncell,
                        (long long)D.nx * D.ny, D.e_ref, 0, s));
   if (!on_device) {
-    CK(cudaMemcpyAsync(Y_out, ctx->staging, n * dw, cudaMemcpyDeviceToHost, s));
+    if (!mapped) CK(cudaMemcpyAsync(Y_out, ctx->staging, n * dw, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
   }
   return SNAP_OK;

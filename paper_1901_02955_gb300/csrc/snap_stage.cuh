@@ -750,8 +750,8 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_al
 //   qp = right state at face c-1/2  = I_weno(Q_{c+2}, .., Q_{c-2})  (Eq. q+, mirror stencil)
 // The Jiang-Shu smoothness indicator of a 3-cell triple does not depend on the direction the
 // triple is read in, so the three indicators (and their inverse squares) serve both faces; the
-// mirror stencil takes them in reverse order. The weights are rescaled by the smallest
-// (eps + beta)^2, which cancels in the normalisation and keeps every sum in range.
+// mirror stencil takes them in reverse order. The linear weights are folded into the
+// candidate coefficients, so each face needs one normalising reciprocal.
 template <class R>
 __device__ __forceinline__ void weno5_pair(R a, R b, R c, R d, R e, R eps, R &qm, R &qp) {
   R t;
