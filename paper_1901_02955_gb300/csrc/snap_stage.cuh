@@ -767,8 +767,21 @@ __device__ __forceinline__ void weno5_pair(R a, R b, R c, R d, R e, R eps, R &qm
   R b2 = R(13.0 / 12.0) * t * t;
   t = R(3) * c - R(4) * d + e;
   b2 += R(0.25) * t * t;
-  // inverse squares 1 / (eps + beta_k)^2, shared by both faces
-  R g0 = Ar<R>::rcp(eps + b0), g1 = Ar<R>::rcp(eps + b1), g2 = Ar<R>::rcp(eps + b2);
+  // inverse squares 1 / (eps + beta_k)^2, shared by both faces. FP64 (whose reciprocal is a
+  // multi-instruction sequence on a slow pipe) forms them up to the common factor
+  // 1 / (e0 e1 e2)^2, which cancels in each face's normalisation: g_k = (product of the other
+  // two e)^2 -- no reciprocal here, and the two normalisations below share one.
+  R g0, g1, g2;
+  if constexpr (sizeof(R) == 8) {
+    const R e0 = eps + b0, e1 = eps + b1, e2 = eps + b2;
+    g0 = e1 * e2;
+    g1 = e0 * e2;
+    g2 = e0 * e1;
+  } else {
+    g0 = Ar<R>::rcp(eps + b0);
+    g1 = Ar<R>::rcp(eps + b1);
+    g2 = Ar<R>::rcp(eps + b2);
+  }
   g0 *= g0;
   g1 *= g1;
   g2 *= g2;
@@ -783,8 +796,22 @@ __device__ __forceinline__ void weno5_pair(R a, R b, R c, R d, R e, R eps, R &qm
   const R p2 = R(0.1) * c + R(0.25) * b - R(0.05) * a;
   const R Sm = R(0.1) * g0 + R(0.6) * g1 + R(0.3) * g2;
   const R Sp = R(0.1) * g2 + R(0.6) * g1 + R(0.3) * g0;
-  qm = (g0 * m0 + g1 * m1 + g2 * m2) * Ar<R>::rcp(Sm);
-  qp = (g2 * p0 + g1 * p1 + g0 * p2) * Ar<R>::rcp(Sp);
+  const R Nm = g0 * m0 + g1 * m1 + g2 * m2, Np = g2 * p0 + g1 * p1 + g0 * p2;
+  if constexpr (sizeof(R) == 8) {
+    // 1/Sm = Sp / (Sm Sp) and 1/Sp = Sm / (Sm Sp); one division each only if the product
+    // leaves the exponent range (g ~ e^4, so Sm Sp ~ e^8: eps far below 1e-6 or huge beta)
+    const R Z = R(1) / (Sm * Sp);
+    if (Z > R(0) && Z < R(INFINITY)) {
+      qm = Nm * (Sp * Z);
+      qp = Np * (Sm * Z);
+    } else {
+      qm = Nm / Sm;
+      qp = Np / Sp;
+    }
+  } else {
+    qm = Nm * Ar<R>::rcp(Sm);
+    qp = Np * Ar<R>::rcp(Sp);
+  }
 }
 
 // weno5_pair<float> for two variables at once on the packed FP32x2 pipe of sm_100-class SMs
