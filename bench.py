@@ -130,19 +130,30 @@ def kernel_sources_md5():
     return h.hexdigest()
 
 
-def ncu_traffic():
-    """DRAM bytes per launch of the stage kernel from the committed ncu summary, if it was
-    taken on the current kernel sources (else None)."""
+def ncu_record():
+    """The committed ncu record of the stage kernel (DRAM bytes and warp instructions per
+    launch), if it was taken on the current kernel sources (else an empty dict)."""
     path = os.path.join(ROOT, "profiles", "stage_kernel_density_current_traffic.json")
     if not os.path.exists(path):
-        return None
+        return {}
     try:
         d = json.load(open(path))
         if d.get("sources_md5") == kernel_sources_md5():
-            return float(d["dram_bytes_per_launch"])
+            return d
     except Exception:
         pass
-    return None
+    return {}
+
+
+def ncu_traffic():
+    """DRAM bytes per launch of the stage kernel (None without a current ncu record)."""
+    d = ncu_record()
+    return float(d["dram_bytes_per_launch"]) if "dram_bytes_per_launch" in d else None
+
+
+# Instruction issue limit of the part: 152 SMs x 4 schedulers, one warp instruction each per
+# clock at 2070 MHz
+ISSUE_PEAK_WARP_INST = 152 * 4 * 2.070e9
 
 
 class Clocks:
@@ -589,6 +600,14 @@ def main():
                 "hbm": {"achieved": achieved, "peak": peak, "unit": "GB/s",
                         "frac": achieved / peak, "peak_source": f"{peak_src} HBM copy bandwidth",
                         "algorithmic_bytes_per_launch": alg_bytes}}
+    inst = ncu_record().get("warp_instructions_per_launch")
+    if inst:
+        # issued warp instructions per launch (ncu, same sources) over the event-timed stage
+        rate = float(inst) / (stage_ms * 1e-3)
+        roofline["issue"] = {"achieved": rate, "peak": ISSUE_PEAK_WARP_INST,
+                             "unit": "warp instructions/s", "frac": rate / ISSUE_PEAK_WARP_INST,
+                             "warp_instructions_per_launch": float(inst),
+                             "peak_source": "4 schedulers x 152 SMs x 2070 MHz"}
 
     # ---- end to end through the C ABI with pinned host buffers --------------------------------
     host_in = torch.from_numpy(w32.Y.astype(np.float32)).pin_memory()

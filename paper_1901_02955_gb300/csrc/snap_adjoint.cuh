@@ -511,7 +511,8 @@ __device__ __forceinline__ void adj_face(const AdjArgs &a, const DomDev &D, cons
 
 // One thread per face; the faces of x, then y (3-D), then z.
 template <class R, class L>
-__global__ void __launch_bounds__(128) adj_face_kernel(const AdjArgs a) {
+__global__ void __launch_bounds__(128, (sizeof(R) == 4 && !L::MOIST && !L::D3) ? 7 : 0)
+    adj_face_kernel(const AdjArgs a) {
   const DomDev &D = a.doms[0];
   const CstT<R> &C = acst<R>(a);
   const int nx = D.nx, ny = D.ny, nz = D.nz;
