@@ -42,7 +42,7 @@ def parse():
                    choices=[WORKLOAD, "jovian_256x256x128", "jovian_256x256x128_kessler",
                             "jovian_rce_256x256x128",
                             "ensemble_96", "ensemble_96_autotuned", "adjoint_256x256",
-                            "bryan_1000s"],
+                            "bryan_1000s", "density_current_900s"],
                    help="the default is the headline workload; the others print an extra "
                         "measurement line of the same form (3-D moist column, the same with "
                         "Kessler microphysics and falling precipitation, moist ensemble) or "
@@ -429,6 +429,54 @@ def bryan_workload(args, local):
     print(json.dumps(line), flush=True)
 
 
+def straka_workload(args, local):
+    """The density current (Sec. 5.1, after Straka et al.) run to 900 s at 25 m on the GPU,
+    FP64 and FP32, with the CFL time step: the extrema of the potential-temperature anomaly
+    against the 300 K background and the position of the front (the farthest surface cell
+    colder than -1 K). The paper reports a largest anomaly of 0.12 K at 900 s with LMARS (1.84 K
+    with HLLC); the minimum starts at -15 K and mixing by the viscosity raises it."""
+    import torch
+    import workloads as W
+    from paper_1901_02955_gb300 import Context
+    torch.cuda.set_device(local)
+    w = W.density_current(dtype="f64")
+    kappa = (w.gamma_d - 1.0) / w.gamma_d
+    out = {}
+    for dt_name in ("f64", "f32"):
+        ctx = Context(w, dtype=dt_name)
+        ctx.set_state(w.Y)
+        t, n = 0.0, 0
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        while t < 900.0 - 1e-9:
+            dt = min(ctx.compute_dt(), 900.0 - t)
+            ctx.step(1, dt_fixed=dt)
+            t += dt
+            n += 1
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        Y = ctx.get_state()
+        rho = Y[0]
+        p = (w.gamma_d - 1.0) * (Y[3] - 0.5 * (Y[1] ** 2 + Y[2] ** 2) / rho)
+        theta = p / (rho * w.R_d) * (1e5 / p) ** kappa
+        dth = theta - 300.0
+        cold = np.nonzero(dth[0, 0] < -1.0)[0]
+        out[dt_name] = {"max_theta_anomaly_K": float(dth.max()),
+                        "min_theta_anomaly_K": float(dth.min()),
+                        "front_x_m": float((cold.max() + 0.5) * w.dx) if cold.size else 0.0,
+                        "steps": n, "wall_s": wall,
+                        "cell_updates_per_s": w.ncells * 3 * n / wall}
+        ctx.close()
+    line = {"metric": "potential temperature anomaly extrema at 900 s", "unit": "K",
+            "value": out["f64"]["max_theta_anomaly_K"], "higher_is_better": None,
+            "n_gpus": 1, "vs_baseline": None, "data": "synthetic",
+            "config": {"workload": "density_current_1024x256", "t_end_s": 900.0,
+                       "paper_max_anomaly_K": 0.12, "viscosity_m2_s": w.nu,
+                       "note": "wall clock includes one host round trip per step for the CFL "
+                               "time step", "results": out}}
+    print(json.dumps(line), flush=True)
+
+
 def adjoint_workload(args, local):
     """Forward and discrete-adjoint cost of the 2-D warm bubble at 256 x 256 and of its moist
     variant (cloud forming in the core), 400 steps with a checkpoint every 20 steps or with
@@ -499,6 +547,10 @@ def main():
     if args.workload == "bryan_1000s":
         if rank == 0:
             bryan_workload(args, local)
+        return
+    if args.workload == "density_current_900s":
+        if rank == 0:
+            straka_workload(args, local)
         return
     if args.workload != WORKLOAD:
         if args.workload.startswith("ensemble_96"):

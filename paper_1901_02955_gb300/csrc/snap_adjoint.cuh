@@ -783,7 +783,9 @@ __global__ void __launch_bounds__(128) adj_cell_kernel(const AdjArgs a) {
   const R *lo = reinterpret_cast<const R *>(a.lam_out);
   R *ls = reinterpret_cast<R *>(a.lam_s);
   R *ln = reinterpret_cast<R *>(a.lam_n);
-  const R grav = Prof<R>::grav(D), bdt = R(a.b * a.dt), av = R(a.a), bv = R(a.b);
+  // the forward combine is Y^n + b (s1 - Y^n): the weights of Y^n and s1 are 1 - b and b in
+  // the kernel's type, summing to exactly one
+  const R grav = Prof<R>::grav(D), bdt = R(a.b * a.dt), bv = R(a.b), av = R(1) - bv;
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell;
        c += (long long)gridDim.x * blockDim.x) {
     const int i = int(c % nx), j = int((c / nx) % ny), k = int(c / ((long long)nx * ny));
