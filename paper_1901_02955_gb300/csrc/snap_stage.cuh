@@ -367,7 +367,8 @@ __device__ __forceinline__ void lmars(const CstT<R> &C, const R *XL, const R *XR
 // ------------------------------------------------------------------------------------------
 template <class R, class L>
 __device__ __forceinline__ void cell_Tp(const Phys &ph, const R *y, double eref, double &T,
-                                        double &p) {
+                                        double &p, double *Cv_out = nullptr,
+                                        double *Rm_out = nullptr) {
   double rho = 0.0, K2 = 0.0, A = 0.0, Cv = y[0], Rm = y[0];
 #pragma unroll
   for (int s = 0; s < L::IM0; ++s) rho += double(y[s]);
@@ -386,6 +387,8 @@ __device__ __forceinline__ void cell_Tp(const Phys &ph, const R *y, double eref,
   double U = (double(y[L::IE]) + eref) - 0.5 * K2 / rho - A;
   T = U / (Cv * ph.c_vd);
   p = Rm * ph.R_d * T;
+  if (Cv_out) *Cv_out = Cv * ph.c_vd;  // heat capacity at constant volume, J/(m^3 K)
+  if (Rm_out) *Rm_out = Rm;            // sum of the gas densities / molar-mass ratios
 }
 
 template <class R, class L>
@@ -431,16 +434,16 @@ __device__ int satadj_cell(const Phys &ph, const CstT<R> &C, R *y, double eref, 
         if (clear) return 1;
       }
     }
-    double Td = 0.0, pd = 0.0;
-    bool stale = true;  // T and p must be recomputed from the conserved energy
+    // T and p from the conserved energy once, in FP64 (Eq. energy, App. B); after each
+    // transfer they are carried forward in FP64 by the change of the two densities: rho e
+    // and the momenta are fixed, so C_v T + A is, and T' = T - (dA + T dC) / (C_v + dC),
+    // p' = R_d (R_m + dR_m) T' -- exact algebra, no inversion per sweep
+    double Td = 0.0, pd = 0.0, Cvd = 0.0, Rmd = 0.0;
+    cell_Tp<R, L>(ph, y, eref, Td, pd, &Cvd, &Rmd);
     for (int sweep = 1; sweep <= max_iter; ++sweep) {
       bool conv = true;
 #pragma unroll
       for (int i = 0; i < L::NVAP; ++i) {
-        if (stale) {
-          cell_Tp<R, L>(ph, y, eref, Td, pd);
-          stale = false;
-        }
         R T = R(Td), p = R(pd);
         const R dTr = R(Td - ph.Tref[i]);  // T - T^r kept accurate: s(T) is steep
         R N = y[0], gas = y[0], heat = R(0);
@@ -487,9 +490,17 @@ __device__ int satadj_cell(const Phys &ph, const CstT<R> &C, R *y, double eref, 
           drho = dq * C.eps[i] * N;
         }
         if (drho != R(0)) {
+          const R yv = y[1 + i], yc = y[L::cond(i, 0)];
           y[1 + i] -= drho;
           y[L::cond(i, 0)] += drho;
-          stale = true;
+          // the changes as stored (after rounding to the state's type)
+          const double dv = double(y[1 + i]) - double(yv);
+          const double dc = double(y[L::cond(i, 0)]) - double(yc);
+          const double dC = (ph.sig_v[i] * dv + ph.sig_c[i][0] * dc) * ph.c_vd;
+          Td -= (ph.mu[i][0] * dc + Td * dC) / (Cvd + dC);
+          Cvd += dC;
+          Rmd += ph.inv_eps[i] * dv;
+          pd = Rmd * ph.R_d * Td;
         }
         if (fabs(dq) > tol * (qv + qc)) conv = false;
       }
@@ -593,17 +604,25 @@ __device__ __forceinline__ void sediment_flux(const CstT<R> &C, const R *XL, con
 // ------------------------------------------------------------------------------------------
 template <class R, class L>
 __device__ __forceinline__ void kessler_eval(const Phys &ph, const CstT<R> &C, const R *y,
-                                             double eref, int i, R rho, const R *yn, R dt,
+                                             double T0, R Cv0, int i, R rho, const R *yn, R dt,
                                              bool sat, R G[2], R A[2][2], R &s_out,
                                              R &tol_out) {
   const int vi = 1 + i, ci = L::cond(i, 0), ri = L::cond(i, 1);
-  double Td, pd;
-  cell_Tp<R, L>(ph, y, eref, Td, pd);
-  const R T = R(Td), iT = Ar<R>::rcp(T), t = T * C.inv_Tref[i], it = Ar<R>::rcp(t);
-  // T - T^r kept accurate (from the FP64 temperature): rho*(T) is steep, d ln rho*/d ln T ~
-  // beta / t ~ 20 near water's triple point, so T rounded to FP32 alone would put ~1e-6
-  // relative noise into s = rho_v - rho* -- the size of the FP32 Newton stop tolerance
-  const R dTr = R(Td - ph.Tref[i]);
+  // T from T0, the FP64 temperature of the densities yn this vapour started from, and the
+  // phase changes since: rho e and the momenta are fixed, so C_v T + A is (Sec. 2), and
+  // T = T0 - (sum_k mu_k d_k + T0 sum_k c_k d_k) / (C_v0 + sum_k c_k d_k) over the vapour,
+  // cloud and precipitation changes d_k (the vapour's mu is zero) -- no FP64 inversion per
+  // Newton iteration
+  const R dv = y[vi] - yn[0], dc = y[ci] - yn[1], dr = y[ri] - yn[2];
+  const R dC = (C.sig_v[i] * dv + C.sig_c[i][0] * dc + C.sig_c[i][1] * dr) * C.c_vd;
+  const R dA = C.mu[i][0] * dc + C.mu[i][1] * dr;
+  const R incr = -(dA + R(T0) * dC) * Ar<R>::rcp(Cv0 + dC);
+  const R T = R(T0) + incr, iT = Ar<R>::rcp(T), t = T * C.inv_Tref[i], it = Ar<R>::rcp(t);
+  // T - T^r kept accurate (T0 - T^r from the FP64 temperature): rho*(T) is steep,
+  // d ln rho*/d ln T ~ beta / t ~ 20 near water's triple point, so T rounded to FP32 alone
+  // would put ~1e-6 relative noise into s = rho_v - rho* -- the size of the FP32 Newton stop
+  // tolerance
+  const R dTr = R(T0 - ph.Tref[i]) + incr;
   const R arg = C.beta[i] * dTr * iT - C.delta[i] * Ar<R>::log1p_(dTr * C.inv_Tref[i]);
   const R rs = C.pref[i] * Ar<R>::exp_(arg) * C.eps[i] * C.iR_d * iT;  // p* / (R_i T)
   // rho* is held only to ~(|arg| + 2) eps relative: the Newton stop test allows 4 times it
@@ -658,15 +677,15 @@ __device__ __forceinline__ void kessler_eval(const Phys &ph, const CstT<R> &C, c
 
 template <class R, class L>
 __device__ __forceinline__ int kessler_branch(const Phys &ph, const CstT<R> &C, R *y,
-                                              double eref, int i, R rho, const R *yn, R tot,
-                                              R dt, bool sat, R &s) {
+                                              double T0, R Cv0, int i, R rho, const R *yn,
+                                              R tot, R dt, bool sat, R &s) {
   const int vi = 1 + i, ci = L::cond(i, 0), ri = L::cond(i, 1);
   y[vi] = yn[0];
   y[ci] = yn[1];
   y[ri] = yn[2];
   for (int m = 1; m <= ph.kessler_max_iter; ++m) {
     R G[2], A[2][2], tol;
-    kessler_eval<R, L>(ph, C, y, eref, i, rho, yn, dt, sat, G, A, s, tol);
+    kessler_eval<R, L>(ph, C, y, T0, Cv0, i, rho, yn, dt, sat, G, A, s, tol);
     const R idet = Ar<R>::rcp(A[0][0] * A[1][1] - A[0][1] * A[1][0]);
     const R dv = (-G[0] * A[1][1] + G[1] * A[0][1]) * idet;
     const R dc = (-G[1] * A[0][0] + G[0] * A[1][0]) * idet;
@@ -675,7 +694,7 @@ __device__ __forceinline__ int kessler_branch(const Phys &ph, const CstT<R> &C, 
     y[ri] = tot - y[vi] - y[ci];
     if (fabs(dv) + fabs(dc) <= tol * (fabs(y[vi]) + fabs(y[ci]) + fabs(y[ri]))) {
       R Gt[2], At[2][2], tt;
-      kessler_eval<R, L>(ph, C, y, eref, i, rho, yn, dt, sat, Gt, At, s, tt);
+      kessler_eval<R, L>(ph, C, y, T0, Cv0, i, rho, yn, dt, sat, Gt, At, s, tt);
       return m;
     }
   }
@@ -690,19 +709,32 @@ __device__ int kessler_cell(const Phys &ph, const CstT<R> &C, R *y, double eref,
     R rho = R(0);
 #pragma unroll
     for (int s = 0; s < L::IM0; ++s) rho += y[s];
+    // the cell's temperature and heat capacity once in FP64; each vapour then updates them
+    // by its own phase changes
+    double T0, p0, Cv0;
+    cell_Tp<R, L>(ph, y, eref, T0, p0, &Cv0);
     int worst = 0;
     for (int i = 0; i < L::NVAP; ++i) {
       const int vi = 1 + i, ci = L::cond(i, 0), ri = L::cond(i, 1);
       const R yn[3] = {y[vi], y[ci], y[ri]};
       const R tot = yn[0] + yn[1] + yn[2];
       R G[2], A[2][2], s0, s, tol0;
-      kessler_eval<R, L>(ph, C, y, eref, i, rho, yn, dt, true, G, A, s0, tol0);
+      const R cv0 = R(Cv0);
+      kessler_eval<R, L>(ph, C, y, T0, cv0, i, rho, yn, dt, true, G, A, s0, tol0);
       const bool first = s0 > R(0);
-      int it = kessler_branch<R, L>(ph, C, y, eref, i, rho, yn, tot, dt, first, s);
+      int it = kessler_branch<R, L>(ph, C, y, T0, cv0, i, rho, yn, tot, dt, first, s);
       if (!(it > 0 && (first ? s > R(0) : s <= R(0)))) {
-        it = kessler_branch<R, L>(ph, C, y, eref, i, rho, yn, tot, dt, !first, s);
+        it = kessler_branch<R, L>(ph, C, y, T0, cv0, i, rho, yn, tot, dt, !first, s);
         if (!(it > 0 && (!first ? s > R(0) : s <= R(0))))
-          it = kessler_branch<R, L>(ph, C, y, eref, i, rho, yn, tot, dt, true, s);
+          it = kessler_branch<R, L>(ph, C, y, T0, cv0, i, rho, yn, tot, dt, true, s);
+      }
+      {  // this vapour's phase changes, in FP64, carried to the next vapour's T0 and C_v0
+        const double dv = double(y[vi]) - double(yn[0]), dc = double(y[ci]) - double(yn[1]);
+        const double dr = double(y[ri]) - double(yn[2]);
+        const double dC = (ph.sig_v[i] * dv + ph.sig_c[i][0] * dc + ph.sig_c[i][1] * dr) * ph.c_vd;
+        const double dA = ph.mu[i][0] * dc + ph.mu[i][1] * dr;
+        T0 -= (dA + T0 * dC) / (Cv0 + dC);
+        Cv0 += dC;
       }
       if (it < 0)
         worst = -1;
