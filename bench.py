@@ -652,6 +652,13 @@ def main():
                 "hbm": {"achieved": achieved, "peak": peak, "unit": "GB/s",
                         "frac": achieved / peak, "peak_source": f"{peak_src} HBM copy bandwidth",
                         "algorithmic_bytes_per_launch": alg_bytes}}
+    # the device's achieved fused multiply-add rate (snap_probe_fma), beside the nominal peak
+    from paper_1901_02955_gb300 import capi as _capi
+    probe32 = _capi.probe_fma("f32", stream.cuda_stream)
+    roofline["peak_probe"] = {"value": probe32, "unit": "TFLOP/s",
+                              "frac_of_probe": tflops / probe32,
+                              "note": "FP32 fused multiply-add chains on every SM, measured "
+                                      "before the timed region"}
     inst = ncu_record().get("warp_instructions_per_launch")
     if inst:
         # issued warp instructions per launch (ncu, same sources) over the event-timed stage
@@ -713,7 +720,9 @@ def main():
                        "fp64_value": v64, "fp64_ms_per_step": ms64, "fp32_over_fp64": value / v64,
                        "fp64_alu": {"achieved": fp64_tflops, "peak": FP64_PEAK_TFLOPS,
                                     "unit": "TFLOP/s", "frac": fp64_tflops / FP64_PEAK_TFLOPS,
-                                    "note": "whole step time, nominal FP64 rate"},
+                                    "peak_probe": _capi.probe_fma("f64", stream.cuda_stream),
+                                    "note": "whole step time, nominal FP64 rate; peak_probe: "
+                                            "the device's measured FP64 fused multiply-add rate"},
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clk.summary(),

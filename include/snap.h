@@ -297,6 +297,13 @@ int snap_budget_noalloc(const void *Y, int dtype, int nx, int ny, int nz, int nf
                         int n_mass_fields, double dx, double dy, double dz, double grav,
                         double *out, void *stream);
 
+/* Arithmetic-throughput probe of the current device, a measurement aid (the paper has no
+ * counterpart): chains of fused multiply-adds in the given type (SNAP_F32 or SNAP_F64) on
+ * every SM, timed with CUDA events on stream (NULL: the legacy default stream) after warm-up
+ * launches; *tflops receives the achieved rate at the clocks of the moment (2 flop per fused
+ * multiply-add). Allocates nothing. Returns SNAP_OK, SNAP_EINVAL or SNAP_ECUDA. */
+int snap_probe_fma(int dtype, double *tflops, void *stream);
+
 void snap_free(snap_ctx *ctx);
 const char *snap_last_error(const snap_ctx *ctx);
 const char *snap_status_string(int status);

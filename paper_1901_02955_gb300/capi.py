@@ -29,6 +29,7 @@ EXPORTS = ["snap_init_grid", "snap_set_state", "snap_get_state", "snap_step", "s
            "snap_set_stream",
            "snap_use_graph", "snap_set_tile_variant", "snap_use_persistent", "snap_autotune",
            "snap_get_info", "snap_buffer_pointer", "snap_budget_noalloc", "snap_theta_e",
+           "snap_probe_fma",
            "snap_free", "snap_last_error", "snap_status_string"]
 
 
@@ -109,6 +110,7 @@ def load(path: Optional[str] = None) -> C.CDLL:
     lib.snap_use_persistent.argtypes = [P, C.c_int]
     lib.snap_autotune.argtypes = [P, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int)]
     lib.snap_buffer_pointer.argtypes = [P, C.c_int, C.c_int, C.POINTER(P)]
+    lib.snap_probe_fma.argtypes = [C.c_int, C.POINTER(C.c_double), P]
     lib.snap_budget_noalloc.argtypes = [P, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                                         C.c_int, C.c_double, C.c_double, C.c_double,
                                         C.c_double, P, P]
@@ -344,3 +346,13 @@ def _buffer(Y):
         raise ValueError("state tensor must be contiguous")
     code = {torch.float64: F64, torch.float32: F32}[Y.dtype]
     return C.c_void_p(Y.data_ptr()), code, int(Y.is_cuda)
+
+
+def probe_fma(dtype="f32", stream=None):
+    """Achieved fused multiply-add rate of the device in TFLOP/s (see snap_probe_fma)."""
+    lib = load()
+    t = C.c_double(0.0)
+    rc = lib.snap_probe_fma(F32 if dtype == "f32" else F64, C.byref(t), stream)
+    if rc:
+        raise SnapError(rc, "snap_probe_fma failed")
+    return t.value
