@@ -806,21 +806,27 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_al
 // triple is read in, so the three indicators (and their inverse squares) serve both faces; the
 // mirror stencil takes them in reverse order. The linear weights are folded into the
 // candidate coefficients, so each face needs one normalising reciprocal.
+// Common factors cancel in a face's normalisation sum_k w_k q_k / sum_k w_k, so the kernel
+// takes (a) every eps + beta_k times 12/13: beta_k = 13/12 s^2 + 1/4 r^2 becomes s^2 + 3/13 r^2
+// (three operations instead of four) against eps 12/13; (b) the linear weights (0.1, 0.6, 0.3)
+// times 10: each normalisation g0 + 6 g1 + 3 g2 is two fused multiply-adds.
 template <class R>
 __device__ __forceinline__ void weno5_pair(R a, R b, R c, R d, R e, R eps, R &qm, R &qp) {
+  constexpr R k3 = R(3.0 / 13.0);
   R t;
   t = a - R(2) * b + c;
-  R b0 = R(13.0 / 12.0) * t * t;
+  R b0 = t * t;
   t = a - R(4) * b + R(3) * c;
-  b0 += R(0.25) * t * t;
+  b0 += (k3 * t) * t;
   t = b - R(2) * c + d;
-  R b1 = R(13.0 / 12.0) * t * t;
+  R b1 = t * t;
   t = b - d;
-  b1 += R(0.25) * t * t;
+  b1 += (k3 * t) * t;
   t = c - R(2) * d + e;
-  R b2 = R(13.0 / 12.0) * t * t;
+  R b2 = t * t;
   t = R(3) * c - R(4) * d + e;
-  b2 += R(0.25) * t * t;
+  b2 += (k3 * t) * t;
+  eps *= R(12.0 / 13.0);
   // inverse squares 1 / (eps + beta_k)^2, shared by both faces. FP64 (whose reciprocal is a
   // multi-instruction sequence on a slow pipe) forms them up to the common factor
   // 1 / (e0 e1 e2)^2, which cancels in each face's normalisation: g_k = (product of the other
@@ -839,17 +845,17 @@ __device__ __forceinline__ void weno5_pair(R a, R b, R c, R d, R e, R eps, R &qm
   g0 *= g0;
   g1 *= g1;
   g2 *= g2;
-  // linear weight times the candidate interpolant of Eq. weno5: (0.1, 0.6, 0.3) x
+  // ten times the linear weight times the candidate interpolant of Eq. weno5: (1, 6, 3) x
   // (1/3, -7/6, 11/6), (-1/6, 5/6, 1/3), (1/3, 5/6, -1/6); the right state reads the window
   // backwards and takes the weights in reverse order
-  const R m0 = R(0.1 / 3.0) * a - R(0.7 / 6.0) * b + R(1.1 / 6.0) * c;
-  const R m1 = R(-0.1) * b + R(0.5) * c + R(0.2) * d;
-  const R m2 = R(0.1) * c + R(0.25) * d - R(0.05) * e;
-  const R p0 = R(0.1 / 3.0) * e - R(0.7 / 6.0) * d + R(1.1 / 6.0) * c;
-  const R p1 = R(-0.1) * d + R(0.5) * c + R(0.2) * b;
-  const R p2 = R(0.1) * c + R(0.25) * b - R(0.05) * a;
-  const R Sm = R(0.1) * g0 + R(0.6) * g1 + R(0.3) * g2;
-  const R Sp = R(0.1) * g2 + R(0.6) * g1 + R(0.3) * g0;
+  const R m0 = R(1.0 / 3.0) * a - R(7.0 / 6.0) * b + R(11.0 / 6.0) * c;
+  const R m1 = R(5) * c + R(2) * d - b;
+  const R m2 = c + R(2.5) * d - R(0.5) * e;
+  const R p0 = R(1.0 / 3.0) * e - R(7.0 / 6.0) * d + R(11.0 / 6.0) * c;
+  const R p1 = R(5) * c + R(2) * b - d;
+  const R p2 = c + R(2.5) * b - R(0.5) * a;
+  const R Sm = g0 + R(6) * g1 + R(3) * g2;
+  const R Sp = g2 + R(6) * g1 + R(3) * g0;
   const R Nm = g0 * m0 + g1 * m1 + g2 * m2, Np = g2 * p0 + g1 * p1 + g0 * p2;
   if constexpr (sizeof(R) == 8) {
     // 1/Sm = Sp / (Sm Sp) and 1/Sp = Sm / (Sm Sp); one division each only if the product
@@ -877,35 +883,36 @@ __device__ __forceinline__ float2 f2rcp(float2 x) {
 }
 __device__ __forceinline__ void weno5_pair2(float2 a, float2 b, float2 c, float2 d, float2 e,
                                             float eps, float2 &qm, float2 &qp) {
-  const float2 k1312 = f2c(13.0f / 12.0f), kq = f2c(0.25f);
+  // the scaled indicators and weights of weno5_pair: beta_k 12/13 times, weights 10 times
+  const float2 k3 = f2c(3.0f / 13.0f);
   float2 t = __ffma2_rn(f2c(-2.0f), b, __fadd2_rn(a, c));
-  float2 b0 = __fmul2_rn(__fmul2_rn(k1312, t), t);
+  float2 b0 = __fmul2_rn(t, t);
   t = __ffma2_rn(f2c(-4.0f), b, __ffma2_rn(f2c(3.0f), c, a));
-  b0 = __ffma2_rn(__fmul2_rn(kq, t), t, b0);
+  b0 = __ffma2_rn(__fmul2_rn(k3, t), t, b0);
   t = __ffma2_rn(f2c(-2.0f), c, __fadd2_rn(b, d));
-  float2 b1 = __fmul2_rn(__fmul2_rn(k1312, t), t);
+  float2 b1 = __fmul2_rn(t, t);
   t = __ffma2_rn(f2c(-1.0f), d, b);
-  b1 = __ffma2_rn(__fmul2_rn(kq, t), t, b1);
+  b1 = __ffma2_rn(__fmul2_rn(k3, t), t, b1);
   t = __ffma2_rn(f2c(-2.0f), d, __fadd2_rn(c, e));
-  float2 b2 = __fmul2_rn(__fmul2_rn(k1312, t), t);
+  float2 b2 = __fmul2_rn(t, t);
   t = __ffma2_rn(f2c(3.0f), c, __ffma2_rn(f2c(-4.0f), d, e));
-  b2 = __ffma2_rn(__fmul2_rn(kq, t), t, b2);
-  const float2 ke = f2c(eps);
+  b2 = __ffma2_rn(__fmul2_rn(k3, t), t, b2);
+  const float2 ke = f2c(eps * (12.0f / 13.0f));
   float2 g0 = f2rcp(__fadd2_rn(ke, b0)), g1 = f2rcp(__fadd2_rn(ke, b1)),
          g2 = f2rcp(__fadd2_rn(ke, b2));
   g0 = __fmul2_rn(g0, g0);
   g1 = __fmul2_rn(g1, g1);
   g2 = __fmul2_rn(g2, g2);
-  const float2 m0 = __ffma2_rn(f2c(0.1f / 3.0f), a,
-                               __ffma2_rn(f2c(-0.7f / 6.0f), b, __fmul2_rn(f2c(1.1f / 6.0f), c)));
-  const float2 m1 = __ffma2_rn(f2c(-0.1f), b, __ffma2_rn(f2c(0.5f), c, __fmul2_rn(f2c(0.2f), d)));
-  const float2 m2 = __ffma2_rn(f2c(0.1f), c, __ffma2_rn(f2c(0.25f), d, __fmul2_rn(f2c(-0.05f), e)));
-  const float2 p0 = __ffma2_rn(f2c(0.1f / 3.0f), e,
-                               __ffma2_rn(f2c(-0.7f / 6.0f), d, __fmul2_rn(f2c(1.1f / 6.0f), c)));
-  const float2 p1 = __ffma2_rn(f2c(-0.1f), d, __ffma2_rn(f2c(0.5f), c, __fmul2_rn(f2c(0.2f), b)));
-  const float2 p2 = __ffma2_rn(f2c(0.1f), c, __ffma2_rn(f2c(0.25f), b, __fmul2_rn(f2c(-0.05f), a)));
-  const float2 Sm = __ffma2_rn(f2c(0.1f), g0, __ffma2_rn(f2c(0.6f), g1, __fmul2_rn(f2c(0.3f), g2)));
-  const float2 Sp = __ffma2_rn(f2c(0.1f), g2, __ffma2_rn(f2c(0.6f), g1, __fmul2_rn(f2c(0.3f), g0)));
+  const float2 m0 = __ffma2_rn(f2c(1.0f / 3.0f), a,
+                               __ffma2_rn(f2c(-7.0f / 6.0f), b, __fmul2_rn(f2c(11.0f / 6.0f), c)));
+  const float2 m1 = __ffma2_rn(f2c(-1.0f), b, __ffma2_rn(f2c(5.0f), c, __fmul2_rn(f2c(2.0f), d)));
+  const float2 m2 = __ffma2_rn(f2c(2.5f), d, __ffma2_rn(f2c(-0.5f), e, c));
+  const float2 p0 = __ffma2_rn(f2c(1.0f / 3.0f), e,
+                               __ffma2_rn(f2c(-7.0f / 6.0f), d, __fmul2_rn(f2c(11.0f / 6.0f), c)));
+  const float2 p1 = __ffma2_rn(f2c(-1.0f), d, __ffma2_rn(f2c(5.0f), c, __fmul2_rn(f2c(2.0f), b)));
+  const float2 p2 = __ffma2_rn(f2c(2.5f), b, __ffma2_rn(f2c(-0.5f), a, c));
+  const float2 Sm = __ffma2_rn(f2c(3.0f), g2, __ffma2_rn(f2c(6.0f), g1, g0));
+  const float2 Sp = __ffma2_rn(f2c(3.0f), g0, __ffma2_rn(f2c(6.0f), g1, g2));
   const float2 nm = __ffma2_rn(g0, m0, __ffma2_rn(g1, m1, __fmul2_rn(g2, m2)));
   const float2 np = __ffma2_rn(g2, p0, __ffma2_rn(g1, p1, __fmul2_rn(g0, p2)));
   qm = __fmul2_rn(nm, f2rcp(Sm));
