@@ -26,6 +26,9 @@ template <class R>
 struct Ar;
 template <>
 struct Ar<float> {
+  // a b + c rounded once, whatever the compiler would contract: the same source then rounds
+  // the same way in every kernel it is inlined into
+  static __device__ __forceinline__ float fma_(float a, float b, float c) { return __fmaf_rn(a, b, c); }
   // approximate reciprocal (hardware rcp, ~1 ulp) -- FP32 path only
   static __device__ __forceinline__ float rcp(float x) { return __fdividef(1.0f, x); }
   static __device__ __forceinline__ float div(float a, float b) { return __fdividef(a, b); }
@@ -47,6 +50,7 @@ struct Ar<float> {
 };
 template <>
 struct Ar<double> {
+  static __device__ __forceinline__ double fma_(double a, double b, double c) { return __fma_rn(a, b, c); }
   // Reciprocal by Newton-Raphson iteration y <- y + y (1 - x y), which squares the relative
   // error at each step, from the hardware's approximate FP64 reciprocal (rcp.approx.ftz.f64,
   // about 1e-6): two steps reach the last bit (equal to the IEEE quotient on a million random
@@ -809,23 +813,30 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_al
 // Common factors cancel in a face's normalisation sum_k w_k q_k / sum_k w_k, so the kernel
 // takes (a) every eps + beta_k times 12/13: beta_k = 13/12 s^2 + 1/4 r^2 becomes s^2 + 3/13 r^2
 // (three operations instead of four) against eps 12/13; (b) the linear weights (0.1, 0.6, 0.3)
-// times 10: each normalisation g0 + 6 g1 + 3 g2 is two fused multiply-adds.
+// times 10: each normalisation g0 + 6 g1 + 3 g2 is two fused multiply-adds. And since the
+// weights sum to the normalisation, a face state is c + sum_k w_k (q_k - c) / sum_k w_k, where
+// each offset q_k - c is a short combination of the neighbour differences u = c - b,
+// v = d - c, w = b - a, z = e - d, which also give the indicators' stencils.
 template <class R>
 __device__ __forceinline__ void weno5_pair(R a, R b, R c, R d, R e, R eps, R &qm, R &qp) {
+  // every multiply-add below is an explicit fused one (Ar::fma_), so that each kernel
+  // instantiation rounds the same way whatever its register allocation
+  using A = Ar<R>;
   constexpr R k3 = R(3.0 / 13.0);
+  const R u = c - b, v = d - c, w = b - a, z = e - d;
   R t;
-  t = a - R(2) * b + c;
+  t = u - w;  // a - 2b + c
   R b0 = t * t;
-  t = a - R(4) * b + R(3) * c;
-  b0 += (k3 * t) * t;
-  t = b - R(2) * c + d;
+  t = A::fma_(R(3), u, -w);  // a - 4b + 3c
+  b0 = A::fma_(k3 * t, t, b0);
+  t = v - u;  // b - 2c + d
   R b1 = t * t;
-  t = b - d;
-  b1 += (k3 * t) * t;
-  t = c - R(2) * d + e;
+  const R bd = b - d;
+  b1 = A::fma_(k3 * bd, bd, b1);
+  t = z - v;  // c - 2d + e
   R b2 = t * t;
-  t = R(3) * c - R(4) * d + e;
-  b2 += (k3 * t) * t;
+  t = A::fma_(R(-3), v, z);  // 3c - 4d + e
+  b2 = A::fma_(k3 * t, t, b2);
   eps *= R(12.0 / 13.0);
   // inverse squares 1 / (eps + beta_k)^2, shared by both faces. FP64 (whose reciprocal is a
   // multi-instruction sequence on a slow pipe) forms them up to the common factor
@@ -838,39 +849,41 @@ __device__ __forceinline__ void weno5_pair(R a, R b, R c, R d, R e, R eps, R &qm
     g1 = e0 * e2;
     g2 = e0 * e1;
   } else {
-    g0 = Ar<R>::rcp(eps + b0);
-    g1 = Ar<R>::rcp(eps + b1);
-    g2 = Ar<R>::rcp(eps + b2);
+    g0 = A::rcp(eps + b0);
+    g1 = A::rcp(eps + b1);
+    g2 = A::rcp(eps + b2);
   }
   g0 *= g0;
   g1 *= g1;
   g2 *= g2;
-  // ten times the linear weight times the candidate interpolant of Eq. weno5: (1, 6, 3) x
-  // (1/3, -7/6, 11/6), (-1/6, 5/6, 1/3), (1/3, 5/6, -1/6); the right state reads the window
-  // backwards and takes the weights in reverse order
-  const R m0 = R(1.0 / 3.0) * a - R(7.0 / 6.0) * b + R(11.0 / 6.0) * c;
-  const R m1 = R(5) * c + R(2) * d - b;
-  const R m2 = c + R(2.5) * d - R(0.5) * e;
-  const R p0 = R(1.0 / 3.0) * e - R(7.0 / 6.0) * d + R(11.0 / 6.0) * c;
-  const R p1 = R(5) * c + R(2) * b - d;
-  const R p2 = c + R(2.5) * b - R(0.5) * a;
-  const R Sm = g0 + R(6) * g1 + R(3) * g2;
-  const R Sp = g2 + R(6) * g1 + R(3) * g0;
-  const R Nm = g0 * m0 + g1 * m1 + g2 * m2, Np = g2 * p0 + g1 * p1 + g0 * p2;
+  // ten times the linear weight, (1, 6, 3), times the candidate interpolant of Eq. weno5 less
+  // c: (1/3, -7/6, 11/6) - c = 5/6 u - 1/3 w; (-1/6, 5/6, 1/3) - c = 1/6 u + 1/3 v;
+  // (1/3, 5/6, -1/6) - c = 2/3 v - 1/6 z. The right state reads the window backwards (u, v, w,
+  // z become -v, -u, -z, -w) and takes the weights in reverse order.
+  const R m0 = A::fma_(R(5.0 / 6.0), u, R(-1.0 / 3.0) * w);
+  const R m1 = A::fma_(R(2), v, u);
+  const R m2 = A::fma_(R(2), v, R(-0.5) * z);
+  const R p0 = A::fma_(R(-5.0 / 6.0), v, R(1.0 / 3.0) * z);
+  const R p1 = bd - u;  // -v - 2u
+  const R p2 = A::fma_(R(-2), u, R(0.5) * w);
+  const R Sm = A::fma_(R(3), g2, A::fma_(R(6), g1, g0));
+  const R Sp = A::fma_(R(3), g0, A::fma_(R(6), g1, g2));
+  const R Nm = A::fma_(g0, m0, A::fma_(g1, m1, g2 * m2));
+  const R Np = A::fma_(g2, p0, A::fma_(g1, p1, g0 * p2));
   if constexpr (sizeof(R) == 8) {
     // 1/Sm = Sp / (Sm Sp) and 1/Sp = Sm / (Sm Sp); one division each only if the product
     // leaves the exponent range (g ~ e^4, so Sm Sp ~ e^8: eps far below 1e-6 or huge beta)
-    const R Z = Ar<R>::rcp(Sm * Sp);  // NaN outside the normal range: the test below fails
+    const R Z = A::rcp(Sm * Sp);  // NaN outside the normal range: the test below fails
     if (Z > R(0) && Z < R(INFINITY)) {
-      qm = Nm * (Sp * Z);
-      qp = Np * (Sm * Z);
+      qm = A::fma_(Nm, Sp * Z, c);
+      qp = A::fma_(Np, Sm * Z, c);
     } else {
-      qm = Nm / Sm;
-      qp = Np / Sp;
+      qm = c + Nm / Sm;
+      qp = c + Np / Sp;
     }
   } else {
-    qm = Nm * Ar<R>::rcp(Sm);
-    qp = Np * Ar<R>::rcp(Sp);
+    qm = A::fma_(Nm, A::rcp(Sm), c);
+    qp = A::fma_(Np, A::rcp(Sp), c);
   }
 }
 
@@ -883,19 +896,21 @@ __device__ __forceinline__ float2 f2rcp(float2 x) {
 }
 __device__ __forceinline__ void weno5_pair2(float2 a, float2 b, float2 c, float2 d, float2 e,
                                             float eps, float2 &qm, float2 &qp) {
-  // the scaled indicators and weights of weno5_pair: beta_k 12/13 times, weights 10 times
-  const float2 k3 = f2c(3.0f / 13.0f);
-  float2 t = __ffma2_rn(f2c(-2.0f), b, __fadd2_rn(a, c));
+  // the scaled indicators and weights and the difference form of weno5_pair
+  const float2 k3 = f2c(3.0f / 13.0f), m1f = f2c(-1.0f);
+  const float2 u = __ffma2_rn(m1f, b, c), v = __ffma2_rn(m1f, c, d), w = __ffma2_rn(m1f, a, b),
+               z = __ffma2_rn(m1f, d, e);
+  float2 t = __ffma2_rn(m1f, w, u);  // a - 2b + c
   float2 b0 = __fmul2_rn(t, t);
-  t = __ffma2_rn(f2c(-4.0f), b, __ffma2_rn(f2c(3.0f), c, a));
+  t = __ffma2_rn(f2c(3.0f), u, __fmul2_rn(m1f, w));  // a - 4b + 3c
   b0 = __ffma2_rn(__fmul2_rn(k3, t), t, b0);
-  t = __ffma2_rn(f2c(-2.0f), c, __fadd2_rn(b, d));
+  t = __ffma2_rn(m1f, u, v);  // b - 2c + d
   float2 b1 = __fmul2_rn(t, t);
-  t = __ffma2_rn(f2c(-1.0f), d, b);
-  b1 = __ffma2_rn(__fmul2_rn(k3, t), t, b1);
-  t = __ffma2_rn(f2c(-2.0f), d, __fadd2_rn(c, e));
+  const float2 bd = __ffma2_rn(m1f, d, b);  // b - d
+  b1 = __ffma2_rn(__fmul2_rn(k3, bd), bd, b1);
+  t = __ffma2_rn(m1f, v, z);  // c - 2d + e
   float2 b2 = __fmul2_rn(t, t);
-  t = __ffma2_rn(f2c(3.0f), c, __ffma2_rn(f2c(-4.0f), d, e));
+  t = __ffma2_rn(f2c(-3.0f), v, z);  // 3c - 4d + e
   b2 = __ffma2_rn(__fmul2_rn(k3, t), t, b2);
   const float2 ke = f2c(eps * (12.0f / 13.0f));
   float2 g0 = f2rcp(__fadd2_rn(ke, b0)), g1 = f2rcp(__fadd2_rn(ke, b1)),
@@ -903,20 +918,18 @@ __device__ __forceinline__ void weno5_pair2(float2 a, float2 b, float2 c, float2
   g0 = __fmul2_rn(g0, g0);
   g1 = __fmul2_rn(g1, g1);
   g2 = __fmul2_rn(g2, g2);
-  const float2 m0 = __ffma2_rn(f2c(1.0f / 3.0f), a,
-                               __ffma2_rn(f2c(-7.0f / 6.0f), b, __fmul2_rn(f2c(11.0f / 6.0f), c)));
-  const float2 m1 = __ffma2_rn(f2c(-1.0f), b, __ffma2_rn(f2c(5.0f), c, __fmul2_rn(f2c(2.0f), d)));
-  const float2 m2 = __ffma2_rn(f2c(2.5f), d, __ffma2_rn(f2c(-0.5f), e, c));
-  const float2 p0 = __ffma2_rn(f2c(1.0f / 3.0f), e,
-                               __ffma2_rn(f2c(-7.0f / 6.0f), d, __fmul2_rn(f2c(11.0f / 6.0f), c)));
-  const float2 p1 = __ffma2_rn(f2c(-1.0f), d, __ffma2_rn(f2c(5.0f), c, __fmul2_rn(f2c(2.0f), b)));
-  const float2 p2 = __ffma2_rn(f2c(2.5f), b, __ffma2_rn(f2c(-0.5f), a, c));
+  const float2 m0 = __ffma2_rn(f2c(5.0f / 6.0f), u, __fmul2_rn(f2c(-1.0f / 3.0f), w));
+  const float2 m1 = __ffma2_rn(f2c(2.0f), v, u);
+  const float2 m2 = __ffma2_rn(f2c(2.0f), v, __fmul2_rn(f2c(-0.5f), z));
+  const float2 p0 = __ffma2_rn(f2c(-5.0f / 6.0f), v, __fmul2_rn(f2c(1.0f / 3.0f), z));
+  const float2 p1 = __ffma2_rn(m1f, u, bd);  // -v - 2u = (b - d) - u
+  const float2 p2 = __ffma2_rn(f2c(-2.0f), u, __fmul2_rn(f2c(0.5f), w));
   const float2 Sm = __ffma2_rn(f2c(3.0f), g2, __ffma2_rn(f2c(6.0f), g1, g0));
   const float2 Sp = __ffma2_rn(f2c(3.0f), g0, __ffma2_rn(f2c(6.0f), g1, g2));
   const float2 nm = __ffma2_rn(g0, m0, __ffma2_rn(g1, m1, __fmul2_rn(g2, m2)));
   const float2 np = __ffma2_rn(g2, p0, __ffma2_rn(g1, p1, __fmul2_rn(g0, p2)));
-  qm = __fmul2_rn(nm, f2rcp(Sm));
-  qp = __fmul2_rn(np, f2rcp(Sp));
+  qm = __ffma2_rn(nm, f2rcp(Sm), c);
+  qp = __ffma2_rn(np, f2rcp(Sp), c);
 }
 
 // CFL rate sum_d (|u_d| + c) / dx_d in the kernel's type (FP32 kernels: FP32; the time step
