@@ -304,6 +304,25 @@ int snap_budget_noalloc(const void *Y, int dtype, int nx, int ny, int nz, int nf
  * multiply-add). Allocates nothing. Returns SNAP_OK, SNAP_EINVAL or SNAP_ECUDA. */
 int snap_probe_fma(int dtype, double *tflops, void *stream);
 
+/* Arithmetic self-checks, test aids that run pieces of the stage kernels on given arguments.
+ * All pointers are device (or device-mapped) memory owned by the caller; the kernels run
+ * asynchronously on stream. Allocate nothing. Return SNAP_OK, SNAP_EINVAL (a NULL pointer
+ * with n > 0, n < 0, an unknown dtype, or a packed check that is not SNAP_F32 with n even)
+ * or SNAP_ECUDA (launch failure).
+ *
+ * snap_check_rcp64: for the n doubles x, y[2i] = the FP64 kernels' reciprocal of x[i]
+ * (Newton-Raphson from the approximate hardware reciprocal) and y[2i+1] = 1.0 / x[i] by IEEE
+ * division.
+ *
+ * snap_check_weno: n windows of five values (a, b, c, d, e) = (Q_{c-2} .. Q_{c+2}) of the given
+ * dtype, laid out [n][5]; out [n][2] receives the kernels' WENO5 states of Sec. 4.2 (Eq. weno5
+ * with the Jiang-Shu indicators and the given eps): the left state at face c+1/2 and the
+ * right state at face c-1/2. packed = 1 (SNAP_F32, n even) runs windows 2p and 2p+1 through
+ * the packed two-variable form the FP32 kernels use for pairs of variables. */
+int snap_check_rcp64(const double *x, double *y, long long n, void *stream);
+int snap_check_weno(int dtype, int packed, const void *win, void *out, long long n, double eps,
+                    void *stream);
+
 void snap_free(snap_ctx *ctx);
 const char *snap_last_error(const snap_ctx *ctx);
 const char *snap_status_string(int status);

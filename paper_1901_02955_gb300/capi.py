@@ -29,7 +29,7 @@ EXPORTS = ["snap_init_grid", "snap_set_state", "snap_get_state", "snap_step", "s
            "snap_set_stream",
            "snap_use_graph", "snap_set_tile_variant", "snap_use_persistent", "snap_autotune",
            "snap_get_info", "snap_buffer_pointer", "snap_budget_noalloc", "snap_theta_e",
-           "snap_probe_fma",
+           "snap_probe_fma", "snap_check_rcp64", "snap_check_weno",
            "snap_free", "snap_last_error", "snap_status_string"]
 
 
@@ -111,6 +111,8 @@ def load(path: Optional[str] = None) -> C.CDLL:
     lib.snap_autotune.argtypes = [P, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int)]
     lib.snap_buffer_pointer.argtypes = [P, C.c_int, C.c_int, C.POINTER(P)]
     lib.snap_probe_fma.argtypes = [C.c_int, C.POINTER(C.c_double), P]
+    lib.snap_check_rcp64.argtypes = [P, P, C.c_longlong, P]
+    lib.snap_check_weno.argtypes = [C.c_int, C.c_int, P, P, C.c_longlong, C.c_double, P]
     lib.snap_budget_noalloc.argtypes = [P, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                                         C.c_int, C.c_double, C.c_double, C.c_double,
                                         C.c_double, P, P]
@@ -346,6 +348,23 @@ def _buffer(Y):
         raise ValueError("state tensor must be contiguous")
     code = {torch.float64: F64, torch.float32: F32}[Y.dtype]
     return C.c_void_p(Y.data_ptr()), code, int(Y.is_cuda)
+
+
+def check_rcp64(x_ptr, y_ptr, n, stream=None):
+    """Device pointers: y[2i] = the FP64 kernels' reciprocal of x[i], y[2i+1] = 1 / x[i]
+    (see snap_check_rcp64)."""
+    rc = load().snap_check_rcp64(x_ptr, y_ptr, n, stream)
+    if rc:
+        raise SnapError(rc, "snap_check_rcp64 failed")
+
+
+def check_weno(dtype, packed, win_ptr, out_ptr, n, eps, stream=None):
+    """Device pointers: the kernels' WENO5 face states of n five-value windows (see
+    snap_check_weno)."""
+    rc = load().snap_check_weno(F32 if dtype == "f32" else F64, int(packed), win_ptr, out_ptr,
+                                n, eps, stream)
+    if rc:
+        raise SnapError(rc, "snap_check_weno failed")
 
 
 def probe_fma(dtype="f32", stream=None):
