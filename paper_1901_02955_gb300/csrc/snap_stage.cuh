@@ -1104,10 +1104,11 @@ __device__ __forceinline__ void stage_tiles(const StageArgs &a, const int stage,
     {
       constexpr int NHX = 6 * TY * TZ, NHY = L::D3 ? 6 * TX * TZ : 0, NHZ = 6 * TX * TY;
       for (int h = tid; h < NHX + NHY + NHZ; h += NT) {
-        int bx, by, bz, dirn;
+        int bx, by, bz, dirn, layer;
         bool ok;
         if (h < NHX) {
           const int r = h % 6, q = h / 6, ly = q % TY, lz = q / TY;
+          layer = r;
           ok = ly < ey && lz < ez;
           bx = r < 3 ? r : ex + r;
           by = ly + B::HY;
@@ -1115,6 +1116,7 @@ __device__ __forceinline__ void stage_tiles(const StageArgs &a, const int stage,
           dirn = 0;
         } else if (h < NHX + NHY) {
           const int hh = h - NHX, lx = hh % TX, r = (hh / TX) % 6, lz = hh / (6 * TX);
+          layer = r;
           ok = lx < ex && lz < ez;
           bx = lx + 3;
           by = r < 3 ? r : ey + r;
@@ -1122,6 +1124,7 @@ __device__ __forceinline__ void stage_tiles(const StageArgs &a, const int stage,
           dirn = 1;
         } else {
           const int hh = h - NHX - NHY, lx = hh % TX, ly = (hh / TX) % TY, r = hh / (TX * TY);
+          layer = r;
           ok = lx < ex && ly < ey;
           bx = lx + 3;
           by = ly + B::HY;
@@ -1161,10 +1164,14 @@ __device__ __forceinline__ void stage_tiles(const StageArgs &a, const int stage,
         const int bi = B::idx(bx, by, bz);
 #pragma unroll
         for (int v = 0; v < NV; ++v) s_prim[v * B::NSTORE + bi] = x[v];
+        // the viscous heat flux reads theta and the Exner function only on the two sides of
+        // a face, so of the halo only the ring next to the tile (layers 2 and 3) needs them
         if constexpr (VISC) {
-          const R Pi = Ar<R>::pow_small(pt * R(1e-5), C.kappa);
-          s_th[bi] = pt * Ar<R>::rcp(x[0] * Pi) * C.iR_d;
-          s_pi[bi] = Pi;
+          if (layer == 2 || layer == 3) {
+            const R Pi = Ar<R>::pow_small(pt * R(1e-5), C.kappa);
+            s_th[bi] = pt * Ar<R>::rcp(x[0] * Pi) * C.iR_d;
+            s_pi[bi] = Pi;
+          }
         }
       }
     }
