@@ -44,8 +44,12 @@ typedef enum snap_status {
 /* Boundary of one side of a domain. SNAP_REFLECT: free-slip wall (ghost cells mirror the
  * state with the normal velocity negated). SNAP_PERIODIC: wrap (both opposite sides).
  * SNAP_NOSLIP: no-slip wall (ghost cells mirror the state with every velocity component
- * negated; Sec. 6 puts one at the bottom of the Jovian simulation). */
-enum { SNAP_REFLECT = 0, SNAP_PERIODIC = 1, SNAP_NOSLIP = 2 };
+ * negated; Sec. 6 puts one at the bottom of the Jovian simulation). SNAP_HALO (x sides only):
+ * the domain is one slab of a larger domain split along x, and the side's three ghost columns
+ * are the neighbouring slab's cells, exchanged before every Runge-Kutta stage (the domain
+ * decomposition over which Athena++, the paper's framework, parallelises a grid; see
+ * snap_link_halo, snap_halo_buffer and snap_halo_pack). */
+enum { SNAP_REFLECT = 0, SNAP_PERIODIC = 1, SNAP_NOSLIP = 2, SNAP_HALO = 3 };
 enum { SNAP_F64 = 0, SNAP_F32 = 1 };
 
 /* One condensable vapour i and its condensates (i,j); j = 0 is the cloud that exchanges mass
@@ -64,8 +68,8 @@ typedef struct snap_grid_desc {
   int nx, ny, nz;          /* cells; ny == 1: x-z plane. Each active extent >= 3 */
   double dx, dy, dz;       /* cell sizes, m (dy ignored when ny == 1) */
   int bc[6];               /* x-, x+, y-, y+, z-, z+ : SNAP_REFLECT, SNAP_PERIODIC or
-                              SNAP_NOSLIP; z must be walls; a periodic side needs its
-                              opposite side periodic */
+                              SNAP_NOSLIP, or SNAP_HALO on an x side; z must be walls; a
+                              periodic side needs its opposite side periodic */
   double grav;             /* gravitational acceleration, m/s^2 (along -z) */
   double gamma_d;          /* c_p,d / c_v,d of the dry gas */
   double R_d;              /* dry-gas constant, J/(kg K) */
@@ -238,15 +242,29 @@ int snap_use_graph(snap_ctx *ctx, int enable);
  * spreads over every SM. Domains are re-tiled; results do not depend on the shape. */
 int snap_set_tile_variant(snap_ctx *ctx, int variant);
 
-/* 1: each step is one persistent cooperative launch whose CTAs (all co-resident) walk the tile
- * queue of every domain and meet at a grid barrier between the three stages; every barrier
- * wait is bounded (about 2 s) and reports SNAP_ETIMEOUT instead of hanging. 0 (default):
- * three launches per step. */
+/* Launch mode of a step. 0 (default): three launches per step, one per stage. 1: one
+ * persistent cooperative launch whose CTAs (all co-resident) walk the tile queue of every
+ * domain and meet at a grid barrier between the three stages. 2: the resident step, for grids
+ * whose tiles are all co-resident at once (SNAP_ENOTSUP otherwise, or with SNAP_HALO sides):
+ * one cooperative launch with one tile per CTA; each CTA keeps its tile's state on chip
+ * through the three stages and, between stages, waits only for the tiles its ghost cells
+ * come from (a flag per tile) instead of for the whole grid. Every device-side wait of modes
+ * 1 and 2 is bounded (about 2 s) and reports SNAP_ETIMEOUT instead of hanging. Results are
+ * the same in every mode. */
 int snap_use_persistent(snap_ctx *ctx, int enable);
 
+/* Test aid for the persistent step's grid barrier (the paper has no counterpart): each wait
+ * spins at most spin_cycles SM clock cycles (0 restores the default, about 2 s) and CTA
+ * absent_cta (-1: none) neither arrives at nor waits on the barriers, so that every other
+ * CTA's wait runs out and the step reports SNAP_ETIMEOUT through snap_check / snap_step
+ * instead of hanging. The results of such a step are not meaningful; every persistent
+ * launch starts from a cleared barrier, so the next normal step is unaffected. Takes effect
+ * from the next step (a captured graph is rebuilt). */
+int snap_set_barrier_test(snap_ctx *ctx, long long spin_cycles, int absent_cta);
 /* Autotuner: times `steps` steps of every tile shape in both launch modes on the current
  * state (which is restored afterwards) and keeps the fastest. best_ms (may be NULL) receives
- * its time per step, choice (may be NULL) variant * 2 + persistent. Allocates one temporary
+ * its time per step, choice (may be NULL) variant * 3 + launch mode (snap_use_persistent).
+ * Allocates one temporary
  * copy of the state. */
 int snap_autotune(snap_ctx *ctx, int steps, double *best_ms, int *choice);
 
@@ -266,6 +284,36 @@ typedef struct snap_info {
 } snap_info;
 int snap_get_info(const snap_ctx *ctx, snap_info *info);
 
+/* Slab decomposition of one domain along x (the ghost cells of a SNAP_HALO side).
+ *
+ * snap_link_halo: within one context, the ghost columns of side `side` (0: x-, 1: x+) of
+ * `domain` are read by the stage kernels straight from the stage input of domain `nbr` (its
+ * last three columns for x-, its first three for x+): no copy, no extra launch. Both sides
+ * must be SNAP_HALO (nbr's side 1 - side), and the two domains must have the same ny, nz, dz,
+ * grav and reference profile. Linked domains form one group that shares a single CFL time
+ * step (the largest rate over the group, as the undecomposed domain has), so a group
+ * advances exactly like the whole domain: an x-periodic domain becomes a ring of slabs
+ * (link the last slab's x+ to the first), a walled one a chain. Set up the links before
+ * stepping; link each pair from both sides.
+ *
+ * snap_halo_buffer: for a neighbour in another context, process or GPU: *ptr receives the
+ * device address of the side's ghost buffer, nfields x nz x ny x 3 values of the context's
+ * dtype in the stored layout (i fastest; the energy field stored as rho e - pbar_k/(gamma_d
+ * - 1), identical on both slabs of one domain), which the stage kernels read as the side's
+ * ghost columns. The caller fills it before each stage with the neighbour's snap_halo_pack
+ * output of the same stage input (e.g. an NCCL receive into it). Valid until snap_free.
+ *
+ * snap_halo_pack: writes the three columns of `domain` next to `side` of state buffer `slot`
+ * (0, 1, 2: the input of stage 0, 1, 2; see snap_buffer_pointer) to the device buffer out in
+ * the layout of snap_halo_buffer, ordered so that it is the opposite neighbour's ghost
+ * buffer as it stands. Stream-ordered on stream (NULL: the context's).
+ *
+ * snap_step and snap_stage return SNAP_EINVAL while a SNAP_HALO side is neither linked nor
+ * given to the caller through snap_halo_buffer. Contexts with SNAP_HALO sides have no
+ * adjoint (SNAP_ENOTSUP). */
+int snap_link_halo(snap_ctx *ctx, int domain, int side, int nbr);
+int snap_halo_buffer(snap_ctx *ctx, int domain, int side, void **ptr);
+int snap_halo_pack(snap_ctx *ctx, int domain, int side, int slot, void *out, void *stream);
 /* Device pointer of one of a domain's three state buffers: slot 0 the current state, slot 1
  * the result of stage 0, slot 2 the result of stage 1 (dtype of the context, stored layout:
  * the energy field holds rho e - pbar_k/(gamma_d - 1)).
@@ -290,8 +338,13 @@ int snap_buffer_pointer(snap_ctx *ctx, int domain, int slot, void **ptr);
  * SNAP_MAX_FIELDS (SNAP_EINVAL beyond). Each call writes every partial-sum row it later
  * reads, so nothing has to be cleared between calls; but all calls on a device share the
  * array, so calls whose work overlaps on the GPU (other streams, other host threads) race
- * and give wrong sums: serialise them. The first call on each device looks up the array's
- * device address with cudaGetSymbolAddress; make that first call before any stream capture.
+ * and give wrong sums: serialise them. Every call made outside stream capture looks up the
+ * array's device address in the device's current context (cudaGetSymbolAddress), so a
+ * context destroyed and created again (cudaDeviceReset) is followed; a call on a capturing
+ * stream reuses the address of the last call outside capture on that device, so make one
+ * call before capturing (and again after a reset): with none, the call returns SNAP_ECUDA.
+ * A CUDA error already pending in the process when the call starts is left in place for its
+ * owner and reported as SNAP_ECUDA, with nothing launched.
  * Returns SNAP_OK, SNAP_EINVAL or SNAP_ECUDA; out is complete when the stream reaches it. */
 int snap_budget_noalloc(const void *Y, int dtype, int nx, int ny, int nz, int nfields,
                         int n_mass_fields, double dx, double dy, double dz, double grav,

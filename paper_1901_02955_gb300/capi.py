@@ -19,7 +19,7 @@ MAX_COND = 2
 MAX_FIELDS = 24
 
 OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, ENOCONV, ETIMEOUT, ENOTSUP = 0, -1, -2, -3, -4, -5, -6, -7
-REFLECT, PERIODIC, NOSLIP = 0, 1, 2
+REFLECT, PERIODIC, NOSLIP, HALO = 0, 1, 2, 3
 F64, F32 = 0, 1
 
 # every function declared in include/snap.h
@@ -28,6 +28,7 @@ EXPORTS = ["snap_init_grid", "snap_set_state", "snap_get_state", "snap_step", "s
            "snap_compute_dt", "snap_saturation_adjust", "snap_record", "snap_step_adjoint",
            "snap_set_stream",
            "snap_use_graph", "snap_set_tile_variant", "snap_use_persistent", "snap_autotune",
+           "snap_set_barrier_test", "snap_link_halo", "snap_halo_buffer", "snap_halo_pack",
            "snap_get_info", "snap_buffer_pointer", "snap_budget_noalloc", "snap_theta_e",
            "snap_probe_fma", "snap_check_rcp64", "snap_check_weno",
            "snap_free", "snap_last_error", "snap_status_string"]
@@ -109,6 +110,10 @@ def load(path: Optional[str] = None) -> C.CDLL:
     lib.snap_set_tile_variant.argtypes = [P, C.c_int]
     lib.snap_use_persistent.argtypes = [P, C.c_int]
     lib.snap_autotune.argtypes = [P, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int)]
+    lib.snap_set_barrier_test.argtypes = [P, C.c_longlong, C.c_int]
+    lib.snap_link_halo.argtypes = [P, C.c_int, C.c_int, C.c_int]
+    lib.snap_halo_buffer.argtypes = [P, C.c_int, C.c_int, C.POINTER(P)]
+    lib.snap_halo_pack.argtypes = [P, C.c_int, C.c_int, C.c_int, P, P]
     lib.snap_buffer_pointer.argtypes = [P, C.c_int, C.c_int, C.POINTER(P)]
     lib.snap_probe_fma.argtypes = [C.c_int, C.POINTER(C.c_double), P]
     lib.snap_check_rcp64.argtypes = [P, P, C.c_longlong, P]
@@ -302,15 +307,44 @@ class Context:
     def set_tile_variant(self, variant):
         return self._check(self.lib.snap_set_tile_variant(self._ptr, variant))
 
-    def use_persistent(self, enable=True):
-        return self._check(self.lib.snap_use_persistent(self._ptr, int(enable)))
+    def use_persistent(self, mode=True):
+        """Launch mode of a step: 0/False three launches, 1/True one persistent launch with
+        grid barriers, 2 the resident step (see snap_use_persistent)."""
+        return self._check(self.lib.snap_use_persistent(self._ptr, int(mode)))
+
+    def set_barrier_test(self, spin_cycles=0, absent_cta=-1):
+        """Test aid of the persistent step's grid barrier (see snap_set_barrier_test)."""
+        return self._check(self.lib.snap_set_barrier_test(self._ptr, int(spin_cycles),
+                                                          int(absent_cta)))
 
     def autotune(self, steps=5):
         ms = C.c_double(0.0)
         choice = C.c_int(0)
         self._check(self.lib.snap_autotune(self._ptr, steps, C.byref(ms), C.byref(choice)))
-        return {"ms_per_step": ms.value, "variant": choice.value // 2,
-                "persistent": choice.value % 2}
+        return {"ms_per_step": ms.value, "variant": choice.value // 3,
+                "persistent": choice.value % 3}
+
+    # -- slab decomposition (SNAP_HALO sides) ---------------------------------------------
+    def link_halo(self, domain, side, nbr):
+        """Ghost columns of `side` (0: x-, 1: x+) read from domain nbr (see snap_link_halo)."""
+        return self._check(self.lib.snap_link_halo(self._ptr, domain, side, nbr))
+
+    def halo_view(self, domain=0, side=0):
+        """Zero-copy torch view (nfields, nz, ny, 3) of a side's ghost buffer, which the caller
+        fills before each stage (see snap_halo_buffer)."""
+        import torch
+        p = C.c_void_p()
+        self._check(self.lib.snap_halo_buffer(self._ptr, domain, side, C.byref(p)))
+        w = self.workloads[domain]
+        return _device_view((w.nv, w.nz, w.ny, 3), self.f32, p.value)
+
+    def halo_pack(self, domain, side, slot, out, stream=None):
+        """The three columns next to `side` of state buffer `slot` into the device tensor out
+        (see snap_halo_pack)."""
+        if not (out.is_cuda and out.is_contiguous()):
+            raise ValueError("out must be a contiguous CUDA tensor")
+        return self._check(self.lib.snap_halo_pack(self._ptr, domain, side, slot,
+                                                   C.c_void_p(out.data_ptr()), stream))
 
     def buffer_pointer(self, domain=0, slot=0):
         p = C.c_void_p()
@@ -319,18 +353,20 @@ class Context:
 
     def buffer_view(self, domain=0, slot=0):
         """Zero-copy torch view of a device state buffer (see snap_buffer_pointer)."""
-        import torch
         w = self.workloads[domain]
+        return _device_view((w.nv, w.nz, w.ny, w.nx), self.f32,
+                            self.buffer_pointer(domain, slot))
 
-        class _Dev:
-            __cuda_array_interface__ = {
-                "shape": (w.nv, w.nz, w.ny, w.nx),
-                "typestr": "<f4" if self.f32 else "<f8",
-                "data": (self.buffer_pointer(domain, slot), False),
-                "version": 2,
-            }
 
-        return torch.as_tensor(_Dev(), device="cuda")
+def _device_view(shape, f32, ptr):
+    """torch tensor over device memory the library owns (no copy)."""
+    import torch
+
+    class _Dev:
+        __cuda_array_interface__ = {"shape": tuple(shape), "typestr": "<f4" if f32 else "<f8",
+                                    "data": (ptr, False), "version": 2}
+
+    return torch.as_tensor(_Dev(), device="cuda")
 
 
 def _buffer(Y):

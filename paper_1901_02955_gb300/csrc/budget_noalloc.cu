@@ -77,18 +77,28 @@ __global__ void budget_static_finish(const double *partials, int nblocks, int no
   }
 }
 
-// Device address of the scratch array for the current device, looked up once per device.
-cudaError_t scratch_for_current_device(double **out) {
+// Device address of the scratch array for the current device. Outside stream capture it is
+// looked up on every call: the address belongs to the module loaded into the device's current
+// context, and a context that was destroyed and created again (cudaDeviceReset, or the primary
+// context released by its last user) loads the module anew, possibly elsewhere. During capture
+// no lookup is made (it may have to load the module, which capture forbids); the address of
+// the last call outside capture on this device is used, and a capture with no such call fails.
+cudaError_t scratch_for_current_device(cudaStream_t s, double **out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  e = cudaStreamIsCapturing(s, &cap);
+  if (e != cudaSuccess) return e;
   std::lock_guard<std::mutex> lock(g_setup_mutex);
-  if (!g_scratch_ptr[dev]) {
+  if (cap == cudaStreamCaptureStatusNone) {
     void *p = nullptr;
     e = cudaGetSymbolAddress(&p, g_budget_scratch);
     if (e != cudaSuccess) return e;
     g_scratch_ptr[dev] = static_cast<double *>(p);
+  } else if (!g_scratch_ptr[dev]) {
+    return cudaErrorStreamCaptureUnsupported;
   }
   *out = g_scratch_ptr[dev];
   return cudaSuccess;
@@ -104,14 +114,17 @@ extern "C" int snap_budget_noalloc(const void *Y, int dtype, int nx, int ny, int
   if (nfields < 2 || nfields > SNAP_MAX_FIELDS) return SNAP_EINVAL;  // scratch row limit
   if (n_mass_fields < 1 || n_mass_fields >= nfields) return SNAP_EINVAL;
   if (!(dx > 0) || !(dz > 0) || (ny > 1 && !(dy > 0))) return SNAP_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  // an error left pending by earlier work of the caller is reported, not consumed: it stays
+  // for its owner to read, and this call launches nothing
+  if (cudaPeekAtLastError() != cudaSuccess) return SNAP_ECUDA;
   double *partials = nullptr;
-  if (scratch_for_current_device(&partials) != cudaSuccess) return SNAP_ECUDA;
+  if (scratch_for_current_device(s, &partials) != cudaSuccess) return SNAP_ECUDA;
   const long long ncell = (long long)nx * ny * nz;
   const long long plane = (long long)nx * ny;
   long long nb = (ncell + kThreads - 1) / kThreads;
   const int nblocks = int(nb < 1 ? 1 : (nb > kMaxBlocks ? kMaxBlocks : nb));
   const double vol = dx * (ny > 1 ? dy : 1.0) * dz;
-  cudaStream_t s = (cudaStream_t)stream;
   if (dtype == SNAP_F32)
     budget_static_kernel<float><<<nblocks, kThreads, 0, s>>>(
         (const float *)Y, nfields, n_mass_fields, ncell, plane, dz, grav, vol, partials);
@@ -119,5 +132,6 @@ extern "C" int snap_budget_noalloc(const void *Y, int dtype, int nx, int ny, int
     budget_static_kernel<double><<<nblocks, kThreads, 0, s>>>(
         (const double *)Y, nfields, n_mass_fields, ncell, plane, dz, grav, vol, partials);
   budget_static_finish<<<1, 32, 0, s>>>(partials, nblocks, nfields + 1, out);
+  // no error was pending before the launches, so one read here is this call's own
   return cudaGetLastError() == cudaSuccess ? SNAP_OK : SNAP_ECUDA;
 }

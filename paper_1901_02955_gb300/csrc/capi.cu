@@ -6,6 +6,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <new>
 #include <string>
 #include <vector>
@@ -14,7 +15,7 @@
 #include "snap_internal.h"
 
 static_assert(snap::kBcReflect == SNAP_REFLECT && snap::kBcPeriodic == SNAP_PERIODIC &&
-                  snap::kBcNoSlip == SNAP_NOSLIP,
+                  snap::kBcNoSlip == SNAP_NOSLIP && snap::kBcHalo == SNAP_HALO,
               "boundary kinds of the kernels and of the C interface differ");
 
 namespace snap {
@@ -80,6 +81,20 @@ cudaError_t launch_state_copy(const void *src, int src_f32, void *dst, int dst_f
                                                              nv, ncell, plane, e_ref, sg);
   return cudaGetLastError();
 }
+// The three columns x0 .. x0+2 of every row of a state (fields [nv][nrow][nx]) into a
+// contiguous [nv][nrow][3] buffer: a slab's cells next to one of its x sides, which are the
+// neighbouring slab's ghost columns. W is an unsigned type of the state's word size (a copy of
+// the bits).
+template <class W>
+__global__ void halo_pack_kernel(const W *Y, W *out, int nv, int nx, long long nrow, int x0) {
+  const long long n = (long long)nv * nrow * 3, ncell = nrow * nx;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int c = int(i % 3);
+    const long long r = (i / 3) % nrow, v = i / (3 * nrow);
+    out[i] = Y[v * ncell + r * nx + x0 + c];
+  }
+}
 }  // namespace snap
 
 using namespace snap;
@@ -92,12 +107,29 @@ struct snap_ctx {
   Phys ph{};
   std::vector<snap_grid_desc> desc;
   std::vector<DomDev> dom;   // host mirror of doms_dev
+  // slab decomposition: group of each domain (linked slabs share the group's CFL rate and
+  // time step slots, rate_dev[grp] and dt_dev[grp]); per domain and x side, 0 = not a halo
+  // side or not ready, 1 = linked to a domain of this context, 2 = ghost buffer handed out
+  std::vector<int> grp;
+  std::vector<int> halo_state;     // [ndom][2]
+  void *halo_arena = nullptr;      // ghost buffers of the SNAP_HALO sides
+  std::vector<std::vector<double>> rb_host, pf_host;  // reference profiles (host copies)
   std::vector<int> prefix;   // tile prefix per domain
   int ntiles = 0, grid = 0;
   int tv = 0;                // active tile variant
-  int persistent = 0;        // 1: one cooperative launch per step
+  int persistent = 0;        // 1: one cooperative launch per step (grid barriers between
+                             // stages); 2: the resident step (one tile per CTA, neighbour flags)
   int grid_persistent = 0;
   GridSync *gsync = nullptr;
+  long long spin_limit = 4000000000ll;  // grid-barrier wait limit, clock cycles (~2 s)
+  int absent_cta = -1;                  // test aid (snap_set_barrier_test)
+  // resident step: launch bookkeeping, tile flags and ghost-cell dependencies of the current
+  // tiling (res_ready: built for tile variant res_tv)
+  ResidentSync *res = nullptr;
+  unsigned int *tile_flags = nullptr;
+  int *dep_begin = nullptr, *dep_list = nullptr;
+  unsigned long long *rate_next_dev = nullptr;
+  int res_ready = 0, res_tv = -1;
   // discrete adjoint (dry, inviscid, one domain): recording and work buffers
   int has_adj = 0;
   AdjKernels adj{};
@@ -160,9 +192,15 @@ static void release(snap_ctx *ctx) {
   if (!ctx) return;
   if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
   cudaFree(ctx->arena);
+  cudaFree(ctx->halo_arena);
   cudaFree(ctx->doms_dev);
   cudaFree(ctx->prefix_dev);
   cudaFree(ctx->gsync);
+  cudaFree(ctx->res);
+  cudaFree(ctx->tile_flags);
+  cudaFree(ctx->dep_begin);
+  cudaFree(ctx->dep_list);
+  cudaFree(ctx->rate_next_dev);
   cudaFree(ctx->ckpt);
   cudaFree(ctx->segbuf);
   cudaFree(ctx->dt_hist);
@@ -191,8 +229,9 @@ static int validate(const snap_grid_desc &d, const snap_grid_desc &d0, int idx, 
   if (d.nx < 3 || d.nz < 3 || d.ny < 1 || d.ny == 2) return bad("need nx >= 3, nz >= 3, ny == 1 or ny >= 3");
   if (!(d.dx > 0) || !(d.dz > 0) || (d.ny > 1 && !(d.dy > 0))) return bad("cell sizes must be positive");
   for (int s = 0; s < 6; ++s)
-    if (d.bc[s] != SNAP_REFLECT && d.bc[s] != SNAP_PERIODIC && d.bc[s] != SNAP_NOSLIP)
-      return bad("bc must be REFLECT, PERIODIC or NOSLIP");
+    if (d.bc[s] != SNAP_REFLECT && d.bc[s] != SNAP_PERIODIC && d.bc[s] != SNAP_NOSLIP &&
+        !(d.bc[s] == SNAP_HALO && s < 2))
+      return bad("bc must be REFLECT, PERIODIC or NOSLIP (or HALO on an x side)");
   if (d.bc[4] == SNAP_PERIODIC || d.bc[5] == SNAP_PERIODIC) return bad("the z boundaries must be walls");
   if (!isfinite(d.T_bottom) || !(d.T_bottom >= 0.0)) return bad("T_bottom must be finite and >= 0");
   if ((d.bc[0] == SNAP_PERIODIC) != (d.bc[1] == SNAP_PERIODIC)) return bad("periodic x needs both x sides periodic");
@@ -349,6 +388,12 @@ static StageArgs args_of(snap_ctx *ctx, int stage) {
   a.flags = ctx->flags_dev;
   a.max_sweeps = ctx->sweeps_dev;
   a.gsync = ctx->gsync;
+  a.spin_limit = ctx->spin_limit;
+  a.absent_cta = ctx->absent_cta;
+  a.res = ctx->res;
+  a.tile_flags = ctx->tile_flags;
+  a.dep_begin = ctx->dep_begin;
+  a.dep_list = ctx->dep_list;
   a.dt_override = -1.0;
   a.buf_s = a.buf_n = nullptr;
   a.buf_o = nullptr;
@@ -359,10 +404,24 @@ static StageArgs args_of(snap_ctx *ctx, int stage) {
   return a;
 }
 
+// CFL rate of the group of domain dm (the domain itself unless it is a linked slab): the
+// group's slot is cleared and every member's cells take their maximum into it.
 static int refresh_rate(snap_ctx *ctx, int dm, cudaStream_t s) {
-  CK(cudaMemsetAsync(ctx->rate_dev + dm, 0, sizeof(unsigned long long), s));
+  const int g = ctx->grp[dm];
+  CK(cudaMemsetAsync(ctx->rate_dev + g, 0, sizeof(unsigned long long), s));
   StageArgs a = args_of(ctx, 0);
-  CK(ctx->ks.rate(a, dm, 0, s));
+  for (int i = 0; i < ctx->ndom; ++i)
+    if (ctx->grp[i] == g) CK(ctx->ks.rate(a, i, 0, s));
+  return SNAP_OK;
+}
+
+// Every SNAP_HALO side linked or its ghost buffer handed out.
+static int halos_ready(snap_ctx *ctx, const char *who) {
+  for (int i = 0; i < ctx->ndom; ++i)
+    for (int h = 0; h < 2; ++h)
+      if (ctx->dom[i].bc[h] == kBcHalo && ctx->halo_state[2 * i + h] == 0)
+        return fail(ctx, SNAP_EINVAL, std::string(who) + ": a SNAP_HALO side is neither linked "
+                                      "(snap_link_halo) nor fed (snap_halo_buffer)");
   return SNAP_OK;
 }
 
@@ -426,7 +485,8 @@ extern "C" int snap_init_grid(snap_ctx **out, const snap_grid_desc *d, int n_dom
   // the adjoint covers neither the microphysics nor sedimentation, nor no-slip walls or a
   // fixed bottom temperature
   bool plain_walls = d[0].T_bottom == 0.0;
-  for (int s = 0; s < 6; ++s) plain_walls = plain_walls && d[0].bc[s] != SNAP_NOSLIP;
+  for (int s = 0; s < 6; ++s)
+    plain_walls = plain_walls && d[0].bc[s] != SNAP_NOSLIP && d[0].bc[s] != SNAP_HALO;
   if (!ctx->visc && n_domains == 1 && !micro && plain_walls)
     ctx->has_adj = find_adjoint_kernels(ctx->f32, ctx->nvap, ctx->ncond, ctx->three_d, &ctx->adj) ? 1 : 0;
   cudaError_t e = cudaSuccess;
@@ -442,6 +502,12 @@ extern "C" int snap_init_grid(snap_ctx **out, const snap_grid_desc *d, int n_dom
   size_t nprof = 0, nproff = 0;
   ctx->prefix.assign(n_domains + 1, 0);
   ctx->dom.resize(n_domains);
+  ctx->grp.resize(n_domains);
+  ctx->halo_state.assign(2 * (size_t)n_domains, 0);
+  ctx->rb_host.resize(n_domains);
+  ctx->pf_host.resize(n_domains);
+  std::vector<size_t> halo_off(2 * (size_t)n_domains, 0);
+  size_t halo_total = 0;
   for (int i = 0; i < n_domains; ++i) {
     const snap_grid_desc &g = d[i];
     size_t nc = (size_t)g.nx * g.ny * g.nz;
@@ -473,6 +539,18 @@ extern "C" int snap_init_grid(snap_ctx **out, const snap_grid_desc *d, int n_dom
     D.T_bot = g.T_bottom;
     D.ncell = (long long)nc;
     (void)bytes;
+    ctx->grp[i] = i;
+    ctx->rb_host[i].assign(g.rho_bar, g.rho_bar + g.nz);
+    ctx->pf_host[i].assign(g.p_bar_face, g.p_bar_face + g.nz + 1);
+    for (int h = 0; h < 2; ++h) {
+      D.hnx[h] = 3;
+      D.hoff[h] = 0;
+      for (int st = 0; st < 3; ++st) D.hsrc[h][st] = nullptr;
+      if (g.bc[h] == SNAP_HALO) {
+        halo_off[2 * i + h] = halo_total;
+        halo_total += ((size_t)ctx->nv * g.nz * g.ny * 3 * ctx->word + 255) / 256 * 256;
+      }
+    }
   }
   ctx->ntiles = ctx->prefix[n_domains];
   int ret = SNAP_OK;
@@ -482,6 +560,15 @@ extern "C" int snap_init_grid(snap_ctx **out, const snap_grid_desc *d, int n_dom
     ctx->stream = ctx->own_stream;
     if ((e = cudaMalloc(&ctx->arena, total)) != cudaSuccess) break;
     if ((e = cudaMemset(ctx->arena, 0, total)) != cudaSuccess) break;
+    if (halo_total) {
+      if ((e = cudaMalloc(&ctx->halo_arena, halo_total)) != cudaSuccess) break;
+      if ((e = cudaMemset(ctx->halo_arena, 0, halo_total)) != cudaSuccess) break;
+      for (int i = 0; i < n_domains; ++i)
+        for (int h = 0; h < 2; ++h)
+          if (d[i].bc[h] == SNAP_HALO)
+            for (int st = 0; st < 3; ++st)
+              ctx->dom[i].hsrc[h][st] = (char *)ctx->halo_arena + halo_off[2 * i + h];
+    }
     if ((e = cudaMalloc(&ctx->doms_dev, sizeof(DomDev) * n_domains)) != cudaSuccess) break;
     if ((e = cudaMalloc(&ctx->prefix_dev, sizeof(int) * (n_domains + 1))) != cudaSuccess) break;
     if ((e = cudaMalloc(&ctx->gsync, sizeof(GridSync))) != cudaSuccess) break;
@@ -489,6 +576,9 @@ extern "C" int snap_init_grid(snap_ctx **out, const snap_grid_desc *d, int n_dom
     if ((e = cudaMalloc(&ctx->prof_dev, sizeof(double) * nprof)) != cudaSuccess) break;
     if ((e = cudaMalloc(&ctx->proff_dev, sizeof(float) * nproff)) != cudaSuccess) break;
     if ((e = cudaMalloc(&ctx->rate_dev, sizeof(unsigned long long) * n_domains)) != cudaSuccess) break;
+    if ((e = cudaMalloc(&ctx->rate_next_dev, sizeof(unsigned long long) * n_domains)) != cudaSuccess) break;
+    if ((e = cudaMemset(ctx->rate_next_dev, 0, sizeof(unsigned long long) * n_domains)) != cudaSuccess) break;
+    if ((e = cudaMalloc(&ctx->res, sizeof(ResidentSync))) != cudaSuccess) break;
     if ((e = cudaMalloc(&ctx->dt_dev, sizeof(double) * n_domains)) != cudaSuccess) break;
     if ((e = cudaMalloc(&ctx->flags_dev, sizeof(unsigned int))) != cudaSuccess) break;
     if ((e = cudaMalloc(&ctx->sweeps_dev, sizeof(int))) != cudaSuccess) break;
@@ -544,6 +634,7 @@ extern "C" int snap_init_grid(snap_ctx **out, const snap_grid_desc *d, int n_dom
       D.fidz = (float)D.idz;
       D.fgrav = (float)g.grav;
       D.rate = ctx->rate_dev + i;
+      D.rate_next = ctx->rate_next_dev + i;
       D.dt_step = ctx->dt_dev + i;
       po += 4 * (size_t)g.nz + 1;
       pof += 5 * (size_t)g.nz + 1;
@@ -593,6 +684,7 @@ static int apply_variant(snap_ctx *ctx, int v) {
   if (mrb <= 0) return fail(ctx, SNAP_ECUDA, "occupancy query of the step kernel failed");
   ctx->grid_persistent = mrb < ctx->ntiles ? mrb : ctx->ntiles;
   ctx->tv = v;
+  ctx->res_ready = 0;
   CK(cudaMemcpyAsync(ctx->doms_dev, ctx->dom.data(), sizeof(DomDev) * ctx->ndom,
                      cudaMemcpyHostToDevice, ctx->stream));
   CK(cudaMemcpyAsync(ctx->prefix_dev, ctx->prefix.data(), sizeof(int) * (ctx->ndom + 1),
@@ -681,9 +773,106 @@ static int set_dt_fixed(snap_ctx *ctx, double dt_fixed) {
   return SNAP_OK;
 }
 
+// Tile index along one axis of the cell a ghost at position p (outside [0, n)) copies:
+// wrapped on a periodic axis, mirrored at a wall.
+static int ghost_source(int p, int n, bool periodic) {
+  if (periodic) return ((p % n) + n) % n;
+  return p < 0 ? -1 - p : 2 * n - 1 - p;
+}
+
+// Whether the resident step can run the current tiling: every tile co-resident, and no slab
+// boundary (its ghost cells come from another domain's tiles).
+static bool resident_possible(snap_ctx *ctx, std::string *why) {
+  for (int i = 0; i < ctx->ndom; ++i)
+    if (ctx->dom[i].bc[0] == kBcHalo || ctx->dom[i].bc[1] == kBcHalo) {
+      if (why) *why = "the resident step does not take slab boundaries (SNAP_HALO)";
+      return false;
+    }
+  const int mrt = ctx->ks.var[ctx->tv].max_resident_tiles();
+  if (mrt <= 0 || ctx->ntiles > mrt) {
+    if (why) *why = "the resident step needs every tile co-resident (" + std::to_string(ctx->ntiles) +
+                    " tiles, " + std::to_string(mrt) + " co-resident CTAs for this tile shape)";
+    return false;
+  }
+  return true;
+}
+
+// Ghost-cell dependencies of every tile for the resident step: the tiles holding the cells
+// its three ghost layers per side copy (the same tile rows and columns, shifted along one
+// axis, with the wrap or mirror of the domain boundary), made symmetric -- a tile that reads
+// another's cells is also waited on by it, so no tile overwrites its state of a previous
+// stage while a neighbour may still read it -- and without the tile itself.
+static int build_resident(snap_ctx *ctx) {
+  std::string why;
+  if (!resident_possible(ctx, &why)) return fail(ctx, SNAP_ENOTSUP, "snap_use_persistent: " + why);
+  const int *tl = ctx->ks.var[ctx->tv].tile;
+  const int nt = ctx->ntiles;
+  std::vector<std::vector<int>> dep(nt);
+  for (int i = 0; i < ctx->ndom; ++i) {
+    const DomDev &D = ctx->dom[i];
+    const int n[3] = {D.nx, D.ny, D.nz}, tc[3] = {D.tx, D.ty, D.tz};
+    const bool per[3] = {D.bc[0] == kBcPeriodic, D.bc[2] == kBcPeriodic, false};
+    for (int t = 0; t < tc[0] * tc[1] * tc[2]; ++t) {
+      const int ti[3] = {t % tc[0], (t / tc[0]) % tc[1], t / (tc[0] * tc[1])};
+      for (int d = 0; d < 3; ++d) {
+        if (n[d] == 1) continue;
+        const int c0 = ti[d] * tl[d], c1 = std::min(c0 + tl[d], n[d]);
+        for (int r = 1; r <= 3; ++r)
+          for (int p : {c0 - r, c1 - 1 + r}) {
+            const int q = (p >= 0 && p < n[d]) ? p : ghost_source(p, n[d], per[d]);
+            int tj[3] = {ti[0], ti[1], ti[2]};
+            tj[d] = q / tl[d];
+            const int u = D.tile_begin + (tj[2] * tc[1] + tj[1]) * tc[0] + tj[0];
+            if (u != D.tile_begin + t) dep[D.tile_begin + t].push_back(u);
+          }
+      }
+    }
+  }
+  for (int t = 0; t < nt; ++t)
+    for (int u : std::vector<int>(dep[t])) dep[u].push_back(t);
+  std::vector<int> begin(nt + 1, 0), list;
+  for (int t = 0; t < nt; ++t) {
+    std::sort(dep[t].begin(), dep[t].end());
+    dep[t].erase(std::unique(dep[t].begin(), dep[t].end()), dep[t].end());
+    list.insert(list.end(), dep[t].begin(), dep[t].end());
+    begin[t + 1] = (int)list.size();
+  }
+  cudaFree(ctx->tile_flags);
+  cudaFree(ctx->dep_begin);
+  cudaFree(ctx->dep_list);
+  ctx->tile_flags = nullptr;
+  ctx->dep_begin = ctx->dep_list = nullptr;
+  CK(cudaMalloc(&ctx->tile_flags, sizeof(unsigned int) * nt));
+  CK(cudaMalloc(&ctx->dep_begin, sizeof(int) * (nt + 1)));
+  CK(cudaMalloc(&ctx->dep_list, sizeof(int) * (list.size() + 1)));
+  CK(cudaMemsetAsync(ctx->tile_flags, 0, sizeof(unsigned int) * nt, ctx->stream));
+  CK(cudaMemsetAsync(ctx->res, 0, sizeof(ResidentSync), ctx->stream));
+  CK(cudaMemcpyAsync(ctx->dep_begin, begin.data(), sizeof(int) * (nt + 1),
+                     cudaMemcpyHostToDevice, ctx->stream));
+  if (!list.empty())
+    CK(cudaMemcpyAsync(ctx->dep_list, list.data(), sizeof(int) * list.size(),
+                       cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->res_ready = 1;
+  ctx->res_tv = ctx->tv;
+  return SNAP_OK;
+}
+
 static int enqueue_stages(snap_ctx *ctx, cudaStream_t s) {
   const TileVariant &tv = ctx->ks.var[ctx->tv];
+  if (ctx->persistent == 2) {
+    if (!ctx->res_ready) {
+      int rc = build_resident(ctx);
+      if (rc) return rc;
+    }
+    StageArgs a = args_of(ctx, 0);
+    CK(tv.resident(a, ctx->ntiles, s));
+    return SNAP_OK;
+  }
   if (ctx->persistent) {
+    // a barrier wait that gave up in an earlier launch leaves its arrival count behind:
+    // every launch starts from a cleared barrier (a memset node in the captured graph)
+    CK(cudaMemsetAsync(ctx->gsync, 0, sizeof(GridSync), s));
     StageArgs a = args_of(ctx, 0);
     CK(tv.step(a, ctx->grid_persistent, s));
     return SNAP_OK;
@@ -698,7 +887,9 @@ static int enqueue_stages(snap_ctx *ctx, cudaStream_t s) {
 extern "C" int snap_stage(snap_ctx *ctx, int stage, double dt_fixed) {
   if (!ctx) return fail(nullptr, SNAP_EINVAL, "snap_stage: NULL context");
   if (stage < 0 || stage > 2) return fail(ctx, SNAP_EINVAL, "snap_stage: stage must be 0, 1 or 2");
-  int rc = set_dt_fixed(ctx, dt_fixed);
+  int rc = halos_ready(ctx, "snap_stage");
+  if (rc) return rc;
+  rc = set_dt_fixed(ctx, dt_fixed);
   if (rc) return rc;
   StageArgs a = args_of(ctx, stage);
   CK(ctx->ks.var[ctx->tv].stage(a, ctx->grid, ctx->stream));
@@ -709,7 +900,10 @@ extern "C" int snap_step_async(snap_ctx *ctx, int nsteps, double dt_fixed) {
   if (!ctx) return fail(nullptr, SNAP_EINVAL, "snap_step_async: NULL context");
   if (nsteps < 0) return fail(ctx, SNAP_EINVAL, "snap_step_async: nsteps < 0");
   if (nsteps == 0) return SNAP_OK;
-  int rc = set_dt_fixed(ctx, dt_fixed);
+  int rc = halos_ready(ctx, "snap_step_async");
+  if (rc) return rc;
+  if (ctx->persistent == 2 && !ctx->res_ready && (rc = build_resident(ctx))) return rc;
+  rc = set_dt_fixed(ctx, dt_fixed);
   if (rc) return rc;
   if (!ctx->use_graph) {
     for (int n = 0; n < nsteps; ++n) {
@@ -761,7 +955,7 @@ extern "C" int snap_budget_compute(snap_ctx *ctx, int domain, snap_budget *out) 
   double host[SNAP_MAX_FIELDS + 1];
   CK(cudaMemcpyAsync(host, ctx->budget_out, sizeof(double) * (ctx->nv + 1), cudaMemcpyDeviceToHost, ctx->stream));
   double dt = 0.0;
-  CK(cudaMemcpyAsync(&dt, ctx->dt_dev + domain, sizeof dt, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(&dt, ctx->dt_dev + ctx->grp[domain], sizeof dt, cudaMemcpyDeviceToHost, ctx->stream));
   unsigned int flags = 0;
   int sweeps = 0;
   int rc = read_status(ctx, &flags, &sweeps);
@@ -817,7 +1011,7 @@ extern "C" int snap_compute_dt(snap_ctx *ctx, int domain, double *dt) {
   int rc = refresh_rate(ctx, domain, ctx->stream);
   if (rc) return rc;
   unsigned long long bits = 0;
-  CK(cudaMemcpyAsync(&bits, ctx->rate_dev + domain, sizeof bits, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(&bits, ctx->rate_dev + ctx->grp[domain], sizeof bits, cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   double r;
   memcpy(&r, &bits, sizeof r);
@@ -1114,9 +1308,14 @@ extern "C" int snap_set_tile_variant(snap_ctx *ctx, int variant) {
 
 extern "C" int snap_use_persistent(snap_ctx *ctx, int enable) {
   if (!ctx) return fail(nullptr, SNAP_EINVAL, "snap_use_persistent: NULL context");
-  if (ctx->grid_persistent <= 0)
+  if (enable < 0 || enable > 2) return fail(ctx, SNAP_EINVAL, "snap_use_persistent: mode 0, 1 or 2");
+  if (enable == 1 && ctx->grid_persistent <= 0)
     return fail(ctx, SNAP_ECUDA, "snap_use_persistent: no co-resident CTA for the step kernel");
-  ctx->persistent = enable ? 1 : 0;
+  if (enable == 2) {
+    const int rc = build_resident(ctx);
+    if (rc) return rc;
+  }
+  ctx->persistent = enable;
   if (ctx->graph) {
     cudaGraphExecDestroy(ctx->graph);
     ctx->graph = nullptr;
@@ -1154,8 +1353,9 @@ extern "C" int snap_autotune(snap_ctx *ctx, int steps, double *best_ms, int *cho
   CK(cudaEventCreate(&e1));
   for (int v = 0; v < ctx->ks.nvariants && rc == SNAP_OK; ++v) {
     rc = apply_variant(ctx, v);
-    for (int p = 0; p < 2 && rc == SNAP_OK; ++p) {
+    for (int p = 0; p < 3 && rc == SNAP_OK; ++p) {
       if (p == 1 && ctx->grid_persistent <= 0) continue;
+      if (p == 2 && !resident_possible(ctx, nullptr)) continue;
       ctx->persistent = p;
       rc = snap_step_async(ctx, 1, 0.0);  // warm-up
       if (rc) break;
@@ -1191,8 +1391,21 @@ extern "C" int snap_autotune(snap_ctx *ctx, int steps, double *best_ms, int *cho
   if (rc) return rc;
   ctx->persistent = best_p;
   if (best_ms) *best_ms = best;
-  if (choice) *choice = best_v * 2 + best_p;
+  if (choice) *choice = best_v * 3 + best_p;
   CK(cudaMemsetAsync(ctx->flags_dev, 0, sizeof(unsigned int), ctx->stream));
+  return SNAP_OK;
+}
+
+extern "C" int snap_set_barrier_test(snap_ctx *ctx, long long spin_cycles, int absent_cta) {
+  if (!ctx) return fail(nullptr, SNAP_EINVAL, "snap_set_barrier_test: NULL context");
+  if (spin_cycles < 0 || absent_cta < -1)
+    return fail(ctx, SNAP_EINVAL, "snap_set_barrier_test: spin_cycles >= 0, absent_cta >= -1");
+  ctx->spin_limit = spin_cycles > 0 ? spin_cycles : 4000000000ll;
+  ctx->absent_cta = absent_cta;
+  if (ctx->graph) {
+    cudaGraphExecDestroy(ctx->graph);
+    ctx->graph = nullptr;
+  }
   return SNAP_OK;
 }
 
@@ -1215,6 +1428,73 @@ extern "C" int snap_get_info(const snap_ctx *ctx, snap_info *info) {
   info->n_tile_variants = ctx->ks.nvariants;
   info->persistent = ctx->persistent;
   info->persistent_grid = ctx->grid_persistent;
+  return SNAP_OK;
+}
+
+extern "C" int snap_link_halo(snap_ctx *ctx, int domain, int side, int nbr) {
+  if (!ctx) return fail(nullptr, SNAP_EINVAL, "snap_link_halo: NULL context");
+  if (domain < 0 || domain >= ctx->ndom || nbr < 0 || nbr >= ctx->ndom || (side != 0 && side != 1))
+    return fail(ctx, SNAP_EINVAL, "snap_link_halo: bad domain, neighbour or side");
+  DomDev &D = ctx->dom[domain];
+  const DomDev &N = ctx->dom[nbr];
+  if (D.bc[side] != kBcHalo || N.bc[1 - side] != kBcHalo)
+    return fail(ctx, SNAP_EINVAL, "snap_link_halo: both facing sides must be SNAP_HALO");
+  if (D.ny != N.ny || D.nz != N.nz || D.dz != N.dz || D.grav != N.grav ||
+      ctx->rb_host[domain] != ctx->rb_host[nbr] || ctx->pf_host[domain] != ctx->pf_host[nbr])
+    return fail(ctx, SNAP_EINVAL, "snap_link_halo: slabs of one domain need the same ny, nz, dz, "
+                                  "grav and reference profile");
+  for (int st = 0; st < 3; ++st) D.hsrc[side][st] = N.buf[st];
+  D.hnx[side] = N.nx;
+  D.hoff[side] = side == 0 ? N.nx - 3 : 0;
+  ctx->halo_state[2 * domain + side] = 1;
+  // one group, one CFL time step: the group of the lower index absorbs the other
+  const int ga = ctx->grp[domain], gb = ctx->grp[nbr];
+  const int keep = ga < gb ? ga : gb, drop = ga < gb ? gb : ga;
+  for (int i = 0; i < ctx->ndom; ++i) {
+    if (ctx->grp[i] == drop) ctx->grp[i] = keep;
+    ctx->dom[i].rate = ctx->rate_dev + ctx->grp[i];
+    ctx->dom[i].dt_step = ctx->dt_dev + ctx->grp[i];
+  }
+  CK(cudaMemcpyAsync(ctx->doms_dev, ctx->dom.data(), sizeof(DomDev) * ctx->ndom,
+                     cudaMemcpyHostToDevice, ctx->stream));
+  if (ctx->graph) {
+    cudaGraphExecDestroy(ctx->graph);
+    ctx->graph = nullptr;
+  }
+  return refresh_rate(ctx, domain, ctx->stream);
+}
+
+extern "C" int snap_halo_buffer(snap_ctx *ctx, int domain, int side, void **ptr) {
+  if (!ctx) return fail(nullptr, SNAP_EINVAL, "snap_halo_buffer: NULL context");
+  if (domain < 0 || domain >= ctx->ndom || (side != 0 && side != 1) || !ptr)
+    return fail(ctx, SNAP_EINVAL, "snap_halo_buffer: bad domain, side or pointer");
+  if (ctx->dom[domain].bc[side] != kBcHalo || ctx->halo_state[2 * domain + side] == 1)
+    return fail(ctx, SNAP_EINVAL, "snap_halo_buffer: not an unlinked SNAP_HALO side");
+  const void *p = ctx->dom[domain].hsrc[side][0];
+  *ptr = const_cast<void *>(p);
+  ctx->halo_state[2 * domain + side] = 2;
+  return SNAP_OK;
+}
+
+extern "C" int snap_halo_pack(snap_ctx *ctx, int domain, int side, int slot, void *out,
+                              void *stream) {
+  if (!ctx) return fail(nullptr, SNAP_EINVAL, "snap_halo_pack: NULL context");
+  if (domain < 0 || domain >= ctx->ndom || (side != 0 && side != 1) || slot < 0 || slot > 2 || !out)
+    return fail(ctx, SNAP_EINVAL, "snap_halo_pack: bad domain, side, slot or pointer");
+  const DomDev &D = ctx->dom[domain];
+  const long long nrow = (long long)D.ny * D.nz;
+  const int x0 = side == 0 ? 0 : D.nx - 3;
+  const long long n = (long long)ctx->nv * nrow * 3;
+  const int grid = int(n / 256 + 1 < 1216 ? n / 256 + 1 : 1216);
+  cudaStream_t s = pick(ctx, stream);
+  if (ctx->f32)
+    halo_pack_kernel<unsigned int><<<grid, 256, 0, s>>>(
+        (const unsigned int *)D.buf[slot], (unsigned int *)out, ctx->nv, D.nx, nrow, x0);
+  else
+    halo_pack_kernel<unsigned long long><<<grid, 256, 0, s>>>(
+        (const unsigned long long *)D.buf[slot], (unsigned long long *)out, ctx->nv, D.nx,
+        nrow, x0);
+  CK(cudaGetLastError());
   return SNAP_OK;
 }
 

@@ -48,7 +48,7 @@ struct CstT {
 
 // One domain as the kernels see it (device memory).
 // Side boundary kinds (the values of SNAP_REFLECT, SNAP_PERIODIC, SNAP_NOSLIP).
-enum BcKind : int { kBcReflect = 0, kBcPeriodic = 1, kBcNoSlip = 2 };
+enum BcKind : int { kBcReflect = 0, kBcPeriodic = 1, kBcNoSlip = 2, kBcHalo = 3 };
 
 struct DomDev {
   int nx, ny, nz;
@@ -74,14 +74,27 @@ struct DomDev {
   float fidx, fidy, fidz, fgrav;
   unsigned long long *rate;  // CFL rate max as double bits (non-negative doubles order as
                              // unsigned integers)
+  unsigned long long *rate_next;  // resident step: the next step's rate while it accumulates
   double *dt_step;           // time step of the current step
   double T_bot;              // > 0: temperature of the ghost cells below the bottom wall
+  // ghost columns of a kBcHalo x side h (0: x-, 1: x+) for the input of stage s: source
+  // array hsrc[h][s] of rows of hnx[h] cells (fields [nv][nz][ny][hnx]); ghost column c
+  // (0..2, left to right) is source column hoff[h] + c
+  const void *hsrc[2][3];
+  int hnx[2], hoff[2];
 };
 
 // State of the grid-wide barrier of the persistent step kernel (device memory).
 struct GridSync {
   unsigned int count;
   unsigned int gen;
+};
+
+// Launch bookkeeping of the resident step kernel (device memory): CTAs finished in the
+// current launch, and the launch count that numbers the tile flags' stage epochs.
+struct ResidentSync {
+  unsigned int done;
+  unsigned int seq;
 };
 
 struct StageArgs {
@@ -93,6 +106,13 @@ struct StageArgs {
   unsigned int *flags;       // bit 0 non-finite, bit 1 no convergence
   int *max_sweeps;
   GridSync *gsync;           // persistent step kernel only
+  long long spin_limit;      // clock cycles a grid-barrier wait spins before giving up
+  // resident step kernel only: launch bookkeeping, per-tile stage flags, and per tile the
+  // tiles its ghost cells come from (dep_list[dep_begin[t] .. dep_begin[t+1]))
+  ResidentSync *res;
+  unsigned int *tile_flags;
+  const int *dep_begin, *dep_list;
+  int absent_cta;            // test aid: this CTA skips its barrier arrivals (-1: none)
   double dt_override;        // > 0: time step of this launch, before any domain setting
   // single-domain launches only: when set, the stage reads its input from buf_s and Y^n from
   // buf_n and writes its output to buf_o instead of the domain's buffers
@@ -115,6 +135,10 @@ struct TileVariant {
   cudaError_t (*step)(const StageArgs &, int grid, cudaStream_t);
   int (*max_resident_blocks)();  // co-resident CTAs of the step kernel on this device
   cudaError_t (*prepare)();      // one-time attribute setup (dynamic shared memory)
+  // all three stages in one cooperative launch, one tile per CTA, neighbour flags between
+  // stages (grid = number of tiles, at most max_resident_tiles())
+  cudaError_t (*resident)(const StageArgs &, int grid, cudaStream_t);
+  int (*max_resident_tiles)();
 };
 
 constexpr int kMaxVariants = 4;

@@ -796,6 +796,17 @@ __device__ __forceinline__ void cp_async_elem(R *smem_dst, const R *gmem_src) {
   else
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem_src) : "memory");
 }
+// Flag accesses of the resident step: a load with acquire and a store with release
+// semantics at device scope (the data written before the release is visible to a CTA whose
+// acquire load saw the flag).
+__device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int *p) {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_u32(unsigned int *p, unsigned int v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
@@ -986,12 +997,17 @@ struct StageSmem {
 };
 
 // Grid-wide barrier of the persistent step kernel (all CTAs co-resident by a cooperative
-// launch). Every wait is bounded: after ~2 s of spinning the CTA records kFlagTimeout and
-// proceeds, so a fault can corrupt results but never hang the device.
+// launch). Every wait is bounded: after spin_limit clock cycles (about 2 s by default) the CTA
+// records kFlagTimeout and proceeds, so a fault can corrupt results but never hang the device.
+// The host clears the barrier state before every persistent launch, so a count left behind by
+// a wait that gave up does not open a later barrier early. absent_cta (a test aid, -1 in
+// normal use) names a CTA that neither arrives nor waits, which makes every other CTA's wait
+// run out.
 __device__ __forceinline__ void grid_barrier(GridSync *gs, unsigned int nblocks,
-                                             unsigned int *flags) {
+                                             unsigned int *flags, long long spin_limit,
+                                             int absent_cta) {
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (threadIdx.x == 0 && int(blockIdx.x) != absent_cta) {
     volatile unsigned int *vgen = &gs->gen;
     const unsigned int g = *vgen;
     __threadfence();
@@ -1003,7 +1019,7 @@ __device__ __forceinline__ void grid_barrier(GridSync *gs, unsigned int nblocks,
     } else {
       const long long t0 = clock64();
       while (*vgen == g) {
-        if (clock64() - t0 > 4000000000ll) {
+        if (clock64() - t0 > spin_limit) {
           atomicOr(flags, (unsigned)kFlagTimeout);
           break;
         }
@@ -1015,9 +1031,17 @@ __device__ __forceinline__ void grid_barrier(GridSync *gs, unsigned int nblocks,
   __syncthreads();
 }
 
-template <class R, class L, bool VISC, class T, bool MICRO>
+// One stage over the CTA's tiles. RES (the resident step, one tile per CTA for all three
+// stages): for stages 1 and 2 ys holds the owned cells' stage input on entry (the previous
+// stage's output, kept in registers) instead of being loaded; Y^n of the owned cells is kept
+// in shared memory from stage 0 on; the time step of stage 0 stays in s_red[0]; ghost cells
+// are read past L1 (other CTAs wrote them during this launch); the CFL maximum goes to
+// D.rate_next (the step's own rate stays readable until every CTA has formed its time step);
+// ys receives the stage output.
+template <class R, class L, bool VISC, class T, bool MICRO, bool RES = false>
 __device__ __forceinline__ void stage_tiles(const StageArgs &a, const int stage,
-                                            unsigned char *smem) {
+                                            unsigned char *smem,
+                                            R (&ys)[Box<T, L::D3>::CPT][L::NV]) {
   using B = Box<T, L::D3>;
   using S = StageSmem<R, L, VISC, T>;
   using P = Prof<R>;
@@ -1055,15 +1079,17 @@ __device__ __forceinline__ void stage_tiles(const StageArgs &a, const int stage,
         dt = a.dt_override > 0.0 ? a.dt_override
              : (D.dt_fixed > 0.0 ? D.dt_fixed : D.cfl / __longlong_as_double((long long)*D.rate));
         if (lt == 0) *D.dt_step = dt;
-      } else {
+      } else if (!RES) {
         dt = *(volatile double *)D.dt_step;
         if (stage == 1 && lt == 0) *D.rate = 0ull;
+      } else {
+        dt = s_red[0];  // this CTA's own stage-0 time step
       }
       s_red[0] = dt;
     }
 
     // ---- 1. owned cells: load, keep the conserved values, store primitives -------------
-    if constexpr (S::PREFETCH) {
+    if constexpr (S::PREFETCH && !RES) {
       if (stage != 0) {
 #pragma unroll
         for (int m = 0; m < B::CPT; ++m) {
@@ -1078,7 +1104,6 @@ __device__ __forceinline__ void stage_tiles(const StageArgs &a, const int stage,
         cp_async_commit();
       }
     }
-    R ys[B::CPT][NV];
 #pragma unroll
     for (int m = 0; m < B::CPT; ++m) {
       const int c = tid + m * NT;
@@ -1086,8 +1111,14 @@ __device__ __forceinline__ void stage_tiles(const StageArgs &a, const int stage,
       if (c < B::NCELL && lx < ex && ly < ey && lz < ez) {
         const int k = z0 + lz;
         const long long g = ((long long)k * ny + (y0 + ly)) * nx + (x0 + lx);
+        if (!RES || stage == 0) {
 #pragma unroll
-        for (int v = 0; v < NV; ++v) ys[m][v] = Ys[v * ncell + g];
+          for (int v = 0; v < NV; ++v) ys[m][v] = Ys[v * ncell + g];
+          if constexpr (RES && S::PREFETCH) {
+#pragma unroll
+            for (int v = 0; v < NV; ++v) s_yn[v * B::NCELL + c] = ys[m][v];
+          }
+        }
         R x[NV], pt, Tt;
         cons_to_prim<R, L>(ph, C, D, k, ys[m], x, pt, Tt);
         const int bi = B::idx(lx + 3, ly + B::HY, lz + 3);
@@ -1136,13 +1167,29 @@ __device__ __forceinline__ void stage_tiles(const StageArgs &a, const int stage,
         // the side this ghost lies beyond (x-, x+, y-, y+, z-, z+)
         const int side = 2 * dirn + ((dirn == 0 ? gx : (dirn == 1 ? gy : gz)) < 0 ? 0 : 1);
         bool flip = false;
-        if (dirn == 0) gx = map_index(gx, nx, D.bc[0], D.bc[1], flip);
-        if (dirn == 1) gy = map_index(gy, ny, D.bc[2], D.bc[3], flip);
-        if (dirn == 2) gz = map_index(gz, nz, D.bc[4], D.bc[5], flip);
-        const long long g = ((long long)gz * ny + gy) * nx + gx;
+        const R *src = Ys;
+        long long g, nsrc = ncell;
+        if (dirn == 0 && (gx < 0 || gx >= nx) && D.bc[side] == kBcHalo && !a.buf_s) {
+          // a slab boundary: the neighbouring slab's cells (a linked domain's stage input,
+          // or the ghost buffer the caller filled)
+          const int h = side, hn = D.hnx[h];
+          src = reinterpret_cast<const R *>(D.hsrc[h][stage]);
+          nsrc = (long long)hn * ny * nz;
+          g = ((long long)gz * ny + gy) * hn + D.hoff[h] + (h ? gx - nx : gx + 3);
+        } else {
+          if (dirn == 0) gx = map_index(gx, nx, D.bc[0], D.bc[1], flip);
+          if (dirn == 1) gy = map_index(gy, ny, D.bc[2], D.bc[3], flip);
+          if (dirn == 2) gz = map_index(gz, nz, D.bc[4], D.bc[5], flip);
+          g = ((long long)gz * ny + gy) * nx + gx;
+        }
         R y[NV], x[NV], pt, Tt;
+        if constexpr (RES) {
 #pragma unroll
-        for (int v = 0; v < NV; ++v) y[v] = Ys[v * ncell + g];
+          for (int v = 0; v < NV; ++v) y[v] = __ldcg(src + v * nsrc + g);
+        } else {
+#pragma unroll
+          for (int v = 0; v < NV; ++v) y[v] = src[v * nsrc + g];
+        }
         cons_to_prim<R, L>(ph, C, D, gz, y, x, pt, Tt);
         if (flip) {
           // a wall: free-slip negates the normal velocity, no-slip every component
@@ -1325,7 +1372,7 @@ __device__ __forceinline__ void stage_tiles(const StageArgs &a, const int stage,
     }
 
     // ---- 4. gravity source, stage combine, saturation adjustment, store ------------------
-    if constexpr (S::PREFETCH) {
+    if constexpr (S::PREFETCH && !RES) {
       if (stage != 0) cp_async_wait();  // this thread's own copies of Y^n
     }
     R rate_max = R(0);
@@ -1406,6 +1453,10 @@ __device__ __forceinline__ void stage_tiles(const StageArgs &a, const int stage,
         if (!(rs > R(0)) || !isfinite(yo[L::IE])) atomicOr(a.flags, (unsigned)kFlagNonFinite);
 #pragma unroll
         for (int v = 0; v < NV; ++v) Yo[v * ncell + g] = yo[v];
+        if constexpr (RES) {
+#pragma unroll
+          for (int v = 0; v < NV; ++v) ys[m][v] = yo[v];
+        }
         if (stage == 2)
           rate_max = fmax(rate_max, cell_rate_r<R, L>(C, yo, P::er(D, k), P::ih(D, 0),
                                                       P::ih(D, 1), P::ih(D, 2)));
@@ -1417,7 +1468,8 @@ __device__ __forceinline__ void stage_tiles(const StageArgs &a, const int stage,
         bm = double(block_max_f(rate_max, reinterpret_cast<float *>(s_red + 1)));
       else
         bm = block_max(rate_max, s_red + 1);
-      if (tid == 0) atomicMax(D.rate, (unsigned long long)__double_as_longlong(bm));
+      if (tid == 0)
+        atomicMax(RES ? D.rate_next : D.rate, (unsigned long long)__double_as_longlong(bm));
     }
     __syncthreads();
   }
@@ -1427,7 +1479,8 @@ __device__ __forceinline__ void stage_tiles(const StageArgs &a, const int stage,
 template <class R, class L, bool VISC, class T, bool MICRO>
 __global__ void __launch_bounds__(T::NT, T::MINB) stage_kernel(const StageArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
-  stage_tiles<R, L, VISC, T, MICRO>(a, a.stage, smem);
+  R ys[Box<T, L::D3>::CPT][L::NV];
+  stage_tiles<R, L, VISC, T, MICRO>(a, a.stage, smem, ys);
 }
 
 // One whole step (three stages) in a single persistent cooperative launch: the CTAs walk the
@@ -1435,10 +1488,66 @@ __global__ void __launch_bounds__(T::NT, T::MINB) stage_kernel(const StageArgs a
 template <class R, class L, bool VISC, class T, bool MICRO>
 __global__ void __launch_bounds__(T::NT, T::MINB) step_kernel(const StageArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
+  R ys[Box<T, L::D3>::CPT][L::NV];
 #pragma unroll 1
   for (int st = 0; st < 3; ++st) {
-    stage_tiles<R, L, VISC, T, MICRO>(a, st, smem);
-    if (st < 2) grid_barrier(a.gsync, gridDim.x, a.flags);
+    stage_tiles<R, L, VISC, T, MICRO>(a, st, smem, ys);
+    if (st < 2) grid_barrier(a.gsync, gridDim.x, a.flags, a.spin_limit, a.absent_cta);
+  }
+}
+
+// One whole step in a single cooperative launch with one tile per CTA (every tile of the
+// launch co-resident): each CTA keeps its tile's state in registers through the three stages
+// and, between stages, waits only for the tiles its ghost cells come from -- a flag per tile,
+// set to 3 seq + s + 1 once the tile's stage-s output is in memory (seq counts the launches) --
+// instead of a grid barrier or a new launch. Waits are bounded like the grid barrier's. The
+// last CTA to finish moves each domain's next CFL rate into place and advances seq.
+template <class R, class L, bool VISC, class T, bool MICRO>
+__global__ void __launch_bounds__(T::NT, T::MINB) resident_step_kernel(const StageArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ unsigned int s_seq;
+  R ys[Box<T, L::D3>::CPT][L::NV];
+  const int tile = blockIdx.x, tid = threadIdx.x;
+  if (tid == 0) s_seq = ld_acquire_u32(&a.res->seq);
+  __syncthreads();
+  const unsigned int seq = s_seq;
+  const int d0 = a.dep_begin[tile], nd = a.dep_begin[tile + 1] - d0;
+#pragma unroll 1
+  for (int st = 0; st < 3; ++st) {
+    if (st > 0) {
+      // the tiles this one's ghost cells come from have finished stage st - 1
+      const unsigned int want = 3u * seq + unsigned(st);
+      for (int i = tid; i < nd; i += blockDim.x) {
+        const unsigned int *f = a.tile_flags + a.dep_list[d0 + i];
+        const long long t0 = clock64();
+        while (int(ld_acquire_u32(f) - want) < 0) {
+          if (clock64() - t0 > a.spin_limit) {
+            atomicOr(a.flags, (unsigned)kFlagTimeout);
+            break;
+          }
+          __nanosleep(20);
+        }
+      }
+      __syncthreads();
+    }
+    stage_tiles<R, L, VISC, T, MICRO, true>(a, st, smem, ys);  // ends with a CTA barrier
+    if (st < 2 && tid == 0) {
+      __threadfence();
+      st_release_u32(a.tile_flags + tile, 3u * seq + unsigned(st) + 1u);
+    }
+  }
+  if (tid == 0) {
+    __threadfence();
+    if (atomicAdd(&a.res->done, 1u) == gridDim.x - 1) {
+      __threadfence();
+      for (int d = 0; d < a.ndom; ++d) {
+        const DomDev &D = a.doms[d];
+        *D.rate = atomicExch(D.rate_next, 0ull);
+      }
+      a.res->done = 0u;
+      __threadfence();
+      st_release_u32(&a.res->seq, seq + 1u);
+    }
   }
 }
 
@@ -1551,8 +1660,34 @@ struct Variant {
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          int(S::total));
     if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(resident_step_kernel<R, L, VISC, T, MICRO>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, int(S::total));
+    if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(step_kernel<R, L, VISC, T, MICRO>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, int(S::total));
+  }
+  static int max_resident_tiles() {
+    int dev = 0, nsm = 0, per = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &per, resident_step_kernel<R, L, VISC, T, MICRO>, T::NT, S::total) != cudaSuccess)
+      return 0;
+    return per * nsm;
+  }
+  static cudaError_t resident(const StageArgs &a, int grid, cudaStream_t s) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(T::NT);
+    cfg.dynamicSmemBytes = S::total;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, resident_step_kernel<R, L, VISC, T, MICRO>, a);
   }
   static cudaError_t stage(const StageArgs &a, int grid, cudaStream_t s) {
     stage_kernel<R, L, VISC, T, MICRO><<<grid, T::NT, S::total, s>>>(a);
@@ -1592,6 +1727,8 @@ struct Variant {
     v.step = &step;
     v.max_resident_blocks = &max_resident_blocks;
     v.prepare = &prepare;
+    v.resident = &resident;
+    v.max_resident_tiles = &max_resident_tiles;
     return v;
   }
 };

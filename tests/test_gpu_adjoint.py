@@ -1,4 +1,4 @@
-"""Discrete adjoint in the CUDA library (SURVEY row a-12), dry and moist, against the
+"""Discrete adjoint in the CUDA library, dry and moist, against the
 oracle's adjoint (whose own pins are central differences of the oracle step), against central
 differences of the library's forward run, between FP32 and FP64, and across checkpoint
 spacings; and the gradients of the final kinetic energy and of a column's cloud mass with
@@ -144,10 +144,10 @@ def test_adjoint_dot_product_with_forward_differences(torch):
     assert rich == pytest.approx(np.sum(lam0 * v), rel=1e-6)
 
 
-def theta_gradient_check(torch, moving, tol, ndir=4):
-    from paper_1901_02955_gb300 import Context
-    from paper_1901_02955_gb300.autograd import SnapSteps, dry_state_from_theta, kinetic_energy
-    w = W.warm_bubble(n=48)
+def dry_theta_setup(torch, n, moving, seed=46):
+    """Warm bubble on n x n cells as a potential-temperature field theta_0 on the reference
+    pressure, optionally with a seeded random velocity field of +-2 m/s per component."""
+    w = W.warm_bubble(n=n)
     pk = torch.tensor(0.5 * (w.p_bar_face[:-1] + w.p_bar_face[1:]), dtype=torch.float64,
                       device="cuda")
     kappa = (w.gamma_d - 1.0) / w.gamma_d
@@ -156,41 +156,88 @@ def theta_gradient_check(torch, moving, tol, ndir=4):
                           dtype=torch.float64, device="cuda")
     vel = None
     if moving:
-        rs = np.random.default_rng(46)
+        rs = np.random.default_rng(seed)
         vel = torch.tensor(rs.uniform(-2.0, 2.0, size=(2,) + theta0.shape), device="cuda")
-    ctx = Context(w, dtype="f64")
-    dt = 0.5 * Oracle(w).dt_cfl(w.Y, 0.8)
-    nsteps = 12
+    return w, pk, theta0, vel
+
+
+def directional_checks(torch, J_cells, theta0, grad, ndir, seed, h=1e-4):
+    """Adjoint directional derivatives grad . d against central differences of J along ndir
+    seeded Gaussian directions d. J_cells(theta) returns J's per-cell terms (summed after the
+    difference: J is a large sum against differences of order h, so the difference of two
+    sums would carry the sums' rounding). Returns per direction (g, rich, fd_h, fd_2h): the
+    adjoint value, the Richardson extrapolation (4 fd_h - fd_2h) / 3 and the two central
+    differences."""
+    out = []
+    rs = np.random.default_rng(seed)
+    for _ in range(ndir):
+        d = torch.tensor(rs.normal(size=tuple(theta0.shape)), device="cuda",
+                         dtype=theta0.dtype)
+        with torch.no_grad():
+            def fd(hh):
+                return float((J_cells(theta0 + hh * d) - J_cells(theta0 - hh * d)).sum()) / (2 * hh)
+            f1, f2 = fd(h), fd(2 * h)
+        out.append((float((grad * d).sum()), (4.0 * f1 - f2) / 3.0, f1, f2))
+    return out
+
+
+def smooth_along(f1, f2, rtol=1e-6, floor=0.0):
+    """A central difference of a smooth J changes with h only at O(h^2) (relative ~1e-8 for
+    h = 1e-4 K here); one whose stencil straddles a kink of J (an LMARS upwind switch at
+    u* = 0, a cloud edge) changes at first order in the kink's jump. The two differences at
+    h and 2h disagreeing beyond rtol therefore marks a direction along which J is not smooth
+    within +-2h, where no derivative exists to compare with."""
+    return abs(f1 - f2) <= rtol * max(abs(f1), floor)
+
+
+def dry_ke_gradient(torch, n, nsteps, ckpt, ndir, moving, dtype="f64", dt=None, seed=45):
+    """dJ/dtheta_0 of the final kinetic energy through torch.autograd (initial-state map in
+    torch, steps and adjoint in the library) and its directional checks."""
+    from paper_1901_02955_gb300 import Context
+    from paper_1901_02955_gb300.autograd import SnapSteps, dry_state_from_theta, kinetic_energy
+    w, pk, theta0, vel = dry_theta_setup(torch, n, moving)
+    ctx = Context(w, dtype=dtype)
+    if dt is None:
+        dt = 0.5 * Oracle(w).dt_cfl(w.Y, 0.8)
     vol = w.dx * w.dz
+    tdt = torch.float32 if dtype == "f32" else torch.float64
 
     def final(theta):
         Y0 = dry_state_from_theta(theta, pk, w.R_d, w.gamma_d, velocity=vel)
-        return SnapSteps.apply(Y0.contiguous(), ctx, nsteps, 5, dt)
-
-    def J(theta):
-        return kinetic_energy(final(theta), vol)
+        return SnapSteps.apply(Y0.to(tdt).contiguous(), ctx, nsteps, ckpt, dt)
 
     def ke_cells(Y):
+        Y = Y.double()
         return 0.5 * (Y[1:-1] ** 2).sum(dim=0) / Y[0] * vol
 
     th = theta0.clone().requires_grad_(True)
-    J(th).backward()
+    kinetic_energy(final(th).double(), vol).backward()
     grad = th.grad.detach()
-    # g = grad . d over Gaussian directions d has standard deviation |grad|; a direction that
-    # is nearly orthogonal to the gradient (|g| far below that) is held to the relative
-    # tolerance of 1 % of the typical size, not of its own tiny derivative
+    checks = directional_checks(torch, lambda t: ke_cells(final(t)), theta0, grad, ndir,
+                                seed) if ndir else []
+    ctx.close()
+    return grad, checks
+
+
+def assert_directions(checks, grad, tol, min_smooth=1.0):
+    """Every direction along which J is smooth within the differences' stencil agrees to tol
+    (relative, with a floor of 1 % of |grad| for directions nearly orthogonal to it: g = grad
+    . d over Gaussian d has standard deviation |grad|); at least min_smooth of them are
+    smooth. Returns the fraction of directions that straddle a kink."""
     floor = 0.01 * float(grad.norm())
-    rs = np.random.default_rng(45)
-    for _ in range(ndir):
-        d = torch.tensor(rs.normal(size=theta0.shape), device="cuda")
-        with torch.no_grad():
-            def fd(h):
-                # cell by cell before the sum: J ~ 1e6 against differences ~ 1e-5, so the
-                # difference of the two sums would carry the sums' rounding (~1e-10)
-                return float((ke_cells(final(theta0 + h * d)) -
-                              ke_cells(final(theta0 - h * d))).sum()) / (2 * h)
-            rich = (4.0 * fd(1e-4) - fd(2e-4)) / 3.0
-        g = float((grad * d).sum())
+    smooth = [smooth_along(f1, f2, 1e-6, floor) for _, _, f1, f2 in checks]
+    for (g, rich, f1, f2), ok in zip(checks, smooth):
+        if ok:
+            assert abs(rich - g) <= tol * max(abs(g), floor), (rich, g, f1, f2)
+    frac_kink = 1.0 - sum(smooth) / len(smooth)
+    assert 1.0 - frac_kink >= min_smooth, frac_kink
+    return frac_kink
+
+
+def theta_gradient_check(torch, moving, tol, ndir=4):
+    grad, checks = dry_ke_gradient(torch, 48, 12, 5, ndir, moving)
+    floor = 0.01 * float(grad.norm())
+    for g, rich, _, _ in checks:
         assert abs(rich - g) <= tol * max(abs(g), floor), (rich, g)
 
 

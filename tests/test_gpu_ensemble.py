@@ -1,4 +1,4 @@
-"""Ensemble launch modes: every tile shape and the persistent one-launch
+"""Ensemble launch modes (many domains in the same launches): every tile shape and the persistent one-launch
 step give the same result as the default three-launch step (the per-cell and per-face
 arithmetic does not depend on the tiling), and the autotuner leaves the state untouched.
 Dry layouts agree bitwise. With the saturation adjustment two compiled instances of the same
@@ -128,3 +128,65 @@ def test_autotune_keeps_state_and_picks_a_mode():
     ctx.step(3)
     ref, _ = run(ws, "f32")
     assert all(agree(ctx.get_state(domain=d), ref[d], exact=False) for d in range(len(ws)))
+
+
+def test_persistent_barrier_timeout_reports_and_recovers():
+    """A persistent step whose grid-barrier waits run out -- CTA 0 told to skip its arrivals,
+    every wait limited to about 1 ms -- returns SNAP_ETIMEOUT instead of hanging, and the
+    next normal step starts from a cleared barrier: bitwise the three-launch step."""
+    from paper_1901_02955_gb300 import Context, SnapError, capi
+    ws = [W.add_random_motion(W.density_current(nx=70, nz=37, dtype="f32"))]
+    ref, _ = run(ws, "f32", steps=2)
+    ctx = Context(ws, dtype="f32")
+    ctx.use_persistent(True)
+    assert ctx.info()["persistent_grid"] >= 2
+    ctx.set_state(ws[0].Y)
+    ctx.set_barrier_test(spin_cycles=2_000_000, absent_cta=0)
+    with pytest.raises(SnapError) as err:
+        ctx.step(1)
+    assert err.value.code == capi.ETIMEOUT
+    ctx.set_barrier_test(0, -1)
+    ctx.reset_flags()
+    ctx.set_state(ws[0].Y)
+    ctx.step(2)
+    assert np.array_equal(ctx.get_state(), ref[0])
+    ctx.close()
+
+
+def test_resident_step_matches_three_launches():
+    """The resident step (one tile per CTA for all three stages, neighbour flags between
+    stages) against three launches: bitwise for dry layouts (ragged tiles, walls, periodic,
+    3-D, several domains), to the moist tolerance with the saturation adjustment."""
+    cases = [
+        ([W.add_random_motion(W.density_current(nx=70, nz=37, dtype="f32"))], "f32", True),
+        ([W.add_random_motion(W.density_current(nx=70, nz=37, dtype="f64"))], "f64", True),
+        ([W.add_random_motion(W.dry_bubble_3d(nx=19, ny=10, nz=9))], "f32", True),
+        ([W.add_random_motion(W.warm_bubble(n=5))], "f64", True),
+        (members(), "f32", False),
+    ]
+    for ws, dtype, exact in cases:
+        ref, _ = run(ws, dtype, steps=4)
+        out, info = run(ws, dtype, persistent=2, steps=4)
+        assert info["persistent"] == 2 and info["kernel_launches_per_step"] == 1
+        for a, b in zip(out, ref):
+            assert agree(a, b, exact), (ws[0].name, dtype)
+
+
+def test_resident_step_on_the_density_current_grid():
+    """The 1024 x 256 density current: 304 tiles of 64 x 14 cells, two per SM -- the grid the
+    resident step is for; bitwise the three-launch step, with the CFL time step carried from
+    step to step through the launch's last CTA."""
+    ws = [W.density_current(dtype="f32")]
+    ref, _ = run(ws, "f32", steps=3)
+    out, info = run(ws, "f32", persistent=2, steps=3)
+    assert info["tiles_total"] == 304
+    assert np.array_equal(out[0], ref[0])
+
+
+def test_resident_step_refuses_grids_beyond_one_wave():
+    from paper_1901_02955_gb300 import Context, SnapError, capi
+    ctx = Context(W.density_current(nx=4096, nz=256, dtype="f32"), dtype="f32")
+    with pytest.raises(SnapError) as e:
+        ctx.use_persistent(2)
+    assert e.value.code == capi.ENOTSUP
+    ctx.close()
