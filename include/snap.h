@@ -261,11 +261,12 @@ int snap_use_persistent(snap_ctx *ctx, int enable);
  * launch starts from a cleared barrier, so the next normal step is unaffected. Takes effect
  * from the next step (a captured graph is rebuilt). */
 int snap_set_barrier_test(snap_ctx *ctx, long long spin_cycles, int absent_cta);
-/* Autotuner: times `steps` steps of every tile shape in both launch modes on the current
- * state (which is restored afterwards) and keeps the fastest. best_ms (may be NULL) receives
- * its time per step, choice (may be NULL) variant * 3 + launch mode (snap_use_persistent).
- * Allocates one temporary
- * copy of the state. */
+/* Autotuner: times `steps` steps of every tile shape in every launch mode that applies
+ * (snap_use_persistent) on the current state, which is restored afterwards; with several
+ * size classes it also times each class alone on every shape and then the step with every
+ * class on its fastest shape, and keeps whichever configuration is fastest. best_ms (may be
+ * NULL) receives its time per step; choice (may be NULL) variant * 3 + launch mode, or -1 for
+ * per-class shapes (snap_get_class_info). Allocates one temporary copy of the state. */
 int snap_autotune(snap_ctx *ctx, int steps, double *best_ms, int *choice);
 
 /* Sizes the context was built with. */
@@ -281,8 +282,23 @@ typedef struct snap_info {
   int n_tile_variants;
   int persistent;             /* 1: one cooperative launch per step */
   int persistent_grid;        /* CTAs of that launch (all co-resident) */
+  int n_size_classes;         /* groups of domains of identical nx, ny, nz */
+  int per_class_tiles;        /* 1: each size class on its own tile shape (see
+                                 snap_set_class_tile_variant) */
 } snap_info;
 int snap_get_info(const snap_ctx *ctx, snap_info *info);
+/* Tile shapes per size class. The domains of a context fall into size classes (identical
+ * nx, ny, nz; numbered in the order of their first domain). snap_set_class_tile_variant
+ * gives class cls its own tile shape (an index as for snap_set_tile_variant); from then on,
+ * in the three-launch mode, every stage is one launch per class, the classes' launches
+ * running in parallel on streams of the context (forked from and joined back into its
+ * stream; parallel branches of the step's graph). snap_set_tile_variant returns every class
+ * to the one shape. The persistent and resident modes run one kernel, so one shape: they
+ * ignore the classes' shapes. snap_get_class_info reports a class's domain count, cells per
+ * domain, tile shape and variant (NULL pointers are skipped). */
+int snap_set_class_tile_variant(snap_ctx *ctx, int cls, int variant);
+int snap_get_class_info(const snap_ctx *ctx, int cls, int *n_domains, int *cells, int tile[3],
+                        int *variant);
 
 /* Slab decomposition of one domain along x (the ghost cells of a SNAP_HALO side).
  *

@@ -29,6 +29,7 @@ EXPORTS = ["snap_init_grid", "snap_set_state", "snap_get_state", "snap_step", "s
            "snap_set_stream",
            "snap_use_graph", "snap_set_tile_variant", "snap_use_persistent", "snap_autotune",
            "snap_set_barrier_test", "snap_link_halo", "snap_halo_buffer", "snap_halo_pack",
+           "snap_set_class_tile_variant", "snap_get_class_info",
            "snap_get_info", "snap_buffer_pointer", "snap_budget_noalloc", "snap_theta_e",
            "snap_probe_fma", "snap_check_rcp64", "snap_check_weno",
            "snap_free", "snap_last_error", "snap_status_string"]
@@ -69,7 +70,8 @@ class Info(C.Structure):
                 ("state_bytes", C.c_longlong), ("tile", C.c_int * 3), ("tiles_total", C.c_int),
                 ("kernel_launches_per_step", C.c_int), ("tile_variant", C.c_int),
                 ("n_tile_variants", C.c_int), ("persistent", C.c_int),
-                ("persistent_grid", C.c_int)]
+                ("persistent_grid", C.c_int), ("n_size_classes", C.c_int),
+                ("per_class_tiles", C.c_int)]
 
 
 class SnapError(RuntimeError):
@@ -112,6 +114,9 @@ def load(path: Optional[str] = None) -> C.CDLL:
     lib.snap_autotune.argtypes = [P, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int)]
     lib.snap_set_barrier_test.argtypes = [P, C.c_longlong, C.c_int]
     lib.snap_link_halo.argtypes = [P, C.c_int, C.c_int, C.c_int]
+    lib.snap_set_class_tile_variant.argtypes = [P, C.c_int, C.c_int]
+    lib.snap_get_class_info.argtypes = [P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                        C.POINTER(C.c_int), C.POINTER(C.c_int)]
     lib.snap_halo_buffer.argtypes = [P, C.c_int, C.c_int, C.POINTER(P)]
     lib.snap_halo_pack.argtypes = [P, C.c_int, C.c_int, C.c_int, P, P]
     lib.snap_buffer_pointer.argtypes = [P, C.c_int, C.c_int, C.POINTER(P)]
@@ -302,7 +307,20 @@ class Context:
                 "state_bytes": i.state_bytes, "tile": tuple(i.tile), "tiles_total": i.tiles_total,
                 "kernel_launches_per_step": i.kernel_launches_per_step,
                 "tile_variant": i.tile_variant, "n_tile_variants": i.n_tile_variants,
-                "persistent": i.persistent, "persistent_grid": i.persistent_grid}
+                "persistent": i.persistent, "persistent_grid": i.persistent_grid,
+                "n_size_classes": i.n_size_classes, "per_class_tiles": i.per_class_tiles,
+                "classes": [self.class_info(c) for c in range(i.n_size_classes)]}
+
+    def class_info(self, cls):
+        nd, cells, var = C.c_int(0), C.c_int(0), C.c_int(0)
+        tile = (C.c_int * 3)()
+        self._check(self.lib.snap_get_class_info(self._ptr, cls, C.byref(nd), C.byref(cells),
+                                                 tile, C.byref(var)))
+        return {"domains": nd.value, "cells": cells.value, "tile": tuple(tile),
+                "variant": var.value}
+
+    def set_class_tile_variant(self, cls, variant):
+        return self._check(self.lib.snap_set_class_tile_variant(self._ptr, cls, variant))
 
     def set_tile_variant(self, variant):
         return self._check(self.lib.snap_set_tile_variant(self._ptr, variant))
@@ -321,6 +339,10 @@ class Context:
         ms = C.c_double(0.0)
         choice = C.c_int(0)
         self._check(self.lib.snap_autotune(self._ptr, steps, C.byref(ms), C.byref(choice)))
+        if choice.value < 0:
+            return {"ms_per_step": ms.value, "variant": None, "persistent": 0,
+                    "per_class": [self.class_info(c)["variant"]
+                                  for c in range(self.info()["n_size_classes"])]}
         return {"ms_per_step": ms.value, "variant": choice.value // 3,
                 "persistent": choice.value % 3}
 

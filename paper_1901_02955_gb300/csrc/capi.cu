@@ -130,6 +130,20 @@ struct snap_ctx {
   int *dep_begin = nullptr, *dep_list = nullptr;
   unsigned long long *rate_next_dev = nullptr;
   int res_ready = 0, res_tv = -1;
+  // size classes (domains of identical nx, ny, nz) and their own tile shapes: with per_class
+  // set (three-launch mode only), a stage is one launch per class on parallel streams, each
+  // over the class's own tile table (cls_dom, uploaded to cls_doms_dev / cls_prefix_dev)
+  std::vector<std::vector<int>> cls;
+  std::vector<int> cls_tv, cls_ntiles, cls_off;
+  int per_class = 0;
+  std::vector<DomDev> cls_dom;
+  std::vector<int> cls_prefix;
+  DomDev *cls_doms_dev = nullptr;
+  int *cls_prefix_dev = nullptr;
+  std::vector<cudaStream_t> cls_streams;
+  cudaEvent_t ev_fork = nullptr;
+  std::vector<cudaEvent_t> ev_join;
+  int only_class = -1;  // autotuner: launch this class alone
   // discrete adjoint (dry, inviscid, one domain): recording and work buffers
   int has_adj = 0;
   AdjKernels adj{};
@@ -201,6 +215,11 @@ static void release(snap_ctx *ctx) {
   cudaFree(ctx->dep_begin);
   cudaFree(ctx->dep_list);
   cudaFree(ctx->rate_next_dev);
+  cudaFree(ctx->cls_doms_dev);
+  cudaFree(ctx->cls_prefix_dev);
+  for (cudaStream_t st : ctx->cls_streams) cudaStreamDestroy(st);
+  for (cudaEvent_t ev : ctx->ev_join) cudaEventDestroy(ev);
+  if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
   cudaFree(ctx->ckpt);
   cudaFree(ctx->segbuf);
   cudaFree(ctx->dt_hist);
@@ -426,6 +445,7 @@ static int halos_ready(snap_ctx *ctx, const char *who) {
 }
 
 static int apply_variant(snap_ctx *ctx, int v);
+static int build_class_tables(snap_ctx *ctx);
 
 // Default tile shape: the first variant (in the order built, the fastest on large grids) whose
 // tiles over all domains fill every SM at least once; else the one with the most tiles.
@@ -654,6 +674,18 @@ extern "C" int snap_init_grid(snap_ctx **out, const snap_grid_desc *d, int n_dom
     int mrb = ctx->ks.var[0].max_resident_blocks();
     ctx->grid_persistent = mrb < ctx->ntiles ? mrb : ctx->ntiles;
   }
+  for (int i = 0; i < n_domains; ++i) {
+    int c = 0;
+    while (c < (int)ctx->cls.size()) {
+      const DomDev &A = ctx->dom[ctx->cls[c][0]];
+      if (A.nx == ctx->dom[i].nx && A.ny == ctx->dom[i].ny && A.nz == ctx->dom[i].nz) break;
+      ++c;
+    }
+    if (c == (int)ctx->cls.size()) ctx->cls.emplace_back();
+    ctx->cls[c].push_back(i);
+  }
+  ctx->cls_tv.assign(ctx->cls.size(), 0);
+  ctx->cls_ntiles.assign(ctx->cls.size(), 0);
   if (const int v = default_variant(ctx)) {
     if ((ret = apply_variant(ctx, v)) != SNAP_OK) {
       g_init_error = "snap_init_grid: " + ctx->err;
@@ -685,6 +717,8 @@ static int apply_variant(snap_ctx *ctx, int v) {
   ctx->grid_persistent = mrb < ctx->ntiles ? mrb : ctx->ntiles;
   ctx->tv = v;
   ctx->res_ready = 0;
+  for (int &t : ctx->cls_tv) t = v;
+  ctx->per_class = 0;
   CK(cudaMemcpyAsync(ctx->doms_dev, ctx->dom.data(), sizeof(DomDev) * ctx->ndom,
                      cudaMemcpyHostToDevice, ctx->stream));
   CK(cudaMemcpyAsync(ctx->prefix_dev, ctx->prefix.data(), sizeof(int) * (ctx->ndom + 1),
@@ -767,9 +801,91 @@ static int set_dt_fixed(snap_ctx *ctx, double dt_fixed) {
       changed = true;
     }
   }
-  if (changed)
+  if (changed) {
     CK(cudaMemcpyAsync(ctx->doms_dev, ctx->dom.data(), sizeof(DomDev) * ctx->ndom,
                        cudaMemcpyHostToDevice, ctx->stream));
+    if (ctx->per_class || ctx->only_class >= 0) return build_class_tables(ctx);
+  }
+  return SNAP_OK;
+}
+
+// Tile tables of the size classes for their own tile shapes: each class's domains (copies of
+// the context's, re-tiled) with tile numbers starting at 0 within the class.
+static int build_class_tables(snap_ctx *ctx) {
+  const int nc = (int)ctx->cls.size();
+  ctx->cls_dom.clear();
+  ctx->cls_prefix.clear();
+  ctx->cls_off.assign(nc, 0);
+  for (int c = 0; c < nc; ++c) {
+    const int *tl = ctx->ks.var[ctx->cls_tv[c]].tile;
+    ctx->cls_off[c] = (int)ctx->cls_dom.size();
+    int t = 0;
+    ctx->cls_prefix.push_back(0);
+    for (int i : ctx->cls[c]) {
+      DomDev D = ctx->dom[i];
+      D.tx = (D.nx + tl[0] - 1) / tl[0];
+      D.ty = (D.ny + tl[1] - 1) / tl[1];
+      D.tz = (D.nz + tl[2] - 1) / tl[2];
+      D.tile_begin = t;
+      t += D.tx * D.ty * D.tz;
+      ctx->cls_dom.push_back(D);
+      ctx->cls_prefix.push_back(t);
+    }
+    ctx->cls_ntiles[c] = t;
+  }
+  if (!ctx->cls_doms_dev) {
+    CK(cudaMalloc(&ctx->cls_doms_dev, sizeof(DomDev) * ctx->ndom));
+    CK(cudaMalloc(&ctx->cls_prefix_dev, sizeof(int) * (ctx->ndom + nc)));
+  }
+  CK(cudaMemcpyAsync(ctx->cls_doms_dev, ctx->cls_dom.data(), sizeof(DomDev) * ctx->ndom,
+                     cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->cls_prefix_dev, ctx->cls_prefix.data(), sizeof(int) * (ctx->ndom + nc),
+                     cudaMemcpyHostToDevice, ctx->stream));
+  if (ctx->cls_streams.empty()) {
+    ctx->cls_streams.assign(nc, nullptr);
+    ctx->ev_join.assign(nc, nullptr);
+    for (int c = 0; c < nc; ++c) {
+      CK(cudaStreamCreateWithFlags(&ctx->cls_streams[c], cudaStreamNonBlocking));
+      CK(cudaEventCreateWithFlags(&ctx->ev_join[c], cudaEventDisableTiming));
+    }
+    CK(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  return SNAP_OK;
+}
+
+// One stage of every domain in the three-launch mode: a single launch over the context's
+// tile table, or, with per-class tile shapes, one launch per size class on the classes'
+// streams, forked from and joined back into s (parallel branches of a captured graph). The
+// autotuner's only_class launches that class alone on s.
+static int launch_stage(snap_ctx *ctx, const StageArgs &base, int stage, cudaStream_t s) {
+  StageArgs a = base;
+  a.stage = stage;
+  if (!ctx->per_class && ctx->only_class < 0) {
+    CK(ctx->ks.var[ctx->tv].stage(a, ctx->grid, s));
+    return SNAP_OK;
+  }
+  const int nc = (int)ctx->cls.size();
+  auto args_c = [&](int c) {
+    StageArgs b = a;
+    b.doms = ctx->cls_doms_dev + ctx->cls_off[c];
+    b.tile_domain = ctx->cls_prefix_dev + ctx->cls_off[c] + c;
+    b.ndom = (int)ctx->cls[c].size();
+    b.ntiles = ctx->cls_ntiles[c];
+    return b;
+  };
+  if (ctx->only_class >= 0) {
+    const int c = ctx->only_class;
+    CK(ctx->ks.var[ctx->cls_tv[c]].stage(args_c(c), ctx->cls_ntiles[c], s));
+    return SNAP_OK;
+  }
+  CK(cudaEventRecord(ctx->ev_fork, s));
+  for (int c = 0; c < nc; ++c) {
+    CK(cudaStreamWaitEvent(ctx->cls_streams[c], ctx->ev_fork, 0));
+    CK(ctx->ks.var[ctx->cls_tv[c]].stage(args_c(c), ctx->cls_ntiles[c], ctx->cls_streams[c]));
+    CK(cudaEventRecord(ctx->ev_join[c], ctx->cls_streams[c]));
+  }
+  for (int c = 0; c < nc; ++c) CK(cudaStreamWaitEvent(s, ctx->ev_join[c], 0));
   return SNAP_OK;
 }
 
@@ -877,9 +993,10 @@ static int enqueue_stages(snap_ctx *ctx, cudaStream_t s) {
     CK(tv.step(a, ctx->grid_persistent, s));
     return SNAP_OK;
   }
+  const StageArgs a = args_of(ctx, 0);
   for (int st = 0; st < 3; ++st) {
-    StageArgs a = args_of(ctx, st);
-    CK(tv.stage(a, ctx->grid, s));
+    const int rc = launch_stage(ctx, a, st, s);
+    if (rc) return rc;
   }
   return SNAP_OK;
 }
@@ -891,9 +1008,7 @@ extern "C" int snap_stage(snap_ctx *ctx, int stage, double dt_fixed) {
   if (rc) return rc;
   rc = set_dt_fixed(ctx, dt_fixed);
   if (rc) return rc;
-  StageArgs a = args_of(ctx, stage);
-  CK(ctx->ks.var[ctx->tv].stage(a, ctx->grid, ctx->stream));
-  return SNAP_OK;
+  return launch_stage(ctx, args_of(ctx, 0), stage, ctx->stream);
 }
 
 extern "C" int snap_step_async(snap_ctx *ctx, int nsteps, double dt_fixed) {
@@ -1306,6 +1421,32 @@ extern "C" int snap_set_tile_variant(snap_ctx *ctx, int variant) {
   return apply_variant(ctx, variant);
 }
 
+extern "C" int snap_set_class_tile_variant(snap_ctx *ctx, int cls, int variant) {
+  if (!ctx) return fail(nullptr, SNAP_EINVAL, "snap_set_class_tile_variant: NULL context");
+  if (cls < 0 || cls >= (int)ctx->cls.size() || variant < 0 || variant >= ctx->ks.nvariants)
+    return fail(ctx, SNAP_EINVAL, "snap_set_class_tile_variant: no such size class or variant");
+  ctx->cls_tv[cls] = variant;
+  ctx->per_class = 1;
+  if (ctx->graph) {
+    cudaGraphExecDestroy(ctx->graph);
+    ctx->graph = nullptr;
+  }
+  return build_class_tables(ctx);
+}
+
+extern "C" int snap_get_class_info(const snap_ctx *ctx, int cls, int *n_domains, int *cells,
+                                   int tile[3], int *variant) {
+  if (!ctx || cls < 0 || cls >= (int)ctx->cls.size()) return SNAP_EINVAL;
+  const int v = ctx->per_class ? ctx->cls_tv[cls] : ctx->tv;
+  const DomDev &D = ctx->dom[ctx->cls[cls][0]];
+  if (n_domains) *n_domains = (int)ctx->cls[cls].size();
+  if (cells) *cells = D.nx * D.ny * D.nz;
+  if (tile)
+    for (int i = 0; i < 3; ++i) tile[i] = ctx->ks.var[v].tile[i];
+  if (variant) *variant = v;
+  return SNAP_OK;
+}
+
 extern "C" int snap_use_persistent(snap_ctx *ctx, int enable) {
   if (!ctx) return fail(nullptr, SNAP_EINVAL, "snap_use_persistent: NULL context");
   if (enable < 0 || enable > 2) return fail(ctx, SNAP_EINVAL, "snap_use_persistent: mode 0, 1 or 2");
@@ -1373,6 +1514,54 @@ extern "C" int snap_autotune(snap_ctx *ctx, int steps, double *best_ms, int *cho
       }
     }
   }
+  // per size class: the fastest shape for each class launched alone, then the whole step with
+  // every class on its own shape (three launches per class, in parallel) against the best
+  // single shape
+  const int nc = (int)ctx->cls.size();
+  std::vector<int> cls_best(nc, 0);
+  bool use_classes = false;
+  auto time_steps = [&](double &ms_out) -> int {
+    int r = snap_step_async(ctx, 1, 0.0);  // warm-up
+    if (r) return r;
+    CK(cudaEventRecord(e0, ctx->stream));
+    r = snap_step_async(ctx, steps, 0.0);
+    if (r) return r;
+    CK(cudaEventRecord(e1, ctx->stream));
+    CK(cudaEventSynchronize(e1));
+    float ms = 0.0f;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    ms_out = ms / steps;
+    return SNAP_OK;
+  };
+  if (nc > 1 && rc == SNAP_OK && ctx->ks.nvariants > 1) {
+    ctx->persistent = 0;
+    for (int c = 0; c < nc && rc == SNAP_OK; ++c) {
+      double bc = 1e300;
+      for (int v = 0; v < ctx->ks.nvariants && rc == SNAP_OK; ++v) {
+        ctx->cls_tv[c] = v;
+        ctx->only_class = c;
+        if ((rc = build_class_tables(ctx))) break;
+        double ms = 0.0;
+        if ((rc = time_steps(ms))) break;
+        if (ms < bc) {
+          bc = ms;
+          cls_best[c] = v;
+        }
+      }
+    }
+    ctx->only_class = -1;
+    if (rc == SNAP_OK) {
+      ctx->cls_tv = cls_best;
+      ctx->per_class = 1;
+      double ms = 0.0;
+      if ((rc = build_class_tables(ctx)) == SNAP_OK && (rc = time_steps(ms)) == SNAP_OK &&
+          ms < best) {
+        best = ms;
+        use_classes = true;
+      }
+      ctx->per_class = 0;
+    }
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   off = 0;
@@ -1390,8 +1579,14 @@ extern "C" int snap_autotune(snap_ctx *ctx, int steps, double *best_ms, int *cho
   rc = apply_variant(ctx, best_v);
   if (rc) return rc;
   ctx->persistent = best_p;
+  if (use_classes) {
+    ctx->persistent = 0;
+    ctx->cls_tv = cls_best;
+    ctx->per_class = 1;
+    if ((rc = build_class_tables(ctx))) return rc;
+  }
   if (best_ms) *best_ms = best;
-  if (choice) *choice = best_v * 3 + best_p;
+  if (choice) *choice = use_classes ? -1 : best_v * 3 + best_p;
   CK(cudaMemsetAsync(ctx->flags_dev, 0, sizeof(unsigned int), ctx->stream));
   return SNAP_OK;
 }
@@ -1428,6 +1623,9 @@ extern "C" int snap_get_info(const snap_ctx *ctx, snap_info *info) {
   info->n_tile_variants = ctx->ks.nvariants;
   info->persistent = ctx->persistent;
   info->persistent_grid = ctx->grid_persistent;
+  info->n_size_classes = (int)ctx->cls.size();
+  info->per_class_tiles = ctx->per_class;
+  if (ctx->per_class) info->kernel_launches_per_step = 3 * (int)ctx->cls.size();
   return SNAP_OK;
 }
 
@@ -1460,6 +1658,10 @@ extern "C" int snap_link_halo(snap_ctx *ctx, int domain, int side, int nbr) {
   if (ctx->graph) {
     cudaGraphExecDestroy(ctx->graph);
     ctx->graph = nullptr;
+  }
+  if (ctx->per_class) {
+    const int rc = build_class_tables(ctx);
+    if (rc) return rc;
   }
   return refresh_rate(ctx, domain, ctx->stream);
 }

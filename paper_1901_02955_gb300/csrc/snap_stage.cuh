@@ -29,8 +29,14 @@ struct Ar<float> {
   // a b + c rounded once, whatever the compiler would contract: the same source then rounds
   // the same way in every kernel it is inlined into
   static __device__ __forceinline__ float fma_(float a, float b, float c) { return __fmaf_rn(a, b, c); }
-  // approximate reciprocal (hardware rcp, ~1 ulp) -- FP32 path only
-  static __device__ __forceinline__ float rcp(float x) { return __fdividef(1.0f, x); }
+  // approximate reciprocal: the special-function unit's rcp.approx.ftz.f32 alone (~1 ulp; a
+  // subnormal argument or result flushes to zero, which no reciprocal of the scheme meets:
+  // densities, eps + beta >= 1e-6 and the weight sums are normal numbers)
+  static __device__ __forceinline__ float rcp(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+  }
   static __device__ __forceinline__ float div(float a, float b) { return __fdividef(a, b); }
   static __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
   static __device__ __forceinline__ float exp_(float x) { return expf(x); }
@@ -148,6 +154,51 @@ struct Box {
       if ((unsigned)oz < (unsigned)T::TZ)  // y halo: by in 0..2 or TY+3..TY+5
         return NXB + (oz * 6 + (by < 3 ? by : by - T::TY)) * T::TX + (bx - 3);
       return NXB + NYH + ((bz < 3 ? bz : bz - T::TZ) * T::TY + oy) * T::TX + (bx - 3);
+    }
+  }
+};
+
+// Shared-memory arrays of NV fields per location (primitives, face states, fluxes) keep the
+// fields of one location together in groups of G (16 bytes for 4 floats or 2 doubles, 8 for
+// 2 floats; G = 1 when NV has no such divisor): element (v, i) of an N-location array sits at
+// ((v / G) N + i) G + v % G, so one vector access moves a group and a window point, face state
+// or flux of the four dry fields is one 16-byte access instead of four.
+template <class R, int NV>
+struct SV {
+  static constexpr int G = sizeof(R) == 4 ? (NV % 4 == 0 ? 4 : (NV % 2 == 0 ? 2 : 1))
+                                          : (NV % 2 == 0 ? 2 : 1);
+  static __device__ __forceinline__ int at(int v, int i, int N) { return ((v / G) * N + i) * G + v % G; }
+  static __device__ __forceinline__ void load(const R *base, int i, int N, R *out) {
+#pragma unroll
+    for (int g = 0; g < NV / G; ++g) {
+      const R *p = base + (g * N + i) * G;
+      if constexpr (G == 4) {
+        const float4 t = *reinterpret_cast<const float4 *>(p);
+        out[4 * g] = t.x, out[4 * g + 1] = t.y, out[4 * g + 2] = t.z, out[4 * g + 3] = t.w;
+      } else if constexpr (G == 2 && sizeof(R) == 4) {
+        const float2 t = *reinterpret_cast<const float2 *>(p);
+        out[2 * g] = t.x, out[2 * g + 1] = t.y;
+      } else if constexpr (G == 2) {
+        const double2 t = *reinterpret_cast<const double2 *>(p);
+        out[2 * g] = t.x, out[2 * g + 1] = t.y;
+      } else {
+        out[g] = *p;
+      }
+    }
+  }
+  static __device__ __forceinline__ void store(R *base, int i, int N, const R *in) {
+#pragma unroll
+    for (int g = 0; g < NV / G; ++g) {
+      R *p = base + (g * N + i) * G;
+      if constexpr (G == 4) {
+        *reinterpret_cast<float4 *>(p) = make_float4(in[4 * g], in[4 * g + 1], in[4 * g + 2], in[4 * g + 3]);
+      } else if constexpr (G == 2 && sizeof(R) == 4) {
+        *reinterpret_cast<float2 *>(p) = make_float2(in[2 * g], in[2 * g + 1]);
+      } else if constexpr (G == 2) {
+        *reinterpret_cast<double2 *>(p) = make_double2(in[2 * g], in[2 * g + 1]);
+      } else {
+        *p = in[g];
+      }
     }
   }
 };
@@ -903,7 +954,7 @@ __device__ __forceinline__ void weno5_pair(R a, R b, R c, R d, R e, R eps, R &qm
 // reciprocals stay scalar on the special-function unit.
 __device__ __forceinline__ float2 f2c(float x) { return make_float2(x, x); }
 __device__ __forceinline__ float2 f2rcp(float2 x) {
-  return make_float2(__fdividef(1.0f, x.x), __fdividef(1.0f, x.y));
+  return make_float2(Ar<float>::rcp(x.x), Ar<float>::rcp(x.y));
 }
 __device__ __forceinline__ void weno5_pair2(float2 a, float2 b, float2 c, float2 d, float2 e,
                                             float eps, float2 &qm, float2 &qp) {
@@ -983,8 +1034,8 @@ __device__ __forceinline__ R cell_rate_r(const CstT<R> &C, const R *y, R eref, R
 template <class R, class L, bool VISC, class T>
 struct StageSmem {
   using B = Box<T, L::D3>;
-  static constexpr size_t prim = sizeof(R) * L::NV * B::NSTORE;
-  static constexpr size_t visc = VISC ? sizeof(R) * 2 * B::NSTORE : 0;
+  static constexpr size_t prim = (sizeof(R) * L::NV * B::NSTORE + 15) / 16 * 16;
+  static constexpr size_t visc = VISC ? (sizeof(R) * 2 * B::NSTORE + 15) / 16 * 16 : 0;
   static constexpr size_t face = sizeof(R) * 2 * L::NV * B::NF;  // left state/flux, right state
   static constexpr size_t red = 32 * sizeof(double);
   static constexpr size_t base = prim + visc + face + red;
@@ -1052,6 +1103,7 @@ __device__ __forceinline__ void stage_tiles(const StageArgs &a, const int stage,
   R *s_pi = s_th + (VISC ? B::NSTORE : 0);
   R *s_fl = reinterpret_cast<R *>(smem + S::prim + S::visc);  // left states, then fluxes
   R *s_fr = s_fl + NV * B::NF;                                 // right states
+  using V = SV<R, NV>;
   double *s_red = reinterpret_cast<double *>(smem + S::prim + S::visc + S::face);
   R *s_yn = reinterpret_cast<R *>(smem + S::base);  // used when S::PREFETCH
   const Phys &ph = a.ph;
@@ -1122,8 +1174,7 @@ __device__ __forceinline__ void stage_tiles(const StageArgs &a, const int stage,
         R x[NV], pt, Tt;
         cons_to_prim<R, L>(ph, C, D, k, ys[m], x, pt, Tt);
         const int bi = B::idx(lx + 3, ly + B::HY, lz + 3);
-#pragma unroll
-        for (int v = 0; v < NV; ++v) s_prim[v * B::NSTORE + bi] = x[v];
+        V::store(s_prim, bi, B::NSTORE, x);
         if constexpr (VISC) {
           const R Pi = Ar<R>::pow_small(pt * R(1e-5), C.kappa);
           s_th[bi] = pt * Ar<R>::rcp(x[0] * Pi) * C.iR_d;
@@ -1209,8 +1260,7 @@ __device__ __forceinline__ void stage_tiles(const StageArgs &a, const int stage,
           }
         }
         const int bi = B::idx(bx, by, bz);
-#pragma unroll
-        for (int v = 0; v < NV; ++v) s_prim[v * B::NSTORE + bi] = x[v];
+        V::store(s_prim, bi, B::NSTORE, x);
         // the viscous heat flux reads theta and the Exner function only on the two sides of
         // a face, so of the halo only the ring next to the tile (layers 2 and 3) needs them
         if constexpr (VISC) {
@@ -1269,42 +1319,40 @@ __device__ __forceinline__ void stage_tiles(const StageArgs &a, const int stage,
             const int fl = ((lz + fz) * sy + (ly + fy)) * sx + (lx + fx);  // face c+1/2
             const int fr = (lz * sy + ly) * sx + lx;                        // face c-1/2
             const bool has_l = ld < ed, has_r = ld >= 0;
-            if constexpr (sizeof(R) == 4) {
-              // two variables per packed FP32x2 instruction, the odd one alone
-#pragma unroll
-              for (int v = 0; v + 1 < NV; v += 2) {
-                const R *q = s_prim + v * B::NSTORE;
-                const R *r2 = q + B::NSTORE;
-                float2 qm, qp;
-                weno5_pair2(make_float2(q[o[0]], r2[o[0]]), make_float2(q[o[1]], r2[o[1]]),
-                            make_float2(q[o[2]], r2[o[2]]), make_float2(q[o[3]], r2[o[3]]),
-                            make_float2(q[o[4]], r2[o[4]]), weps, qm, qp);
-                if (has_l) {
-                  s_fl[v * B::NF + fl] = qm.x;
-                  s_fl[(v + 1) * B::NF + fl] = qm.y;
-                }
-                if (has_r) {
-                  s_fr[v * B::NF + fr] = qp.x;
-                  s_fr[(v + 1) * B::NF + fr] = qp.y;
-                }
-              }
-              if constexpr (NV % 2 == 1) {
-                const R *q = s_prim + (NV - 1) * B::NSTORE;
-                R qm, qp;
-                weno5_pair<R>(q[o[0]], q[o[1]], q[o[2]], q[o[3]], q[o[4]], weps, qm, qp);
-                if (has_l) s_fl[(NV - 1) * B::NF + fl] = qm;
-                if (has_r) s_fr[(NV - 1) * B::NF + fr] = qp;
-              }
-            } else {
+            R QM[NV], QP[NV];
+            if constexpr (V::G == 1) {
+              // one field at a time (no vector access to gain; fewer values live at once)
 #pragma unroll
               for (int v = 0; v < NV; ++v) {
                 const R *q = s_prim + v * B::NSTORE;
-                R qm, qp;
-                weno5_pair<R>(q[o[0]], q[o[1]], q[o[2]], q[o[3]], q[o[4]], weps, qm, qp);
-                if (has_l) s_fl[v * B::NF + fl] = qm;
-                if (has_r) s_fr[v * B::NF + fr] = qp;
+                weno5_pair<R>(q[o[0]], q[o[1]], q[o[2]], q[o[3]], q[o[4]], weps, QM[v], QP[v]);
               }
+            } else if constexpr (sizeof(R) == 4) {
+              R X[5][NV];
+#pragma unroll
+              for (int k = 0; k < 5; ++k) V::load(s_prim, o[k], B::NSTORE, X[k]);
+              // two variables per packed FP32x2 instruction, the odd one alone
+#pragma unroll
+              for (int v = 0; v + 1 < NV; v += 2) {
+                float2 qm, qp;
+                weno5_pair2(make_float2(X[0][v], X[0][v + 1]), make_float2(X[1][v], X[1][v + 1]),
+                            make_float2(X[2][v], X[2][v + 1]), make_float2(X[3][v], X[3][v + 1]),
+                            make_float2(X[4][v], X[4][v + 1]), weps, qm, qp);
+                QM[v] = qm.x, QM[v + 1] = qm.y, QP[v] = qp.x, QP[v + 1] = qp.y;
+              }
+              if constexpr (NV % 2 == 1)
+                weno5_pair<R>(X[0][NV - 1], X[1][NV - 1], X[2][NV - 1], X[3][NV - 1],
+                              X[4][NV - 1], weps, QM[NV - 1], QP[NV - 1]);
+            } else {
+              R X[5][NV];
+#pragma unroll
+              for (int k = 0; k < 5; ++k) V::load(s_prim, o[k], B::NSTORE, X[k]);
+#pragma unroll
+              for (int v = 0; v < NV; ++v)
+                weno5_pair<R>(X[0][v], X[1][v], X[2][v], X[3][v], X[4][v], weps, QM[v], QP[v]);
             }
+            if (has_l) V::store(s_fl, fl, B::NF, QM);
+            if (has_r) V::store(s_fr, fr, B::NF, QP);
           }
         }
       }
@@ -1318,11 +1366,8 @@ __device__ __forceinline__ void stage_tiles(const StageArgs &a, const int stage,
           const int ix = f % sx, iy = (f / sx) % sy, iz = f / (sx * sy);
           if (f >= nface || ix >= ex + fx || iy >= ey + fy || iz >= ez + fz) continue;
           R QL[NV], QR[NV], F[NV];
-#pragma unroll
-          for (int v = 0; v < NV; ++v) {
-            QL[v] = s_fl[v * B::NF + f];
-            QR[v] = s_fr[v * B::NF + f];
-          }
+          V::load(s_fl, f, B::NF, QL);
+          V::load(s_fr, f, B::NF, QR);
           const R pref = fz ? P::pf(D, z0 + iz) : P::pc(D, z0 + iz);
           lmars<R, L>(C, QL, QR, d, pref, F);
           if constexpr (L::MOIST && MICRO) {
@@ -1335,13 +1380,16 @@ __device__ __forceinline__ void stage_tiles(const StageArgs &a, const int stage,
           if constexpr (VISC) {
             const int bi = B::idx(ix + 3, iy + B::HY, iz + 3);  // right cell of the face
             const int bl = B::idx(ix + 3 - fx, iy + B::HY - fy, iz + 3 - fz);
-            const R rf = R(0.5) * (s_prim[bl] + s_prim[bi]);
+            R XLc[NV], XRc[NV];  // primitives of the two cells of the face
+            V::load(s_prim, bl, B::NSTORE, XLc);
+            V::load(s_prim, bi, B::NSTORE, XRc);
+            const R rf = R(0.5) * (XLc[0] + XRc[0]);
             const R ih = P::ih(D, d), nu = C.nu;
             R work = R(0);
 #pragma unroll
             for (int mm = 0; mm < L::NMOM; ++mm) {
-              const R ul = s_prim[(L::IM0 + mm) * B::NSTORE + bl];
-              const R ur = s_prim[(L::IM0 + mm) * B::NSTORE + bi];
+              const R ul = XLc[L::IM0 + mm];
+              const R ur = XRc[L::IM0 + mm];
               const R grad = (ur - ul) * ih;
               F[L::IM0 + mm] -= rf * nu * grad;
               work += R(0.5) * (ul + ur) * grad;
@@ -1349,8 +1397,7 @@ __device__ __forceinline__ void stage_tiles(const StageArgs &a, const int stage,
             const R heat = R(0.5) * (s_pi[bl] + s_pi[bi]) * (s_th[bi] - s_th[bl]) * ih;
             F[L::IE] -= rf * nu * work + rf * C.c_pd * nu * heat;
           }
-#pragma unroll
-          for (int v = 0; v < NV; ++v) s_fl[v * B::NF + f] = F[v];
+          V::store(s_fl, f, B::NF, F);
         }
       }
       __syncthreads();
@@ -1363,9 +1410,11 @@ __device__ __forceinline__ void stage_tiles(const StageArgs &a, const int stage,
         if (c < B::NCELL && lx < ex && ly < ey && lz < ez) {
           const int f0 = (lz * sy + ly) * sx + lx;
           const int f1 = ((lz + fz) * sy + (ly + fy)) * sx + (lx + fx);
+          R F1[NV], F0[NV];
+          V::load(s_fl, f1, B::NF, F1);
+          V::load(s_fl, f0, B::NF, F0);
 #pragma unroll
-          for (int v = 0; v < NV; ++v)
-            acc[m][v] -= (s_fl[v * B::NF + f1] - s_fl[v * B::NF + f0]) * ih;
+          for (int v = 0; v < NV; ++v) acc[m][v] -= (F1[v] - F0[v]) * ih;
         }
       }
       if (d != 2) __syncthreads();
@@ -1391,8 +1440,8 @@ __device__ __forceinline__ void stage_tiles(const StageArgs &a, const int stage,
         R mb = R(0), mt = R(0);
 #pragma unroll
         for (int s = 0; s < L::IM0; ++s) {
-          mb += s_fl[s * B::NF + f0];
-          mt += s_fl[s * B::NF + f1];
+          mb += s_fl[V::at(s, f0, B::NF)];
+          mt += s_fl[V::at(s, f1, B::NF)];
         }
         acc[m][L::IE] -= grav * R(0.5) * (mb + mt);
         if constexpr (MICRO && L::MOIST) {

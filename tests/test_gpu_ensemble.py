@@ -122,7 +122,10 @@ def test_autotune_keeps_state_and_picks_a_mode():
     res = ctx.autotune(steps=3)
     assert res["ms_per_step"] > 0
     info = ctx.info()
-    assert info["tile_variant"] == res["variant"] and info["persistent"] == res["persistent"]
+    if res["variant"] is None:  # every size class on its own shape
+        assert info["per_class_tiles"] == 1 and info["persistent"] == 0
+    else:
+        assert info["tile_variant"] == res["variant"] and info["persistent"] == res["persistent"]
     after = [ctx.get_state(domain=d) for d in range(len(ws))]
     assert all(np.array_equal(a, b) for a, b in zip(before, after))
     ctx.step(3)
@@ -189,4 +192,55 @@ def test_resident_step_refuses_grids_beyond_one_wave():
     with pytest.raises(SnapError) as e:
         ctx.use_persistent(2)
     assert e.value.code == capi.ENOTSUP
+    ctx.close()
+
+
+def test_per_class_tile_shapes_agree():
+    """Each size class on its own tile shape (one launch per class and stage, the classes in
+    parallel): bitwise the one-shape step for dry domains, to the moist tolerance with the
+    saturation adjustment; with and without graph capture."""
+    from paper_1901_02955_gb300 import Context
+    dry = [W.add_random_motion(W.density_current(nx=n, nz=m, dtype="f32"), seed=W.BASE_SEED + n)
+           for n, m in [(70, 37), (40, 20), (70, 37), (33, 45)]]
+    for ws, exact in ((dry, True), (members() + [members()[0]], False)):
+        ref, _ = run(ws, "f32")
+        for graph in (True, False):
+            ctx = Context(ws, dtype="f32")
+            info = ctx.info()
+            nc, nv = info["n_size_classes"], info["n_tile_variants"]
+            assert nc == len({(w.nx, w.ny, w.nz) for w in ws})
+            for c in range(nc):
+                ctx.set_class_tile_variant(c, (c + 1) % nv)
+            info = ctx.info()
+            assert info["per_class_tiles"] == 1 and info["kernel_launches_per_step"] == 3 * nc
+            assert [k["variant"] for k in info["classes"]] == [(c + 1) % nv for c in range(nc)]
+            assert sum(k["domains"] for k in info["classes"]) == len(ws)
+            ctx.use_graph(graph)
+            for d, w in enumerate(ws):
+                ctx.set_state(w.Y, domain=d)
+            ctx.step(3)
+            out = [ctx.get_state(domain=d) for d in range(len(ws))]
+            ctx.close()
+            assert all(agree(a, b, exact) for a, b in zip(out, ref)), graph
+
+
+def test_autotune_over_size_classes_keeps_state():
+    from paper_1901_02955_gb300 import Context
+    ws = members() + [members()[1]]
+    ctx = Context(ws, dtype="f32")
+    for d, w in enumerate(ws):
+        ctx.set_state(w.Y, domain=d)
+    before = [ctx.get_state(domain=d) for d in range(len(ws))]
+    res = ctx.autotune(steps=2)
+    info = ctx.info()
+    if res["variant"] is None:
+        assert info["per_class_tiles"] == 1
+        assert res["per_class"] == [k["variant"] for k in info["classes"]]
+    else:
+        assert info["per_class_tiles"] == 0 and info["tile_variant"] == res["variant"]
+    after = [ctx.get_state(domain=d) for d in range(len(ws))]
+    assert all(np.array_equal(a, b) for a, b in zip(before, after))
+    ctx.step(3)
+    ref, _ = run(ws, "f32")
+    assert all(agree(ctx.get_state(domain=d), ref[d], exact=False) for d in range(len(ws)))
     ctx.close()

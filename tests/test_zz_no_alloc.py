@@ -58,8 +58,9 @@ def test_noalloc_budget_matches_context_budget(torch, name, dtype):
             ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(stream))
         assert rc == capi.OK
         torch.cuda.synchronize()
-        # nothing allocated through torch's allocator by the call
-        assert torch.cuda.memory_allocated() == torch_before
+        # nothing allocated through torch's allocator by the call (the figure may fall while
+        # the call runs, when torch releases a tensor of earlier work)
+        assert torch.cuda.memory_allocated() <= torch_before
         # device-wide free memory: the first call may load the library's module lazily, and
         # other users of the GPU change this figure too, so one unchanged reading among the later
         # calls is what the check asks for
