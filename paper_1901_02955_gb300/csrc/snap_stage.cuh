@@ -15,6 +15,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "snap_internal.h"
 
 namespace snap {
@@ -159,47 +161,64 @@ struct Box {
 };
 
 // Shared-memory arrays of NV fields per location (primitives, face states, fluxes) keep the
-// fields of one location together in groups of G (16 bytes for 4 floats or 2 doubles, 8 for
-// 2 floats; G = 1 when NV has no such divisor): element (v, i) of an N-location array sits at
-// ((v / G) N + i) G + v % G, so one vector access moves a group and a window point, face state
-// or flux of the four dry fields is one 16-byte access instead of four.
+// fields of one location together in 16-byte groups (4 floats or 2 doubles), then, for the
+// fields left over, an 8-byte pair (floats) and a single field: 11 FP32 fields as 4 + 4 + 2
+// + 1, 7 as 4 + 2 + 1, 4 as one group. Each group of an N-location array is a plane of
+// N x (group width) values at element N x (its first field), so one vector access moves the
+// group of a location: a window point, face state or flux of the four dry fields is one
+// 16-byte access instead of four.
 template <class R, int NV>
 struct SV {
-  static constexpr int G = sizeof(R) == 4 ? (NV % 4 == 0 ? 4 : (NV % 2 == 0 ? 2 : 1))
-                                          : (NV % 2 == 0 ? 2 : 1);
-  static __device__ __forceinline__ int at(int v, int i, int N) { return ((v / G) * N + i) * G + v % G; }
+  static constexpr int W = sizeof(R) == 4 ? 4 : 2;       // fields of a 16-byte group
+  static constexpr int NF = NV / W;                       // full groups
+  static constexpr int T2 = (sizeof(R) == 4 && NV % W >= 2) ? 1 : 0;  // a pair after them
+  static constexpr int T1 = (NV % W) % 2;                 // a single last field
+  static constexpr int P2 = NF * W;                       // first field of the pair
+  static constexpr int P1 = NF * W + 2 * T2;              // the single field
+  static_assert(P2 * sizeof(R) % 16 == 0, "the pair's plane must start on a 16-byte boundary");
+  static __host__ __device__ __forceinline__ int at(int v, int i, int N) {
+    if (v < P2) return ((v / W) * N + i) * W + v % W;
+    if (v < P1) return P2 * N + i * 2 + (v - P2);
+    return P1 * N + i;
+  }
+  template <class Vec>
+  static __device__ __forceinline__ void ld(const R *p, R *out) {
+    const Vec t = *reinterpret_cast<const Vec *>(p);
+    const R *e = reinterpret_cast<const R *>(&t);
+#pragma unroll
+    for (int j = 0; j < int(sizeof(Vec) / sizeof(R)); ++j) out[j] = e[j];
+  }
+  template <class Vec>
+  static __device__ __forceinline__ void st(R *p, const R *in) {
+    Vec t;
+    R *e = reinterpret_cast<R *>(&t);
+#pragma unroll
+    for (int j = 0; j < int(sizeof(Vec) / sizeof(R)); ++j) e[j] = in[j];
+    *reinterpret_cast<Vec *>(p) = t;
+  }
+  using V16 = typename std::conditional<sizeof(R) == 4, float4, double2>::type;
+  // the fields [first, first + width) of group g of location i (g < NF: a 16-byte group;
+  // g == NF: the pair, or the single field)
+  static __device__ __forceinline__ void load_group(const R *base, int g, int i, int N, R *out) {
+    if (g < NF) {
+      ld<V16>(base + (g * N + i) * W, out);
+    } else if (T2 && g == NF) {
+      ld<float2>(base + P2 * N + i * 2, out);
+    } else {
+      out[0] = base[P1 * N + i];
+    }
+  }
   static __device__ __forceinline__ void load(const R *base, int i, int N, R *out) {
 #pragma unroll
-    for (int g = 0; g < NV / G; ++g) {
-      const R *p = base + (g * N + i) * G;
-      if constexpr (G == 4) {
-        const float4 t = *reinterpret_cast<const float4 *>(p);
-        out[4 * g] = t.x, out[4 * g + 1] = t.y, out[4 * g + 2] = t.z, out[4 * g + 3] = t.w;
-      } else if constexpr (G == 2 && sizeof(R) == 4) {
-        const float2 t = *reinterpret_cast<const float2 *>(p);
-        out[2 * g] = t.x, out[2 * g + 1] = t.y;
-      } else if constexpr (G == 2) {
-        const double2 t = *reinterpret_cast<const double2 *>(p);
-        out[2 * g] = t.x, out[2 * g + 1] = t.y;
-      } else {
-        out[g] = *p;
-      }
-    }
+    for (int g = 0; g < NF; ++g) ld<V16>(base + (g * N + i) * W, out + g * W);
+    if constexpr (T2) ld<float2>(base + P2 * N + i * 2, out + P2);
+    if constexpr (T1) out[P1] = base[P1 * N + i];
   }
   static __device__ __forceinline__ void store(R *base, int i, int N, const R *in) {
 #pragma unroll
-    for (int g = 0; g < NV / G; ++g) {
-      R *p = base + (g * N + i) * G;
-      if constexpr (G == 4) {
-        *reinterpret_cast<float4 *>(p) = make_float4(in[4 * g], in[4 * g + 1], in[4 * g + 2], in[4 * g + 3]);
-      } else if constexpr (G == 2 && sizeof(R) == 4) {
-        *reinterpret_cast<float2 *>(p) = make_float2(in[2 * g], in[2 * g + 1]);
-      } else if constexpr (G == 2) {
-        *reinterpret_cast<double2 *>(p) = make_double2(in[2 * g], in[2 * g + 1]);
-      } else {
-        *p = in[g];
-      }
-    }
+    for (int g = 0; g < NF; ++g) st<V16>(base + (g * N + i) * W, in + g * W);
+    if constexpr (T2) st<float2>(base + P2 * N + i * 2, in + P2);
+    if constexpr (T1) base[P1 * N + i] = in[P1];
   }
 };
 
@@ -1036,9 +1055,14 @@ struct StageSmem {
   using B = Box<T, L::D3>;
   static constexpr size_t prim = (sizeof(R) * L::NV * B::NSTORE + 15) / 16 * 16;
   static constexpr size_t visc = VISC ? (sizeof(R) * 2 * B::NSTORE + 15) / 16 * 16 : 0;
-  static constexpr size_t face = sizeof(R) * 2 * L::NV * B::NF;  // left state/flux, right state
+  // left states (then fluxes) and right states, each array starting on a 16-byte boundary:
+  // the grouped layout moves 16-byte vectors
+  static constexpr size_t face_half = (sizeof(R) * L::NV * B::NF + 15) / 16 * 16;
+  static constexpr size_t face = 2 * face_half;
   static constexpr size_t red = 32 * sizeof(double);
   static constexpr size_t base = prim + visc + face + red;
+  static_assert(prim % 16 == 0 && visc % 16 == 0 && face_half % 16 == 0 && red % 16 == 0,
+                "every shared-memory array of the stage starts on a 16-byte boundary");
   // Y^n of the owned cells, prefetched by cp.async, when it costs no resident CTA per SM
   // (228 KB of shared memory per SM, 1 KB reserved per CTA)
   static constexpr size_t yn_bytes = sizeof(R) * L::NV * B::NCELL;
@@ -1102,7 +1126,7 @@ __device__ __forceinline__ void stage_tiles(const StageArgs &a, const int stage,
   R *s_th = reinterpret_cast<R *>(smem + S::prim);
   R *s_pi = s_th + (VISC ? B::NSTORE : 0);
   R *s_fl = reinterpret_cast<R *>(smem + S::prim + S::visc);  // left states, then fluxes
-  R *s_fr = s_fl + NV * B::NF;                                 // right states
+  R *s_fr = s_fl + S::face_half / sizeof(R);                   // right states
   using V = SV<R, NV>;
   double *s_red = reinterpret_cast<double *>(smem + S::prim + S::visc + S::face);
   R *s_yn = reinterpret_cast<R *>(smem + S::base);  // used when S::PREFETCH
@@ -1320,36 +1344,35 @@ __device__ __forceinline__ void stage_tiles(const StageArgs &a, const int stage,
             const int fr = (lz * sy + ly) * sx + lx;                        // face c-1/2
             const bool has_l = ld < ed, has_r = ld >= 0;
             R QM[NV], QP[NV];
-            if constexpr (V::G == 1) {
-              // one field at a time (no vector access to gain; fewer values live at once)
+            // one group of fields at a time (the group's five window points, one vector access
+            // each): FP32 pairs on the packed FP32x2 pipe, an odd field alone
 #pragma unroll
-              for (int v = 0; v < NV; ++v) {
-                const R *q = s_prim + v * B::NSTORE;
-                weno5_pair<R>(q[o[0]], q[o[1]], q[o[2]], q[o[3]], q[o[4]], weps, QM[v], QP[v]);
+            for (int g = 0; g < V::NF + V::T2 + V::T1; ++g) {
+              const int f0 = g < V::NF ? g * V::W : (g == V::NF && V::T2 ? V::P2 : V::P1);
+              const int n = g < V::NF ? V::W : (g == V::NF && V::T2 ? 2 : 1);
+              R X[5][V::W];
+#pragma unroll
+              for (int k = 0; k < 5; ++k) V::load_group(s_prim, g, o[k], B::NSTORE, X[k]);
+              if constexpr (sizeof(R) == 4) {
+#pragma unroll
+                for (int j = 0; j + 1 < V::W; j += 2) {
+                  if (j + 1 < n) {
+                    float2 qm, qp;
+                    weno5_pair2(make_float2(X[0][j], X[0][j + 1]), make_float2(X[1][j], X[1][j + 1]),
+                                make_float2(X[2][j], X[2][j + 1]), make_float2(X[3][j], X[3][j + 1]),
+                                make_float2(X[4][j], X[4][j + 1]), weps, qm, qp);
+                    QM[f0 + j] = qm.x, QM[f0 + j + 1] = qm.y, QP[f0 + j] = qp.x, QP[f0 + j + 1] = qp.y;
+                  }
+                }
+                if (n == 1)
+                  weno5_pair<R>(X[0][0], X[1][0], X[2][0], X[3][0], X[4][0], weps, QM[f0], QP[f0]);
+              } else {
+#pragma unroll
+                for (int j = 0; j < V::W; ++j)
+                  if (j < n)
+                    weno5_pair<R>(X[0][j], X[1][j], X[2][j], X[3][j], X[4][j], weps, QM[f0 + j],
+                                  QP[f0 + j]);
               }
-            } else if constexpr (sizeof(R) == 4) {
-              R X[5][NV];
-#pragma unroll
-              for (int k = 0; k < 5; ++k) V::load(s_prim, o[k], B::NSTORE, X[k]);
-              // two variables per packed FP32x2 instruction, the odd one alone
-#pragma unroll
-              for (int v = 0; v + 1 < NV; v += 2) {
-                float2 qm, qp;
-                weno5_pair2(make_float2(X[0][v], X[0][v + 1]), make_float2(X[1][v], X[1][v + 1]),
-                            make_float2(X[2][v], X[2][v + 1]), make_float2(X[3][v], X[3][v + 1]),
-                            make_float2(X[4][v], X[4][v + 1]), weps, qm, qp);
-                QM[v] = qm.x, QM[v + 1] = qm.y, QP[v] = qp.x, QP[v + 1] = qp.y;
-              }
-              if constexpr (NV % 2 == 1)
-                weno5_pair<R>(X[0][NV - 1], X[1][NV - 1], X[2][NV - 1], X[3][NV - 1],
-                              X[4][NV - 1], weps, QM[NV - 1], QP[NV - 1]);
-            } else {
-              R X[5][NV];
-#pragma unroll
-              for (int k = 0; k < 5; ++k) V::load(s_prim, o[k], B::NSTORE, X[k]);
-#pragma unroll
-              for (int v = 0; v < NV; ++v)
-                weno5_pair<R>(X[0][v], X[1][v], X[2][v], X[3][v], X[4][v], weps, QM[v], QP[v]);
             }
             if (has_l) V::store(s_fl, fl, B::NF, QM);
             if (has_r) V::store(s_fr, fr, B::NF, QP);

@@ -1,7 +1,9 @@
 """Host check of the stage kernel's shared-memory map (no GPU needed): for every tile shape
 the library builds and every ragged extent of a tile, the cells the kernel fills (owned cells
 and the cross-shaped halo) land on distinct in-range locations, and every cell a WENO window
-or a face reads is one that was filled, at the location it was filled. In 3-D the map stores
+or a face reads is one that was filled, at the location it was filled; and every vector
+access of the grouped field layout is aligned to its size, for every instantiated field count
+and tile. In 3-D the map stores
 only the stencil cross (x-lines with both x halos, then the y and the z halos), so an error
 there would silently mix two cells; in the x-z plane it is the plain box."""
 import os
@@ -84,8 +86,53 @@ int all_extents() {
   return bad;
 }
 
+// Every vector access of the grouped field layout (16-byte groups, then an 8-byte pair)
+// lands on a multiple of its size, for every array of the stage's shared memory, every field
+// and every location: the arrays' byte offsets plus SV::at.
+template <class R, int NV, class T, bool D3, bool VISC>
+int aligned() {
+  using L = Lay<0, 0, D3>;  // only NV matters below
+  using B = Box<T, D3>;
+  using V = SV<R, NV>;
+  const size_t prim = (sizeof(R) * NV * B::NSTORE + 15) / 16 * 16;
+  const size_t visc = VISC ? (sizeof(R) * 2 * B::NSTORE + 15) / 16 * 16 : 0;
+  const size_t half = (sizeof(R) * NV * B::NF + 15) / 16 * 16;
+  const size_t bases[3] = {0, prim + visc, prim + visc + half};
+  const int N[3] = {B::NSTORE, B::NF, B::NF};
+  int bad = 0;
+  (void)sizeof(L);
+  for (int a = 0; a < 3; ++a)
+    for (int i = 0; i < N[a]; ++i)
+      for (int v = 0; v < NV; ++v) {
+        const size_t byte = bases[a] + sizeof(R) * V::at(v, i, N[a]);
+        const size_t width = v < V::P2 ? 16 : (v < V::P1 ? 8 : sizeof(R));
+        const int first = v < V::P2 ? v % V::W == 0 : (v < V::P1 ? v == V::P2 : 1);
+        if (first && byte % width) ++bad;
+      }
+  return bad;
+}
+
 int main() {
   int bad = 0;
+  // the layouts and tiles the library instantiates: dry x-z (4 fields), moist x-z (7), dry
+  // 3-D (5), moist 3-D (11), in FP32 and FP64
+  bad += aligned<float, 4, TileT<64, 1, 14>, false, true>();
+  bad += aligned<float, 4, TileT<32, 1, 14>, false, true>();
+  bad += aligned<float, 4, TileT<128, 1, 14>, false, true>();
+  bad += aligned<float, 4, TileT<64, 1, 28>, false, true>();
+  bad += aligned<double, 4, TileT<32, 1, 28>, false, true>();
+  bad += aligned<double, 4, TileT<32, 1, 14>, false, true>();
+  bad += aligned<float, 7, TileT<32, 1, 14>, false, false>();
+  bad += aligned<float, 7, TileT<64, 1, 6>, false, false>();
+  bad += aligned<float, 7, TileT<16, 1, 30>, false, false>();
+  bad += aligned<double, 7, TileT<32, 1, 14>, false, false>();
+  bad += aligned<float, 5, TileT<8, 8, 4>, true, true>();
+  bad += aligned<float, 5, TileT<16, 8, 2>, true, true>();
+  bad += aligned<double, 5, TileT<8, 8, 4>, true, true>();
+  bad += aligned<float, 11, TileT<8, 8, 4>, true, false>();
+  bad += aligned<float, 11, TileT<16, 8, 2>, true, false>();
+  bad += aligned<double, 11, TileT<8, 8, 4>, true, false>();
+  if (bad) printf("misaligned %d\n", bad);
   bad += all_extents<TileT<8, 8, 4>, true>();
   bad += all_extents<TileT<16, 8, 2>, true>();
   bad += all_extents<TileT<32, 1, 14>, false>();
