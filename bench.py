@@ -38,6 +38,9 @@ def parse():
     p.add_argument("--impl", default="cuda", choices=["cuda", "reference"])
     p.add_argument("--cpu-seconds", type=float, default=10.0)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-extra", action="store_true",
+                   help="leave out the Jovian and ensemble sub-lines of the default line (for "
+                        "profiling runs of the headline kernel)")
     p.add_argument("--workload", default=WORKLOAD,
                    choices=[WORKLOAD, "jovian_256x256x128", "jovian_256x256x128_kessler",
                             "jovian_rce_256x256x128",
@@ -727,8 +730,8 @@ def main():
     fp64_tflops = flops_cell * cells * 3 / (ms64 * 1e-3) / 1e12
 
     # ---- the workloads larger than L2, timed in the same run ----------------------------------
-    jov = jovian_line(args, stream, peak, peak_src)
-    ens = ensemble_line(args, stream, peak, peak_src)
+    jov = None if args.no_extra else jovian_line(args, stream, peak, peak_src)
+    ens = None if args.no_extra else ensemble_line(args, stream, peak, peak_src)
 
     # ---- one step of the bench input on the GPU, kept for the parity report -----------------
     gpu_steps = parity_gpu_steps(stream)

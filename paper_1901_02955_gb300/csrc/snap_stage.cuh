@@ -312,7 +312,7 @@ __device__ __forceinline__ void cons_to_prim(const Phys &ph, const CstT<R> &C, c
     Cv *= ph.c_vd;
     Rm *= ph.R_d;
     double U = (double(y[L::IE]) + D.e_ref[k]) - double(K) - A;
-    double T = U / Cv;
+    double T = Ar<double>::div(U, Cv);
     double p = Rm * T;
     p_tot = R(p);
     T_out = R(T);
@@ -480,8 +480,10 @@ __device__ __forceinline__ void cell_Tp(const Phys &ph, const R *y, double eref,
       A += ph.mu[i][j] * double(y[L::cond(i, j)]);
     }
   }
-  double U = (double(y[L::IE]) + eref) - 0.5 * K2 / rho - A;
-  T = U / (Cv * ph.c_vd);
+  // quotients by the Newton-Raphson reciprocal of Ar<double> (within about an ulp of the
+  // IEEE quotient, a third of its FP64 instructions: on this part each costs ~32 FP32 ones)
+  double U = (double(y[L::IE]) + eref) - 0.5 * K2 * Ar<double>::rcp(rho) - A;
+  T = Ar<double>::div(U, Cv * ph.c_vd);
   p = Rm * ph.R_d * T;
   if (Cv_out) *Cv_out = Cv * ph.c_vd;  // heat capacity at constant volume, J/(m^3 K)
   if (Rm_out) *Rm_out = Rm;            // sum of the gas densities / molar-mass ratios
@@ -593,7 +595,7 @@ __device__ int satadj_cell(const Phys &ph, const CstT<R> &C, R *y, double eref, 
           const double dv = double(y[1 + i]) - double(yv);
           const double dc = double(y[L::cond(i, 0)]) - double(yc);
           const double dC = (ph.sig_v[i] * dv + ph.sig_c[i][0] * dc) * ph.c_vd;
-          Td -= (ph.mu[i][0] * dc + Td * dC) / (Cvd + dC);
+          Td -= Ar<double>::div(ph.mu[i][0] * dc + Td * dC, Cvd + dC);
           Cvd += dC;
           Rmd += ph.inv_eps[i] * dv;
           pd = Rmd * ph.R_d * Td;
@@ -829,7 +831,7 @@ __device__ int kessler_cell(const Phys &ph, const CstT<R> &C, R *y, double eref,
         const double dr = double(y[ri]) - double(yn[2]);
         const double dC = (ph.sig_v[i] * dv + ph.sig_c[i][0] * dc + ph.sig_c[i][1] * dr) * ph.c_vd;
         const double dA = ph.mu[i][0] * dc + ph.mu[i][1] * dr;
-        T0 -= (dA + T0 * dC) / (Cv0 + dC);
+        T0 -= Ar<double>::div(dA + T0 * dC, Cv0 + dC);
         Cv0 += dC;
       }
       if (it < 0)
