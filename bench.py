@@ -45,7 +45,7 @@ def parse():
                    choices=[WORKLOAD, "jovian_256x256x128", "jovian_256x256x128_kessler",
                             "jovian_rce_256x256x128",
                             "ensemble_96", "ensemble_96_autotuned", "adjoint_256x256",
-                            "bryan_1000s", "density_current_900s"],
+                            "bryan_1000s", "density_current_900s", "density_current_slabs"],
                    help="the default is the headline workload; the others print an extra "
                         "measurement line of the same form (3-D moist column, the same with "
                         "Kessler microphysics and falling precipitation, moist ensemble) or "
@@ -539,6 +539,66 @@ def adjoint_workload(args, local):
     print(json.dumps(line), flush=True)
 
 
+def slabs_workload(args, local):
+    """The density current split along x into 1, 2 and 4 slabs, all domains of one context
+    with their boundaries linked (the kernels read a neighbour's columns in place; one CFL
+    time step for the group): the cost of the decomposition against the undecomposed grid,
+    FP32, L2 flushed before every timed step, and the states after the timed steps compared
+    bitwise with the undecomposed run."""
+    import torch
+    from paper_1901_02955_gb300 import Context
+    from paper_1901_02955_gb300.slabs import Decomposition, gather, link_slabs, slab_workload
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    w = workload("f32")
+    out, ref = {}, None
+    for nslab in (1, 2, 4):
+        if nslab == 1:
+            ws = [w]
+            ctx = Context(ws, dtype="f32")
+        else:
+            dec = Decomposition(w.nx, nslab, periodic=False)
+            ws = [slab_workload(w, dec, s_) for s_ in range(nslab)]
+            ctx = Context(ws, dtype="f32")
+            ctx.set_tile_variant(0)
+            link_slabs(ctx, dec)
+        ctx.set_stream(stream)
+        for d, ws_ in enumerate(ws):
+            ctx.set_state(ws_.Y.astype(np.float32), domain=d)
+        for _ in range(args.warmup):
+            flush.fill_(1)
+            ctx.step_async(1)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        torch.cuda.synchronize()
+        for s_, e_ in ev:
+            flush.fill_(1)
+            s_.record(stream)
+            ctx.step_async(1)
+            e_.record(stream)
+        torch.cuda.synchronize()
+        rc, flags = ctx.check()
+        ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+        Y = ctx.get_state() if nslab == 1 else \
+            gather(dec, {d: ctx.get_state(domain=d) for d in range(nslab)})
+        if ref is None:
+            ref = Y
+        info = ctx.info()
+        out[f"slabs_{nslab}"] = {"ms_per_step": ms, "cell_updates_per_s": w.ncells * 3 / (ms * 1e-3),
+                                 "tiles": info["tiles_total"], "device_checks": flags,
+                                 "bitwise_equal_to_undecomposed": bool(np.array_equal(Y, ref))}
+        ctx.close()
+    line = {"metric": "slab decomposition of one domain: step time against the undecomposed grid",
+            "unit": "ms", "value": out["slabs_2"]["ms_per_step"], "higher_is_better": False,
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "data": "synthetic",
+            "config": {"workload": WORKLOAD, "dtype": "f32", "l2": "flushed before every step",
+                       "note": "slabs linked in one context; the warm-up and timed steps of "
+                               "every run start from the same state", "results": out}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_info()
@@ -556,6 +616,10 @@ def main():
     if args.workload == "density_current_900s":
         if rank == 0:
             straka_workload(args, local)
+        return
+    if args.workload == "density_current_slabs":
+        if rank == 0:
+            slabs_workload(args, local)
         return
     if args.workload != WORKLOAD:
         if args.workload.startswith("ensemble_96"):

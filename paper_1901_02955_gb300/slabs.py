@@ -125,7 +125,7 @@ class GpuSlab:
 
     def put_halo(self, slot, side, data):
         if data is not self.ghost[side]:
-            self.ghost[side].copy_(data)
+            self.ghost[side].copy_(data)  # device copy, or host to device after a gloo receive
 
     def local_dt(self):
         return self.ctx.compute_dt()
@@ -152,6 +152,8 @@ class SlabRun:
         self.device = device
         if sorted(self.engines) != dec.slabs_of(rank, world):
             raise ValueError("engines must be exactly this rank's slabs")
+        # a backend without device tensors (gloo) moves the columns through host memory
+        self.host_staged = dist is not None and world > 1 and dist.get_backend() == "gloo"
 
     def exchange(self, slot):
         """Ghost columns of every slab boundary for the stage whose input is state slot `slot`
@@ -163,10 +165,14 @@ class SlabRun:
             if mine and theirs:
                 self.engines[n].put_halo(slot, nside, self.engines[s].pack(slot, side))
             elif mine:
-                ops.append(self.dist.P2POp(self.dist.isend, self.engines[s].pack(slot, side),
-                                           self.dec.owner(n, self.world)))
+                data = self.engines[s].pack(slot, side)
+                if self.host_staged and data.is_cuda:
+                    data = data.cpu()
+                ops.append(self.dist.P2POp(self.dist.isend, data, self.dec.owner(n, self.world)))
             elif theirs:
                 buf = self.engines[n].recv_buffer(nside)
+                if self.host_staged and buf.is_cuda:
+                    buf = buf.new_empty(buf.shape, device="cpu")
                 ops.append(self.dist.P2POp(self.dist.irecv, buf, self.dec.owner(s, self.world)))
                 post.append((n, nside, buf))
         if ops:

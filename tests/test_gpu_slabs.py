@@ -130,3 +130,58 @@ def test_halo_entry_points_check_their_arguments(torch):
         ctx.record(2, 1)
     assert e.value.code == capi.ENOTSUP
     ctx.close()
+
+
+def _slab_rank(rank, world, port, name, nslab, nsteps, q):
+    import os
+    import torch
+    import torch.distributed as dist
+    from paper_1901_02955_gb300.slabs import Decomposition, GpuSlab, SlabRun, slab_workload
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        torch.cuda.set_device(0)
+        w, dtype = cases()[name]
+        dec = Decomposition(w.nx, nslab, periodic=w.bc[0] == W.PERIODIC)
+        engines = {s: GpuSlab(slab_workload(w, dec, s), dtype) for s in dec.slabs_of(rank, world)}
+        dt = SlabRun(dec, engines, rank, world, dist).step(nsteps)
+        mine = {s: e.state() for s, e in engines.items()}
+        allst = [None] * world
+        dist.all_gather_object(allst, mine)
+        if rank == 0:
+            merged = {}
+            for d in allst:
+                merged.update(d)
+            q.put((np.concatenate([merged[s] for s in range(nslab)], axis=-1), dt))
+        for e in engines.values():
+            e.close()
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("name", ["walls_dry_xz_f64", "periodic_dry_3d_f64"])
+def test_slabs_in_two_processes_reproduce_the_domain(torch, name):
+    """The multi-process path with the CUDA library: two processes on the GPU, each holding
+    its slabs (of three) in contexts of its own, exchange the ghost columns before every
+    stage through torch.distributed (gloo, staged through host memory; NCCL carries device
+    tensors directly) and take the CFL step as an all-reduced minimum: bitwise the
+    undecomposed run over 10 steps."""
+    import multiprocessing as mp
+    import socket
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_slab_rank, args=(r, 2, port, name, 3, 10, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    Y, dt = q.get(timeout=600)
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    w, dtype = cases()[name]
+    Yw, dtw = whole(w, dtype, 10, 0)
+    assert dt == dtw
+    assert np.array_equal(Y, Yw), float(np.abs(Y - Yw).max())
