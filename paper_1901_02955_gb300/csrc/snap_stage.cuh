@@ -158,6 +158,18 @@ struct Box {
       return NXB + NYH + ((bz < 3 ? bz : bz - T::TZ) * T::TY + oy) * T::TX + (bx - 3);
     }
   }
+  // idx for a location whose z (idx_y) or y (idx_z) lies in the owned range, as along a y or z
+  // reconstruction window: one range test instead of two
+  static __host__ __device__ __forceinline__ int idx_y(int bx, int by, int bz) {
+    const int oy = by - 3, oz = bz - 3;
+    if ((unsigned)oy < (unsigned)T::TY) return (oz * T::TY + oy) * BX + bx;
+    return NXB + (oz * 6 + (by < 3 ? by : by - T::TY)) * T::TX + (bx - 3);
+  }
+  static __host__ __device__ __forceinline__ int idx_z(int bx, int by, int bz) {
+    const int oy = by - 3, oz = bz - 3;
+    if ((unsigned)oz < (unsigned)T::TZ) return (oz * T::TY + oy) * BX + bx;
+    return NXB + NYH + ((bz < 3 ? bz : bz - T::TZ) * T::TY + oy) * T::TX + (bx - 3);
+  }
 };
 
 // Shared-memory arrays of NV fields per location (primitives, face states, fluxes) keep the
@@ -608,15 +620,18 @@ __device__ int satadj_cell(const Phys &ph, const CstT<R> &C, R *y, double eref, 
   }
 }
 
+// The cell a ghost at index g (at most n beyond either edge of an axis of n >= 3 cells)
+// copies: wrapped on a periodic side (one add or subtract, no integer division), mirrored at a
+// wall (flip set).
 __device__ __forceinline__ int map_index(int g, int n, int bc_lo, int bc_hi, bool &flip) {
   flip = false;
   if (g < 0) {
-    if (bc_lo == 1) return ((g % n) + n) % n;
+    if (bc_lo == 1) return g + n;
     flip = true;
     return -1 - g;
   }
   if (g >= n) {
-    if (bc_hi == 1) return g % n;
+    if (bc_hi == 1) return g - n;
     flip = true;
     return 2 * n - 1 - g;
   }
@@ -1334,9 +1349,11 @@ __device__ __forceinline__ void stage_tiles(const StageArgs &a, const int stage,
             // 3-D x-lines; mapped one by one where a 3-D y or z window leaves the x-lines
             int o[5];
             if (L::D3 && !fx) {
+              // the window's fixed coordinate lies in the owned range
 #pragma unroll
               for (int k = 0; k < 5; ++k)
-                o[k] = B::idx(lx + 3, ly + B::HY + fy * (k - 2), lz + 3 + fz * (k - 2));
+                o[k] = fy ? B::idx_y(lx + 3, ly + B::HY + (k - 2), lz + 3)
+                          : B::idx_z(lx + 3, ly + B::HY, lz + 3 + (k - 2));
             } else {
               const int bi = B::idx(lx + 3, ly + B::HY, lz + 3);
 #pragma unroll

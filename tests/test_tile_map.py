@@ -65,7 +65,12 @@ int check(int ex, int ey, int ez) {
         for (int lx = -fx; lx < ex + fx; ++lx) {
           const int ld = fx ? lx : (fy ? ly : lz);
           if (ld > e[d]) continue;
-          for (int k = -2; k <= 2; ++k) read(lx + 3 + fx * k, ly + HY + fy * k, lz + 3 + fz * k);
+          for (int k = -2; k <= 2; ++k) {
+            read(lx + 3 + fx * k, ly + HY + fy * k, lz + 3 + fz * k);
+            // the kernel maps 3-D y and z windows with the one-test forms
+            if (D3 && fy && B::idx_y(lx + 3, ly + HY + k, lz + 3) != B::idx(lx + 3, ly + HY + k, lz + 3)) ++bad;
+            if (D3 && fz && B::idx_z(lx + 3, ly + HY, lz + 3 + k) != B::idx(lx + 3, ly + HY, lz + 3 + k)) ++bad;
+          }
         }
     for (int iz = 0; iz < ez + fz; ++iz)
       for (int iy = 0; iy < ey + fy; ++iy)
