@@ -473,29 +473,66 @@ __device__ __forceinline__ void lmars(const CstT<R> &C, const R *XL, const R *XR
 // phases non-negative, then T and p follow from the conserved energy and the equation of
 // state. Returns the sweep count, or -1 without convergence.
 // ------------------------------------------------------------------------------------------
+// An FP64 quotient a / b for the kernels of type R: FP64 kernels to about an ulp (two
+// Newton-Raphson steps, Ar<double>::div); FP32 kernels, whose states hold 7 digits, to ~1e-12
+// (one step from the approximate FP64 reciprocal)
+template <class R>
+__device__ __forceinline__ double quot64(double a, double b) {
+  if constexpr (sizeof(R) == 8) {
+    return Ar<double>::div(a, b);
+  } else {
+    double r;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(b));
+    r = fma(r, fma(-b, r, 1.0), r);
+    return a * r;
+  }
+}
+
 template <class R, class L>
 __device__ __forceinline__ void cell_Tp(const Phys &ph, const R *y, double eref, double &T,
                                         double &p, double *Cv_out = nullptr,
                                         double *Rm_out = nullptr) {
-  double rho = 0.0, K2 = 0.0, A = 0.0, Cv = y[0], Rm = y[0];
-#pragma unroll
-  for (int s = 0; s < L::IM0; ++s) rho += double(y[s]);
-#pragma unroll
-  for (int m = 0; m < L::NMOM; ++m) K2 += double(y[L::IM0 + m]) * double(y[L::IM0 + m]);
+  double Cv = y[0], Rm = y[0];
 #pragma unroll
   for (int i = 0; i < L::NVAP; ++i) {
     Cv += ph.sig_v[i] * double(y[1 + i]);
     Rm += ph.inv_eps[i] * double(y[1 + i]);
 #pragma unroll
-    for (int j = 0; j < L::NCOND; ++j) {
-      Cv += ph.sig_c[i][j] * double(y[L::cond(i, j)]);
-      A += ph.mu[i][j] * double(y[L::cond(i, j)]);
-    }
+    for (int j = 0; j < L::NCOND; ++j) Cv += ph.sig_c[i][j] * double(y[L::cond(i, j)]);
   }
-  // quotients by the Newton-Raphson reciprocal of Ar<double> (within about an ulp of the
-  // IEEE quotient, a third of its FP64 instructions: on this part each costs ~32 FP32 ones)
-  double U = (double(y[L::IE]) + eref) - 0.5 * K2 * Ar<double>::rcp(rho) - A;
-  T = Ar<double>::div(U, Cv * ph.c_vd);
+  double U;
+  if constexpr (sizeof(R) == 4) {
+    // FP32 states: the kinetic and latent energies (about 1e-4 of U) and the density they
+    // need are summed in FP32 -- their rounding is ~1e-10 of U, far below what the state holds
+    // -- and the inversion itself (U, the heat capacity, T, p) stays in FP64 with a quotient
+    // good to ~1e-12 (one Newton-Raphson step from the approximate FP64 reciprocal); an FP64
+    // instruction costs ~32 FP32 ones on this part
+    float rho = y[0], K2 = 0.0f, A = 0.0f;
+#pragma unroll
+    for (int s = 1; s < L::IM0; ++s) rho += y[s];
+#pragma unroll
+    for (int m = 0; m < L::NMOM; ++m) K2 = fmaf(y[L::IM0 + m], y[L::IM0 + m], K2);
+#pragma unroll
+    for (int i = 0; i < L::NVAP; ++i)
+#pragma unroll
+      for (int j = 0; j < L::NCOND; ++j) A = fmaf(float(ph.mu[i][j]), y[L::cond(i, j)], A);
+    U = (double(y[L::IE]) + eref) - double(0.5f * K2 * Ar<float>::rcp(rho) + A);
+    T = quot64<R>(U, Cv * ph.c_vd);
+  } else {
+    double rho = 0.0, K2 = 0.0, A = 0.0;
+#pragma unroll
+    for (int s = 0; s < L::IM0; ++s) rho += double(y[s]);
+#pragma unroll
+    for (int m = 0; m < L::NMOM; ++m) K2 += double(y[L::IM0 + m]) * double(y[L::IM0 + m]);
+#pragma unroll
+    for (int i = 0; i < L::NVAP; ++i)
+#pragma unroll
+      for (int j = 0; j < L::NCOND; ++j) A += ph.mu[i][j] * double(y[L::cond(i, j)]);
+    // quotients by the Newton-Raphson reciprocal of Ar<double> (within about an ulp of the
+    // IEEE quotient, a third of its FP64 instructions)
+    U = (double(y[L::IE]) + eref) - 0.5 * K2 * Ar<double>::rcp(rho) - A;
+    T = Ar<double>::div(U, Cv * ph.c_vd);
+  }
   p = Rm * ph.R_d * T;
   if (Cv_out) *Cv_out = Cv * ph.c_vd;  // heat capacity at constant volume, J/(m^3 K)
   if (Rm_out) *Rm_out = Rm;            // sum of the gas densities / molar-mass ratios
@@ -607,7 +644,7 @@ __device__ int satadj_cell(const Phys &ph, const CstT<R> &C, R *y, double eref, 
           const double dv = double(y[1 + i]) - double(yv);
           const double dc = double(y[L::cond(i, 0)]) - double(yc);
           const double dC = (ph.sig_v[i] * dv + ph.sig_c[i][0] * dc) * ph.c_vd;
-          Td -= Ar<double>::div(ph.mu[i][0] * dc + Td * dC, Cvd + dC);
+          Td -= quot64<R>(ph.mu[i][0] * dc + Td * dC, Cvd + dC);
           Cvd += dC;
           Rmd += ph.inv_eps[i] * dv;
           pd = Rmd * ph.R_d * Td;
@@ -846,7 +883,7 @@ __device__ int kessler_cell(const Phys &ph, const CstT<R> &C, R *y, double eref,
         const double dr = double(y[ri]) - double(yn[2]);
         const double dC = (ph.sig_v[i] * dv + ph.sig_c[i][0] * dc + ph.sig_c[i][1] * dr) * ph.c_vd;
         const double dA = ph.mu[i][0] * dc + ph.mu[i][1] * dr;
-        T0 -= Ar<double>::div(dA + T0 * dC, Cv0 + dC);
+        T0 -= quot64<R>(dA + T0 * dC, Cv0 + dC);
         Cv0 += dC;
       }
       if (it < 0)
