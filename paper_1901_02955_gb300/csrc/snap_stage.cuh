@@ -641,12 +641,23 @@ __device__ int satadj_cell(const Phys &ph, const CstT<R> &C, R *y, double eref, 
           y[1 + i] -= drho;
           y[L::cond(i, 0)] += drho;
           // the changes as stored (after rounding to the state's type)
-          const double dv = double(y[1 + i]) - double(yv);
-          const double dc = double(y[L::cond(i, 0)]) - double(yc);
-          const double dC = (ph.sig_v[i] * dv + ph.sig_c[i][0] * dc) * ph.c_vd;
-          Td -= quot64<R>(ph.mu[i][0] * dc + Td * dC, Cvd + dC);
-          Cvd += dC;
-          Rmd += ph.inv_eps[i] * dv;
+          if constexpr (sizeof(R) == 4) {
+            // FP32 states: the increments in FP32 (good to ~1e-7 of themselves, ~1e-10 of T),
+            // accumulated into the FP64 T, heat capacity and gas sum
+            const R dv = y[1 + i] - yv, dc = y[L::cond(i, 0)] - yc;
+            const R dC = (C.sig_v[i] * dv + C.sig_c[i][0] * dc) * C.c_vd;
+            const R dT = (C.mu[i][0] * dc + R(Td) * dC) * Ar<R>::rcp(R(Cvd) + dC);
+            Td -= double(dT);
+            Cvd += double(dC);
+            Rmd += double(C.inv_eps[i] * dv);
+          } else {
+            const double dv = double(y[1 + i]) - double(yv);
+            const double dc = double(y[L::cond(i, 0)]) - double(yc);
+            const double dC = (ph.sig_v[i] * dv + ph.sig_c[i][0] * dc) * ph.c_vd;
+            Td -= quot64<R>(ph.mu[i][0] * dc + Td * dC, Cvd + dC);
+            Cvd += dC;
+            Rmd += ph.inv_eps[i] * dv;
+          }
           pd = Rmd * ph.R_d * Td;
         }
         if (fabs(dq) > tol * (qv + qc)) conv = false;
