@@ -39,7 +39,9 @@ struct Ar<float> {
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
   }
-  static __device__ __forceinline__ float div(float a, float b) { return __fdividef(a, b); }
+  // a / b as a times the approximate reciprocal (~2 ulp; b a normal number, as every divisor
+  // of the scheme is: densities, heat capacities, mixing factors, sound-speed sums)
+  static __device__ __forceinline__ float div(float a, float b) { return a * rcp(b); }
   static __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
   static __device__ __forceinline__ float exp_(float x) { return expf(x); }
   static __device__ __forceinline__ float log_(float x) { return logf(x); }
