@@ -799,6 +799,7 @@ def main():
 
     # ---- one step of the bench input on the GPU, kept for the parity report -----------------
     gpu_steps = parity_gpu_steps(stream)
+    jov_windows = None if args.no_extra else jovian_window_steps(stream)
 
     if rank == 0:
         cpu = None
@@ -806,6 +807,8 @@ def main():
         if not args.no_cpu_baseline:
             cpu = cpu_baseline(args.cpu_seconds)
             parity = parity_report(gpu_steps)
+            if jov_windows is not None:
+                parity["jovian_256x256x128_stage0_windows"] = jovian_window_report(jov_windows)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms32,
@@ -968,6 +971,101 @@ def parity_report(gpu_steps):
                    "GPU (C ABI) against the FP64 oracle on the same input (FP32: the "
                    "FP32-rounded input on both sides); 'moving' adds a seeded random velocity "
                    "field to the same state")
+    return rep
+
+
+def jovian_window_steps(stream, nsamp=24):
+    """Stage 0 of the full Jovian column (256 x 256 x 128) on the GPU in FP32 and FP64, at the
+    initial CFL time step; kept: the stage result at seeded sample cells (interior levels) and
+    the input on the 7 x 7 x 7 window around each (a stage result depends only on cells within
+    3 along each axis; x and y periodic), for the parity report."""
+    import torch
+    import workloads as W
+    from paper_1901_02955_gb300 import Context
+    w = W.jovian(dtype="f64")
+    rs = np.random.default_rng(3)
+    cells = [(int(rs.integers(w.nx)), int(rs.integers(w.ny)), int(rs.integers(3, w.nz - 3)))
+             for _ in range(nsamp)]
+    ii = torch.tensor([c[0] for c in cells], device="cuda")
+    jj = torch.tensor([c[1] for c in cells], device="cuda")
+    kk = torch.tensor([c[2] for c in cells], device="cuda")
+    e_ref = 0.5 * (w.p_bar_face[:-1] + w.p_bar_face[1:]) / (w.gamma_d - 1.0)
+    out = {}
+    for dt_name in ("f32", "f64"):
+        Y0 = w.Y.astype(np.float32) if dt_name == "f32" else w.Y
+        ctx = Context(w, dtype=dt_name)
+        ctx.set_stream(stream)
+        ctx.set_state(Y0)
+        dt = ctx.compute_dt()
+        ctx.stage(0, dt_fixed=dt)
+        stream.synchronize()
+        got = ctx.buffer_view(slot=1)[:, kk, jj, ii].double().cpu().numpy().T.copy()
+        ctx.close()
+        Yd = Y0.astype(np.float64)
+        wins = []
+        for n, (i, j, k) in enumerate(cells):
+            got[n, -1] += e_ref[k]  # stored energy -> total energy
+            xi = [(i + s) % w.nx for s in range(-3, 4)]
+            yj = [(j + s) % w.ny for s in range(-3, 4)]
+            wins.append(np.ascontiguousarray(Yd[:, k - 3:k + 4][:, :, yj][:, :, :, xi]))
+        out[dt_name] = (dt, got, wins)
+    return w, cells, out
+
+
+def jovian_window_report(steps):
+    """Per-field errors of the GPU's stage 0 at the sampled cells of the Jovian column against
+    the FP64 oracle's stage 0 on each cell's 7 x 7 x 7 window of the same input: the
+    relative L2 over the samples against the oracle's values (vs_state; a condensate against
+    its vapour's, a momentum component against the momentum vector floored at the density x
+    1 m/s, as in the parity tests) and against the oracle's increment over the stage
+    (vs_increment; None where the oracle's increment is exactly zero, as for the dry air and
+    the energy of a column at rest in hydrostatic balance), the increment over the state, and
+    the largest error over the largest magnitude of the same reference (max_vs_state)."""
+    import dataclasses
+    import oracle
+    oracle.build()
+    w, cells, out = steps
+    names = w.field_names()
+    im0 = 1 + w.nvapor * (1 + w.ncond)
+    rep = {}
+    for dt_name, (dt, got, wins) in out.items():
+        want = np.empty_like(got)
+        y0 = np.empty_like(got)
+        for n, (i, j, k) in enumerate(cells):
+            ww = dataclasses.replace(w, nx=7, ny=7, nz=7, Y=wins[n],
+                                     rho_bar=w.rho_bar[k - 3:k + 4],
+                                     p_bar_face=w.p_bar_face[k - 3:k + 5])
+            o, _ = oracle.Oracle(ww).stage(0, ww.Y, ww.Y, dt)
+            want[n] = o[:, 3, 3, 3]
+            y0[n] = wins[n][:, 3, 3, 3]
+        err = got - want
+        rho = want[:, :im0].sum(axis=1)
+        nmom = len(names) - 1 - im0
+        d = {}
+        for f, nm in enumerate(names):
+            if im0 <= f < len(names) - 1:  # the momentum vector, floored at rho x 1 m/s
+                sel = want[:, im0:im0 + nmom]
+                ref = max(float(np.linalg.norm(sel)), float(np.linalg.norm(rho)))
+                top = max(float(np.abs(sel).max()), float(rho.max()))
+            elif 1 + w.nvapor <= f < im0:  # a condensate against its vapour too
+                sel = want[:, [f, 1 + (f - 1 - w.nvapor) // w.ncond]]
+                ref = max(float(np.linalg.norm(c)) for c in sel.T)
+                top = float(np.abs(sel).max())
+            else:
+                ref = float(np.linalg.norm(want[:, f]))
+                top = float(np.abs(want[:, f]).max())
+            inc = float(np.linalg.norm(want[:, f] - y0[:, f]))
+            e2 = float(np.linalg.norm(err[:, f]))
+            d[nm] = {"vs_state": e2 / max(ref, 1e-300),
+                     "vs_increment": e2 / inc if inc > 0.0 else None,
+                     "increment_over_state": inc / max(ref, 1e-300),
+                     "max_vs_state": float(np.abs(err[:, f]).max()) / max(top, 1e-300)}
+        rep[dt_name] = d
+    rep["note"] = (f"stage 0 of jovian_256x256x128 at {len(cells)} seeded cells, GPU (C ABI) "
+                   "against the FP64 oracle on the 7 x 7 x 7 window of the same input around "
+                   "each (FP32: the FP32-rounded input on both sides); the column starts at "
+                   "rest in hydrostatic balance, so in one stage only the vertical momentum "
+                   "(buoyancy) and the species the adjustment moves change by much")
     return rep
 
 

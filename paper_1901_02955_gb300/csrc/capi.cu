@@ -150,7 +150,10 @@ struct snap_ctx {
   int rec_steps = 0, ckpt_every = 0;
   std::vector<double> rec_dt;
   void *ckpt = nullptr;       // checkpoints every ckpt_every steps, then the final state
-  void *segbuf = nullptr;     // states of one segment
+  void *segbuf = nullptr;     // states of one segment, or of two (see snap_step_adjoint)
+  int nsegbuf = 1;
+  cudaStream_t rec_stream = nullptr;  // recomputation of the next segment
+  cudaEvent_t ev_rec[2] = {nullptr, nullptr}, ev_free[2] = {nullptr, nullptr};
   double *dt_hist = nullptr;  // device copy of the recorded time steps
   void *lam = nullptr;        // four adjoint vectors
   void *gface = nullptr;      // per-direction face contributions
@@ -222,6 +225,11 @@ static void release(snap_ctx *ctx) {
   if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
   cudaFree(ctx->ckpt);
   cudaFree(ctx->segbuf);
+  if (ctx->rec_stream) cudaStreamDestroy(ctx->rec_stream);
+  for (int b = 0; b < 2; ++b) {
+    if (ctx->ev_rec[b]) cudaEventDestroy(ctx->ev_rec[b]);
+    if (ctx->ev_free[b]) cudaEventDestroy(ctx->ev_free[b]);
+  }
   cudaFree(ctx->dt_hist);
   cudaFree(ctx->lam);
   cudaFree(ctx->gface);
@@ -1166,14 +1174,15 @@ static int satadj_adjoint(snap_ctx *ctx, const StageArgs &sa, const void *Yout, 
 // One forward stage; dt > 0 is passed in the launch arguments (the recorded time step). With
 // ys/yn/yo set, the stage reads and writes those states instead of the domain's buffers.
 static int plain_stage(snap_ctx *ctx, const StageArgs &base, int stage, double dt,
-                       const void *ys = nullptr, const void *yn = nullptr, void *yo = nullptr) {
+                       const void *ys = nullptr, const void *yn = nullptr, void *yo = nullptr,
+                       cudaStream_t st = nullptr) {
   StageArgs a = base;
   a.stage = stage;
   a.dt_override = dt;
   a.buf_s = ys;
   a.buf_n = yn;
   a.buf_o = yo;
-  CK(ctx->ks.var[ctx->tv].stage(a, ctx->grid, ctx->stream));
+  CK(ctx->ks.var[ctx->tv].stage(a, ctx->grid, st ? st : ctx->stream));
   return SNAP_OK;
 }
 
@@ -1193,8 +1202,17 @@ extern "C" int snap_record(snap_ctx *ctx, int nsteps, int ckpt_every, double dt_
   cudaFree(ctx->segbuf);
   ctx->ckpt = ctx->segbuf = nullptr;
   CK(cudaMalloc(&ctx->ckpt, sb * nck));
-  // per step: the inputs of its three stages (Y^n and the results of stages 0 and 1)
-  CK(cudaMalloc(&ctx->segbuf, sb * 3 * nseg_states));
+  // per step: the inputs of its three stages (Y^n and the results of stages 0 and 1); with
+  // more than one segment, room for two segments, so that the adjoint recomputes the next
+  // segment while it transposes the current one (one segment's room if two do not fit)
+  ctx->nsegbuf = 1;
+  if (!store_all && nsteps > ckpt_every) {
+    if (cudaMalloc(&ctx->segbuf, sb * 3 * nseg_states * 2) == cudaSuccess)
+      ctx->nsegbuf = 2;
+    else
+      cudaGetLastError();
+  }
+  if (!ctx->segbuf) CK(cudaMalloc(&ctx->segbuf, sb * 3 * nseg_states));
   cudaFree(ctx->dt_hist);
   ctx->dt_hist = nullptr;
   CK(cudaMalloc(&ctx->dt_hist, sizeof(double) * nsteps));
@@ -1338,22 +1356,65 @@ extern "C" int snap_step_adjoint(snap_ctx *ctx, int nsteps, const void *lambda_f
   const int nseg = (nsteps + K - 1) / K;
   const StageArgs base = args_of(ctx, 0);
   const bool sa = ctx->adj.satadj && ctx->ph.satadj;
+  // With two segment buffers the forward recomputation of segment seg - 1 runs on a second
+  // stream while segment seg is transposed: the stage kernel and the adjoint kernels share
+  // no buffer but the checkpoints (read-only); events order each buffer's reuse.
+  const bool overlap = !store_all && ctx->nsegbuf == 2 && nseg > 1;
+  if (overlap && !ctx->rec_stream) {
+    CK(cudaStreamCreateWithFlags(&ctx->rec_stream, cudaStreamNonBlocking));
+    for (int b = 0; b < 2; ++b) {
+      CK(cudaEventCreateWithFlags(&ctx->ev_rec[b], cudaEventDisableTiming));
+      CK(cudaEventCreateWithFlags(&ctx->ev_free[b], cudaEventDisableTiming));
+    }
+  }
+  const size_t segb = sb * 3 * K;
+  auto segment_buffer = [&](int seg) {
+    return (char *)ctx->segbuf + (overlap ? segb * (seg & 1) : 0);
+  };
+  // recompute segment seg forward from its checkpoint, keeping Y^n and both intermediate
+  // stages of each step
+  auto recompute = [&](int seg, cudaStream_t st) -> int {
+    const int n0 = seg * K, n1 = (n0 + K < nsteps) ? n0 + K : nsteps;
+    char *buf = segment_buffer(seg);
+    CK(cudaMemcpyAsync(buf, (char *)ctx->ckpt + sb * seg, sb, cudaMemcpyDeviceToDevice, st));
+    for (int s = n0; s < n1; ++s) {
+      char *slot = buf + sb * 3 * (s - n0);
+      const double dt = ctx->rec_dt[s];
+      int r;
+      if ((r = plain_stage(ctx, base, 0, dt, slot, slot, slot + sb, st))) return r;
+      if ((r = plain_stage(ctx, base, 1, dt, slot + sb, slot, slot + 2 * sb, st))) return r;
+      if (s < n1 - 1 && (r = plain_stage(ctx, base, 2, dt, slot + 2 * sb, slot, slot + 3 * sb, st)))
+        return r;
+    }
+    return SNAP_OK;
+  };
   int rc = SNAP_OK;
+  if (overlap) {
+    // the recomputation stream starts after the work queued so far (the adjoint's input)
+    CK(cudaEventRecord(ctx->ev_free[1], ctx->stream));
+    CK(cudaStreamWaitEvent(ctx->rec_stream, ctx->ev_free[1], 0));
+    rc = recompute(nseg - 1, ctx->rec_stream);
+    if (!rc) CK(cudaEventRecord(ctx->ev_rec[(nseg - 1) & 1], ctx->rec_stream));
+  }
   for (int seg = nseg - 1; seg >= 0 && rc == SNAP_OK; --seg) {
     const int n0 = seg * K, n1 = (n0 + K < nsteps) ? n0 + K : nsteps;
-    // recompute the segment forward, keeping Y^n and both intermediate stages of each step
-    for (int s = n0; s < n1 && rc == SNAP_OK && !store_all; ++s) {
-      char *slot = (char *)ctx->segbuf + sb * 3 * (s - n0);
-      if (s == n0)
-        CK(cudaMemcpyAsync(slot, (char *)ctx->ckpt + sb * seg, sb, cudaMemcpyDeviceToDevice, ctx->stream));
-      const double dt = ctx->rec_dt[s];
-      if ((rc = plain_stage(ctx, base, 0, dt, slot, slot, slot + sb))) break;
-      if ((rc = plain_stage(ctx, base, 1, dt, slot + sb, slot, slot + 2 * sb))) break;
-      if (s < n1 - 1) rc = plain_stage(ctx, base, 2, dt, slot + 2 * sb, slot, slot + 3 * sb);
+    const int b = seg & 1;
+    if (overlap) {
+      if (seg > 0) {
+        // segment seg - 1 goes to the other buffer once the transpose of segment seg + 1
+        // (its last reader) has finished with it
+        if (seg + 1 < nseg) CK(cudaStreamWaitEvent(ctx->rec_stream, ctx->ev_free[b ^ 1], 0));
+        if ((rc = recompute(seg - 1, ctx->rec_stream))) break;
+        CK(cudaEventRecord(ctx->ev_rec[b ^ 1], ctx->rec_stream));
+      }
+      CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_rec[b], 0));
+    } else if (!store_all) {
+      if ((rc = recompute(seg, ctx->stream))) break;
     }
+    char *buf = store_all ? (char *)ctx->segbuf : segment_buffer(seg);
     for (int s = n1 - 1; s >= n0 && rc == SNAP_OK; --s) {
       const double dt = ctx->rec_dt[s];
-      const char *slot = (const char *)ctx->segbuf + sb * 3 * (s - n0);
+      const char *slot = (const char *)buf + sb * 3 * (s - n0);
       // Sec. 4.3 in reverse: Y3 = Y/3 + 2/3 (Y2 + dt L(Y2)), Y2 = 3/4 Y + 1/4 (Y1 + dt L(Y1)),
       // Y1 = Y + dt L(Y); each stage ends with the saturation adjustment, whose transpose is
       // taken at the stage's output first. The output of stage 2 is the next step's state:
@@ -1367,7 +1428,11 @@ extern "C" int snap_step_adjoint(snap_ctx *ctx, int nsteps, const void *lambda_f
       if (sa && (rc = satadj_adjoint(ctx, base, slot + sb, LC))) break;
       if ((rc = adjoint_stage(ctx, base, slot, LC, LA, LN, 0.0, 1.0, dt, 0))) break;
     }
+    if (overlap && rc == SNAP_OK) CK(cudaEventRecord(ctx->ev_free[b], ctx->stream));
   }
+  // the recomputation stream's work is all waited for by the adjoint stream (an error
+  // return may leave some queued: wait for it before the buffers are reused)
+  if (overlap && rc != SNAP_OK) cudaStreamSynchronize(ctx->rec_stream);
   if (rc == SNAP_OK) {
     void *dst = lambda_init;
     cudaPointerAttributes po;

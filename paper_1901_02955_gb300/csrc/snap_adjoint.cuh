@@ -204,12 +204,11 @@ __device__ __forceinline__ void weno5_pair_grad(const R q[5], R eps, R &QL, R &Q
   const R e0 = eps + (tA * tA + (k3 * sA) * sA);
   const R e1 = eps + (tB * tB + (k3 * sB) * sB);
   const R e2 = eps + (tC * tC + (k3 * sC) * sC);
-  // d beta / d q over each sub-stencil's own three cells
+  // d beta / d q over each sub-stencil's own cells, but for the centre q2 (see below)
   const R dA0 = R(2) * tA + R(6.0 / 13.0) * sA, dA1 = R(-4) * tA - R(24.0 / 13.0) * sA;
-  const R dA2 = R(2) * tA + R(18.0 / 13.0) * sA;
-  const R dB1 = R(2) * tB + R(6.0 / 13.0) * sB, dB2 = R(-4) * tB;
+  const R dB1 = R(2) * tB + R(6.0 / 13.0) * sB;
   const R dB3 = R(2) * tB - R(6.0 / 13.0) * sB;
-  const R dC2 = R(2) * tC + R(18.0 / 13.0) * sC, dC3 = R(-4) * tC - R(24.0 / 13.0) * sC;
+  const R dC3 = R(-4) * tC - R(24.0 / 13.0) * sC;
   const R dC4 = R(2) * tC + R(6.0 / 13.0) * sC;
   const R m0 = e1 * e2, m1 = e0 * e2, m2 = e0 * e1, P = e0 * m0;
   const R s0 = m0 * m0, s1 = m1 * m1, s2 = m2 * m2;
@@ -219,7 +218,15 @@ __device__ __forceinline__ void weno5_pair_grad(const R q[5], R eps, R &QL, R &Q
   const R AL = nL0 + n1 + nL2, AR = nR0 + n1 + nR2;
   R iAL, iAR, iP;
   const R Z = Ar<R>::rcp(AL * AR * P);  // NaN outside the normal range: the test below fails
-  if (Z > R(0) && Z < R(INFINITY)) {
+  bool finite_pos;
+  if constexpr (sizeof(R) == 8) {
+    // 0 < Z < infinity (and not a NaN) from the high word, off the FP64 pipe: sign clear,
+    // exponent below all ones, not zero (a Z below 2^-1022 takes the division path)
+    finite_pos = (unsigned)__double2hiint(double(Z)) - 1u < 0x7fefffffu;
+  } else {
+    finite_pos = Z > R(0) && Z < R(INFINITY);
+  }
+  if (finite_pos) {
     iAL = AR * P * Z;
     iAR = AL * P * Z;
     iP = AL * AR * Z;
@@ -230,34 +237,36 @@ __device__ __forceinline__ void weno5_pair_grad(const R q[5], R eps, R &QL, R &Q
   }
   const R wL0 = nL0 * iAL, wL1 = nL1 * iAL, wL2 = nL2 * iAL;
   const R wR0 = nR0 * iAR, wR1 = nR1 * iAR, wR2 = nR2 * iAR;
-  // candidates: the left state's on A, B, C and the right state's on the same sub-stencils
-  const R vL0 = q[0] * R(1.0 / 3.0) - R(7.0 / 6.0) * q[1] + R(11.0 / 6.0) * q[2];
-  const R vL1 = -q[1] * R(1.0 / 6.0) + R(5.0 / 6.0) * q[2] + q[3] * R(1.0 / 3.0);
-  const R vL2 = q[2] * R(1.0 / 3.0) + R(5.0 / 6.0) * q[3] - q[4] * R(1.0 / 6.0);
-  const R vR0 = q[2] * R(1.0 / 3.0) + R(5.0 / 6.0) * q[1] - q[0] * R(1.0 / 6.0);
-  const R vR1 = -q[3] * R(1.0 / 6.0) + R(5.0 / 6.0) * q[2] + q[1] * R(1.0 / 3.0);
-  const R vR2 = q[4] * R(1.0 / 3.0) - R(7.0 / 6.0) * q[3] + R(11.0 / 6.0) * q[2];
-  QL = wL0 * vL0 + wL1 * vL1 + wL2 * vL2;
-  QR = wR0 * vR0 + wR1 * vR1 + wR2 * vR2;
+  // candidates as offsets from the centre value q2, from the same second differences t and
+  // first-difference combinations s as the indicators: the left state's on A, B, C are
+  // q2 + t/12 + s/4, q2 + t/12 - s/4, q2 + t/12 - s/4; the right state's q2 + t/12 - s/4,
+  // q2 + t/12 + s/4, q2 + t/12 + s/4
+  const R TA = tA * R(1.0 / 12.0), TB = tB * R(1.0 / 12.0), TC = tC * R(1.0 / 12.0);
+  const R SA = sA * R(0.25), SB = sB * R(0.25), SC = sC * R(0.25);
+  const R dL0 = TA + SA, dL1 = TB - SB, dL2 = TC - SC;
+  const R dR0 = TA - SA, dR1 = TB + SB, dR2 = TC + SC;
+  const R DL = wL0 * dL0 + wL1 * dL1 + wL2 * dL2, DR = wR0 * dR0 + wR1 * dR1 + wR2 * dR2;
+  QL = q[2] + DL;
+  QR = q[2] + DR;
   // indicator terms: (v_k - Q) dw_k/dbeta_k = -2 (v_k - Q) w_k / e_k
   const R m2iP = R(-2) * iP;
-  const R cL0 = (vL0 - QL) * wL0 * m0 * m2iP, cL1 = (vL1 - QL) * wL1 * m1 * m2iP;
-  const R cL2 = (vL2 - QL) * wL2 * m2 * m2iP;
-  const R cR0 = (vR0 - QR) * wR0 * m0 * m2iP, cR1 = (vR1 - QR) * wR1 * m1 * m2iP;
-  const R cR2 = (vR2 - QR) * wR2 * m2 * m2iP;
+  const R cL0 = (dL0 - DL) * wL0 * m0 * m2iP, cL1 = (dL1 - DL) * wL1 * m1 * m2iP;
+  const R cL2 = (dL2 - DL) * wL2 * m2 * m2iP;
+  const R cR0 = (dR0 - DR) * wR0 * m0 * m2iP, cR1 = (dR1 - DR) * wR1 * m1 * m2iP;
+  const R cR2 = (dR2 - DR) * wR2 * m2 * m2iP;
   gL[0] = wL0 * R(1.0 / 3.0) + cL0 * dA0;
   gL[1] = wL0 * R(-7.0 / 6.0) + wL1 * R(-1.0 / 6.0) + cL0 * dA1 + cL1 * dB1;
-  gL[2] = wL0 * R(11.0 / 6.0) + wL1 * R(5.0 / 6.0) + wL2 * R(1.0 / 3.0) + cL0 * dA2 +
-          cL1 * dB2 + cL2 * dC2;
   gL[3] = wL1 * R(1.0 / 3.0) + wL2 * R(5.0 / 6.0) + cL1 * dB3 + cL2 * dC3;
   gL[4] = wL2 * R(-1.0 / 6.0) + cL2 * dC4;
   // dQR/dq[t], stored at gR[4 - t]
   gR[4] = wR0 * R(-1.0 / 6.0) + cR0 * dA0;
   gR[3] = wR0 * R(5.0 / 6.0) + wR1 * R(1.0 / 3.0) + cR0 * dA1 + cR1 * dB1;
-  gR[2] = wR0 * R(1.0 / 3.0) + wR1 * R(5.0 / 6.0) + wR2 * R(11.0 / 6.0) + cR0 * dA2 +
-          cR1 * dB2 + cR2 * dC2;
   gR[1] = wR1 * R(-1.0 / 6.0) + wR2 * R(-7.0 / 6.0) + cR1 * dB3 + cR2 * dC3;
   gR[0] = wR2 * R(1.0 / 3.0) + cR2 * dC4;
+  // a constant added to the whole window shifts each state by that constant (the indicators
+  // do not change), so each gradient sums to one: the centre entries follow from the others
+  gL[2] = R(1) - ((gL[0] + gL[1]) + (gL[3] + gL[4]));
+  gR[2] = R(1) - ((gR[0] + gR[1]) + (gR[3] + gR[4]));
 }
 
 // Transpose of mix_factors<>: adds the adjoint of (num, den) to the tracer entries of Xb.
@@ -271,8 +280,14 @@ __device__ __forceinline__ void mix_factors_adj(const CstT<R> &C, R numb, R denb
   }
 }
 
+static __device__ __forceinline__ float adj_rsqrt(float x) { return rsqrtf(x); }
+static __device__ __forceinline__ double adj_rsqrt(double x) { return rsqrt(x); }
+
 // Transpose of lmars<>: accumulates XLb, XRb from Fb (forward values recomputed first, then
-// each assignment of lmars<> reversed in the opposite order).
+// each assignment of lmars<> reversed in the opposite order). Each side's sound speed comes
+// from one reciprocal square root r = (gamma p rho)^(-1/2): c = gamma p r, and the factors of
+// its derivative follow without further division, dc/dp = gamma r / 2, dc/drho = -c^2 r / 2
+// (1/rho = c r) and dc/dgamma = p r / 2; the star-state terms share one reciprocal of rho c.
 template <class R, class L>
 __device__ __forceinline__ void lmars_adj(const CstT<R> &C, const R *XL, const R *XR, int dir,
                                           R pref, const R *Fb, R *XLb, R *XRb) {
@@ -283,18 +298,21 @@ __device__ __forceinline__ void lmars_adj(const CstT<R> &C, const R *XL, const R
   mix_factors<R, L>(C, XL, numL, denL);
   mix_factors<R, L>(C, XR, numR, denR);
   const R pL = pref + XL[IE], pR = pref + XR[IE];
-  R gamL, gamR;
+  R gamL, gamR, inL = R(1), inR = R(1);
   if constexpr (L::NVAP == 0) {
     gamL = gamR = C.gamma_d;
   } else {
-    gamL = R(1) + gm1 * Ar<R>::div(denL, numL);
-    gamR = R(1) + gm1 * Ar<R>::div(denR, numR);
+    inL = Ar<R>::rcp(numL);
+    inR = Ar<R>::rcp(numR);
+    gamL = R(1) + gm1 * (denL * inL);
+    gamR = R(1) + gm1 * (denR * inR);
   }
-  const R cL = Ar<R>::sqrt_pos(gamL * pL * Ar<R>::rcp(XL[0]));
-  const R cR = Ar<R>::sqrt_pos(gamR * pR * Ar<R>::rcp(XR[0]));
+  const R rsL = adj_rsqrt(gamL * pL * XL[0]), rsR = adj_rsqrt(gamR * pR * XR[0]);
+  const R cL = gamL * pL * rsL, cR = gamR * pR * rsR;
   const R rhoc = R(0.5) * (XL[0] + XR[0]) * R(0.5) * (cL + cR);
+  const R irc = Ar<R>::rcp(rhoc), i2rc = R(0.5) * irc;
   const R uL = XL[mn], uR = XR[mn];
-  const R us = R(0.5) * (uL + uR) - Ar<R>::div(XR[IE] - XL[IE], R(2) * rhoc);
+  const R us = R(0.5) * (uL + uR) - (XR[IE] - XL[IE]) * i2rc;
   R usb = R(0), numLb = R(0), denLb = R(0), numRb = R(0), denRb = R(0);
   const R psb = Fb[mn];
 #pragma unroll
@@ -318,15 +336,18 @@ __device__ __forceinline__ void lmars_adj(const CstT<R> &C, const R *XL, const R
 #pragma unroll
       for (int j = 0; j < L::NCOND; ++j) muq += C.mu[i][j] * XS[L::cond(i, j)];
     const R K = R(0.5) * rhoS * u2;
-    R rS = R(1);
-    if constexpr (L::NVAP > 0) rS = Ar<R>::div(numS, denS);
+    R rS = R(1), iden = R(1);
+    if constexpr (L::NVAP > 0) {
+      iden = Ar<R>::rcp(denS);
+      rS = numS * iden;
+    }
     const R rhoe = rS * pS * igm1 + K + rhoS * muq;
     // F[E] = u* (rho e + p_S), rho e = (num/den) p_S / (gamma_d - 1) + K + A
     usb += wgt * Fb[IE] * (rhoe + pS);
     const R rhoeb = wgt * Fb[IE] * us;
     const R pSb = rhoeb + rhoeb * rS * igm1;
     if constexpr (L::NVAP > 0) {
-      const R rb = rhoeb * pS * igm1, iden = Ar<R>::rcp(denS);
+      const R rb = rhoeb * pS * igm1;
       if (use_left) {
         numLb += rb * iden;
         denLb -= rb * numS * iden * iden;
@@ -368,12 +389,11 @@ __device__ __forceinline__ void lmars_adj(const CstT<R> &C, const R *XL, const R
     }
   }
   R rhocb = R(0);
-  const R i2rc = Ar<R>::rcp(R(2) * rhoc);
   XLb[mn] += R(0.5) * usb;
   XRb[mn] += R(0.5) * usb;
   XRb[IE] -= usb * i2rc;
   XLb[IE] += usb * i2rc;
-  rhocb += usb * (XR[IE] - XL[IE]) * i2rc * Ar<R>::rcp(rhoc);
+  rhocb += usb * (XR[IE] - XL[IE]) * i2rc * irc;
   XLb[IE] += R(0.5) * psb;
   XRb[IE] += R(0.5) * psb;
   rhocb -= R(0.5) * (uR - uL) * psb;
@@ -382,14 +402,14 @@ __device__ __forceinline__ void lmars_adj(const CstT<R> &C, const R *XL, const R
   XLb[0] += R(0.25) * (cL + cR) * rhocb;
   XRb[0] += R(0.25) * (cL + cR) * rhocb;
   const R cb = R(0.25) * (XL[0] + XR[0]) * rhocb;
-  XLb[IE] += cb * cL * Ar<R>::rcp(R(2) * pL);
-  XLb[0] -= cb * cL * Ar<R>::rcp(R(2) * XL[0]);
-  XRb[IE] += cb * cR * Ar<R>::rcp(R(2) * pR);
-  XRb[0] -= cb * cR * Ar<R>::rcp(R(2) * XR[0]);
+  const R hL = R(0.5) * cb * rsL, hR = R(0.5) * cb * rsR;
+  XLb[IE] += hL * gamL;
+  XLb[0] -= hL * cL * cL;
+  XRb[IE] += hR * gamR;
+  XRb[0] -= hR * cR * cR;
   if constexpr (L::NVAP > 0) {
     // gamma = 1 + (gamma_d - 1) den / num
-    const R gLb = cb * cL * Ar<R>::rcp(R(2) * gamL), gRb = cb * cR * Ar<R>::rcp(R(2) * gamR);
-    const R inL = Ar<R>::rcp(numL), inR = Ar<R>::rcp(numR);
+    const R gLb = hL * pL, gRb = hR * pR;
     denLb += gLb * gm1 * inL;
     numLb -= gLb * gm1 * denL * inL * inL;
     denRb += gRb * gm1 * inR;
@@ -412,7 +432,8 @@ __device__ __forceinline__ void adj_face(const AdjArgs &a, const DomDev &D, cons
   const R *Ys = reinterpret_cast<const R *>(a.Ys);
   const R *lo = reinterpret_cast<const R *>(a.lam_out);
   R *G = reinterpret_cast<R *>(a.G[DIR]);
-  const R bdt = R(a.b * a.dt), ih = Prof<R>::ih(D, DIR);
+  const R bdt = R(a.b * a.dt), bih = bdt * Prof<R>::ih(D, DIR);
+  const R hgb = fz ? R(0.5) * Prof<R>::grav(D) * bdt : R(0);
   const int nd = DIR == 0 ? nx : (DIR == 1 ? ny : nz);
   const int bclo = D.bc[2 * DIR], bchi = D.bc[2 * DIR + 1];
   const int i = int(f % nfx), j = int((f / nfx) % nfy), k = int(f / ((long long)nfx * nfy));
@@ -425,14 +446,14 @@ __device__ __forceinline__ void adj_face(const AdjArgs &a, const DomDev &D, cons
   if (pos > 0) {
     const long long c = ((long long)(k - fz) * ny + (j - fy)) * nx + (i - fx);
 #pragma unroll
-    for (int v = 0; v < NV; ++v) Fb[v] -= bdt * lo[v * ncell + c] * ih;
-    if (fz) Fbz -= R(0.5) * Prof<R>::grav(D) * bdt * lo[L::IE * ncell + c];
+    for (int v = 0; v < NV; ++v) Fb[v] -= bih * lo[v * ncell + c];
+    if (fz) Fbz -= hgb * lo[L::IE * ncell + c];
   }
   if (pos < nd) {
     const long long c = ((long long)k * ny + j) * nx + i;
 #pragma unroll
-    for (int v = 0; v < NV; ++v) Fb[v] += bdt * lo[v * ncell + c] * ih;
-    if (fz) Fbz -= R(0.5) * Prof<R>::grav(D) * bdt * lo[L::IE * ncell + c];
+    for (int v = 0; v < NV; ++v) Fb[v] += bih * lo[v * ncell + c];
+    if (fz) Fbz -= hgb * lo[L::IE * ncell + c];
   }
   if (fz) {
 #pragma unroll
@@ -646,7 +667,8 @@ __device__ __forceinline__ void adj_face_w(const AdjArgs &a, const DomDev &D, co
   const R *lo = reinterpret_cast<const R *>(a.lam_out);
   const R *Wd = reinterpret_cast<const R *>(a.W[DIR]);
   R *G = reinterpret_cast<R *>(a.G[DIR]);
-  const R bdt = R(a.b * a.dt), ih = Prof<R>::ih(D, DIR);
+  const R bdt = R(a.b * a.dt), bih = bdt * Prof<R>::ih(D, DIR);
+  const R hgb = fz ? R(0.5) * Prof<R>::grav(D) * bdt : R(0);
   const int nd = DIR == 0 ? nx : (DIR == 1 ? ny : nz);
   const int i = int(f % nfx), j = int((f / nfx) % nfy), k = int(f / ((long long)nfx * nfy));
   const int pos = DIR == 0 ? i : (DIR == 1 ? j : k);
@@ -657,14 +679,14 @@ __device__ __forceinline__ void adj_face_w(const AdjArgs &a, const DomDev &D, co
   if (pos > 0) {
     const long long c = ((long long)(k - fz) * ny + (j - fy)) * nx + (i - fx);
 #pragma unroll
-    for (int v = 0; v < NV; ++v) Fb[v] -= bdt * lo[v * ncell + c] * ih;
-    if (fz) Fbz -= R(0.5) * Prof<R>::grav(D) * bdt * lo[L::IE * ncell + c];
+    for (int v = 0; v < NV; ++v) Fb[v] -= bih * lo[v * ncell + c];
+    if (fz) Fbz -= hgb * lo[L::IE * ncell + c];
   }
   if (pos < nd) {
     const long long c = ((long long)k * ny + j) * nx + i;
 #pragma unroll
-    for (int v = 0; v < NV; ++v) Fb[v] += bdt * lo[v * ncell + c] * ih;
-    if (fz) Fbz -= R(0.5) * Prof<R>::grav(D) * bdt * lo[L::IE * ncell + c];
+    for (int v = 0; v < NV; ++v) Fb[v] += bih * lo[v * ncell + c];
+    if (fz) Fbz -= hgb * lo[L::IE * ncell + c];
   }
   if (fz) {
 #pragma unroll
