@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdio.h>
+#include <stdint.h>
 #include <string.h>
 
 #include <algorithm>
@@ -48,38 +49,66 @@ int budget_blocks(long long ncell) {
 }
 
 // Caller layout <-> stored layout: the energy field (the last of nv) is shifted by the
-// per-level reference e_ref, in FP64; every value is converted to the destination type.
-template <class S, class D>
-__global__ void state_copy_kernel(const S *src, D *dst, int nv, long long ncell, long long plane,
+// per-level reference e_ref, in FP64; every value is converted to the destination type. One
+// grid row per (field, level) plane, so that a block knows its level without dividing the
+// element index; VW consecutive elements per thread (one 16-byte access of 4 floats, two of 4
+// doubles) where every plane starts on such a boundary, else one.
+template <class S, class D, int VW>
+__global__ void state_copy_kernel(const S *src, D *dst, int nv, int nz, int k0, long long plane,
                                   const double *e_ref, double sign) {
-  const long long n = (long long)nv * ncell, e0 = (long long)(nv - 1) * ncell;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x) {
-    if (i >= e0 && e_ref)
-      dst[i] = D(double(src[i]) + sign * e_ref[(i - e0) / plane]);
-    else
-      dst[i] = D(src[i]);
+  const int k = k0 + (int)blockIdx.y, v = blockIdx.z;
+  const long long base = ((long long)v * nz + k) * plane;
+  const bool shift = e_ref && v == nv - 1;
+  const double sh = shift ? sign * e_ref[k] : 0.0;
+  const long long stride = (long long)gridDim.x * blockDim.x * VW;
+  for (long long q = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * VW; q < plane;
+       q += stride) {
+    if (VW > 1 && q + VW <= plane) {
+      const Pack<S, VW> a = *reinterpret_cast<const Pack<S, VW> *>(src + base + q);
+      Pack<D, VW> b;
+#pragma unroll
+      for (int e = 0; e < VW; ++e) b.x[e] = shift ? D(double(a.x[e]) + sh) : D(a.x[e]);
+      *reinterpret_cast<Pack<D, VW> *>(dst + base + q) = b;
+    } else {
+      for (long long r = q; r < plane && r < q + VW; ++r)
+        dst[base + r] = shift ? D(double(src[base + r]) + sh) : D(src[base + r]);
+    }
   }
+}
+
+template <class S, class D>
+static cudaError_t copy_typed(const void *src, void *dst, int nv, long long ncell,
+                              long long plane, const double *e_ref, double sg, cudaStream_t s) {
+  constexpr int VW = 4;
+  const int block = 256;
+  const long long nz = ncell / plane;
+  const long long per = (plane + (long long)block * VW - 1) / ((long long)block * VW);
+  const bool vec = plane % VW == 0 && (uintptr_t)src % (sizeof(S) * VW) == 0 &&
+                   (uintptr_t)dst % (sizeof(D) * VW) == 0;
+  // levels in chunks of at most 65535 (the grid's y limit); nv is far below the z limit
+  for (long long k0 = 0; k0 < nz; k0 += 65535) {
+    const long long nk = nz - k0 < 65535 ? nz - k0 : 65535;
+    const dim3 grid((unsigned)(per < 4096 ? per : 4096), (unsigned)nk, (unsigned)nv);
+    if (vec)
+      state_copy_kernel<S, D, VW><<<grid, block, 0, s>>>((const S *)src, (D *)dst, nv, (int)nz,
+                                                         (int)k0, plane, e_ref, sg);
+    else
+      state_copy_kernel<S, D, 1><<<grid, block, 0, s>>>((const S *)src, (D *)dst, nv, (int)nz,
+                                                        (int)k0, plane, e_ref, sg);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 cudaError_t launch_state_copy(const void *src, int src_f32, void *dst, int dst_f32, int nv,
                               long long ncell, long long plane, const double *e_ref,
                               int to_stored, cudaStream_t s) {
-  const int grid = 1216, block = 256;
   const double sg = to_stored ? -1.0 : 1.0;
-  if (src_f32 && !dst_f32)
-    state_copy_kernel<float, double><<<grid, block, 0, s>>>((const float *)src, (double *)dst,
-                                                            nv, ncell, plane, e_ref, sg);
-  else if (!src_f32 && dst_f32)
-    state_copy_kernel<double, float><<<grid, block, 0, s>>>((const double *)src, (float *)dst,
-                                                            nv, ncell, plane, e_ref, sg);
-  else if (src_f32)
-    state_copy_kernel<float, float><<<grid, block, 0, s>>>((const float *)src, (float *)dst,
-                                                           nv, ncell, plane, e_ref, sg);
-  else
-    state_copy_kernel<double, double><<<grid, block, 0, s>>>((const double *)src, (double *)dst,
-                                                             nv, ncell, plane, e_ref, sg);
-  return cudaGetLastError();
+  if (src_f32 && !dst_f32) return copy_typed<float, double>(src, dst, nv, ncell, plane, e_ref, sg, s);
+  if (!src_f32 && dst_f32) return copy_typed<double, float>(src, dst, nv, ncell, plane, e_ref, sg, s);
+  if (src_f32) return copy_typed<float, float>(src, dst, nv, ncell, plane, e_ref, sg, s);
+  return copy_typed<double, double>(src, dst, nv, ncell, plane, e_ref, sg, s);
 }
 // The three columns x0 .. x0+2 of every row of a state (fields [nv][nrow][nx]) into a
 // contiguous [nv][nrow][3] buffer: a slab's cells next to one of its x sides, which are the
@@ -774,9 +803,15 @@ extern "C" int snap_set_state(snap_ctx *ctx, int domain, const void *Y, int dtyp
       src = ctx->staging;
     }
   }
-  CK(launch_state_copy(src, src_f32, D.buf[0], ctx->f32, ctx->nv, D.ncell,
-                       (long long)D.nx * D.ny, D.e_ref, 1, s));
-  return refresh_rate(ctx, domain, s);
+  // the stored state and its CFL rate in one pass; the rate slot is shared by the domains of
+  // a CFL group, so the others' rates are formed again after it is cleared
+  const int g = ctx->grp[domain];
+  CK(cudaMemsetAsync(ctx->rate_dev + g, 0, sizeof(unsigned long long), s));
+  const StageArgs a = args_of(ctx, 0);
+  CK(ctx->ks.load(src, src_f32, a, domain, (long long)D.nx * D.ny, D.nz, s));
+  for (int i = 0; i < ctx->ndom; ++i)
+    if (i != domain && ctx->grp[i] == g) CK(ctx->ks.rate(a, i, 0, s));
+  return SNAP_OK;
 }
 
 extern "C" int snap_get_state(snap_ctx *ctx, int domain, void *Y_out, int dtype, int on_device,

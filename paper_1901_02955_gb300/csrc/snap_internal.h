@@ -144,10 +144,20 @@ struct TileVariant {
 constexpr int kMaxVariants = 4;
 
 // Kernel family entry points (one per instantiated layout and type).
+// N consecutive values of type T moved as one aligned access (16 bytes for 4 floats).
+template <class T, int N>
+struct alignas(sizeof(T) * N) Pack {
+  T x[N];
+};
+
 struct KernelSet {
   int nvariants;
   TileVariant var[kMaxVariants];
   cudaError_t (*rate)(const StageArgs &, int dom, int buf, cudaStream_t);
+  // a caller-layout state (FP32 or FP64, device-accessible) into the domain's stored state,
+  // with the CFL rate of the result folded into the domain's rate slot
+  cudaError_t (*load)(const void *src, int src_f32, const StageArgs &, int dom, long long plane,
+                      long long nz, cudaStream_t);
   cudaError_t (*budget)(const StageArgs &, int dom, int buf, double *partials, int nblocks,
                         double *out, cudaStream_t);
   cudaError_t (*satadj)(const StageArgs &, int dom, int buf, cudaStream_t);

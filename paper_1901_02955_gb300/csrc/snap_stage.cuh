@@ -1695,20 +1695,72 @@ __global__ void __launch_bounds__(T::NT, T::MINB) resident_step_kernel(const Sta
 // ------------------------------------------------------------------------------------------
 // auxiliary kernels: CFL rate, budget, saturation adjustment over a domain
 // ------------------------------------------------------------------------------------------
+// The blocks take (level, chunk of blockDim.x cells of the level) items in turn, so the level
+// of a cell comes from one division per item, not one per cell.
 template <class R, class L>
 __global__ void __launch_bounds__(256) rate_kernel(const StageArgs a, int dm, int buf) {
   __shared__ double red[32];
   const DomDev &D = a.doms[dm];
   const R *Y = reinterpret_cast<const R *>(D.buf[buf]);
+  const long long plane = (long long)D.nx * D.ny;
+  const long long chunks = (plane + blockDim.x - 1) / blockDim.x;
+  const long long items = chunks * D.nz;
   double r = 0.0;
-  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < D.ncell;
-       c += (long long)gridDim.x * blockDim.x) {
-    R y[L::NV];
+  for (long long it = blockIdx.x; it < items; it += gridDim.x) {
+    const int k = int(it / chunks);
+    const long long p = (it - k * chunks) * blockDim.x + threadIdx.x;
+    if (p < plane) {
+      const long long c = k * plane + p;
+      R y[L::NV];
 #pragma unroll
-    for (int v = 0; v < L::NV; ++v) y[v] = Y[v * D.ncell + c];
-    const int k = int(c / ((long long)D.nx * D.ny));
-    r = fmax(r, double(cell_rate_r<R, L>(cst<R>(a), y, Prof<R>::er(D, k), Prof<R>::ih(D, 0),
-                                         Prof<R>::ih(D, 1), Prof<R>::ih(D, 2))));
+      for (int v = 0; v < L::NV; ++v) y[v] = Y[v * D.ncell + c];
+      r = fmax(r, double(cell_rate_r<R, L>(cst<R>(a), y, Prof<R>::er(D, k), Prof<R>::ih(D, 0),
+                                           Prof<R>::ih(D, 1), Prof<R>::ih(D, 2))));
+    }
+  }
+  double bm = block_max(r, red);
+  if (threadIdx.x == 0) atomicMax(D.rate, (unsigned long long)__double_as_longlong(bm));
+}
+
+// A caller-layout state (type S: energy as rho e) into the stored state of domain dm (type R,
+// energy as rho e - e_ref of the level, the difference formed in FP64), with the CFL rate of
+// the stored cells folded into the domain's rate slot: the state copy and the rate kernel in
+// one pass. Items as in rate_kernel; VW consecutive cells of a level per thread, each field
+// one aligned access (VW = 4 where every level starts on such a boundary, else 1).
+template <class S, class R, class L, int VW>
+__global__ void __launch_bounds__(256) load_rate_kernel(const S *src, const StageArgs a, int dm) {
+  __shared__ double red[32];
+  const DomDev &D = a.doms[dm];
+  R *Y = reinterpret_cast<R *>(D.buf[0]);
+  const long long plane = (long long)D.nx * D.ny, ncell = D.ncell;
+  const long long span = (long long)blockDim.x * VW;
+  const long long chunks = (plane + span - 1) / span;
+  const long long items = chunks * D.nz;
+  const CstT<R> &C = cst<R>(a);
+  double r = 0.0;
+  for (long long it = blockIdx.x; it < items; it += gridDim.x) {
+    const int k = int(it / chunks);
+    const long long p = (it - k * chunks) * span + (long long)threadIdx.x * VW;
+    if (p < plane) {  // VW divides plane, so all VW cells lie in the level
+      const long long c0 = k * plane + p;
+      const double er = D.e_ref[k];
+      R y[VW][L::NV];
+#pragma unroll
+      for (int v = 0; v < L::NV; ++v) {
+        const Pack<S, VW> in = *reinterpret_cast<const Pack<S, VW> *>(src + v * ncell + c0);
+        Pack<R, VW> out;
+#pragma unroll
+        for (int e = 0; e < VW; ++e) {
+          out.x[e] = v == L::IE ? R(double(in.x[e]) - er) : R(in.x[e]);
+          y[e][v] = out.x[e];
+        }
+        *reinterpret_cast<Pack<R, VW> *>(Y + v * ncell + c0) = out;
+      }
+#pragma unroll
+      for (int e = 0; e < VW; ++e)
+        r = fmax(r, double(cell_rate_r<R, L>(C, y[e], Prof<R>::er(D, k), Prof<R>::ih(D, 0),
+                                             Prof<R>::ih(D, 1), Prof<R>::ih(D, 2))));
+    }
   }
   double bm = block_max(r, red);
   if (threadIdx.x == 0) atomicMax(D.rate, (unsigned long long)__double_as_longlong(bm));
@@ -1880,6 +1932,23 @@ struct Family {
     rate_kernel<R, L><<<304, 256, 0, s>>>(a, dm, buf);
     return cudaGetLastError();
   }
+  template <class S>
+  static cudaError_t load_typed(const void *src, const StageArgs &a, int dm, long long plane,
+                                long long nz, cudaStream_t s) {
+    const long long span = 256ll * 4, chunks = (plane + span - 1) / span;
+    const long long items = chunks * nz;
+    const int grid = int(items < 1216 ? items : 1216);
+    if (plane % 4 == 0 && (uintptr_t)src % (4 * sizeof(S)) == 0)
+      load_rate_kernel<S, R, L, 4><<<grid, 256, 0, s>>>((const S *)src, a, dm);
+    else
+      load_rate_kernel<S, R, L, 1><<<grid, 256, 0, s>>>((const S *)src, a, dm);
+    return cudaGetLastError();
+  }
+  static cudaError_t load(const void *src, int src_f32, const StageArgs &a, int dm,
+                          long long plane, long long nz, cudaStream_t s) {
+    return src_f32 ? load_typed<float>(src, a, dm, plane, nz, s)
+                   : load_typed<double>(src, a, dm, plane, nz, s);
+  }
   static cudaError_t budget(const StageArgs &a, int dm, int buf, double *partials, int nblocks,
                             double *out, cudaStream_t s) {
     budget_kernel<R, L><<<nblocks, 256, 0, s>>>(a, dm, buf, partials);
@@ -1898,6 +1967,7 @@ struct Family {
     TileVariant vs[] = {Variant<R, L, VISC, Ts>::get()...};
     for (const TileVariant &v : vs) k.var[k.nvariants++] = v;
     k.rate = &rate;
+    k.load = &load;
     k.budget = &budget;
     k.satadj = &satadj;
     return k;
@@ -1910,6 +1980,7 @@ struct Family {
     TileVariant vs[] = {Variant<R, L, false, Ts, true>::get()...};
     for (const TileVariant &v : vs) k.var[k.nvariants++] = v;
     k.rate = &rate;
+    k.load = &load;
     k.budget = &budget;
     k.satadj = &satadj;
     return k;
