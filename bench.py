@@ -758,9 +758,7 @@ def main():
     host_in = torch.from_numpy(w32.Y.astype(np.float32)).pin_memory()
     host_out = torch.empty_like(host_in).pin_memory()
     for _ in range(max(2, args.warmup)):
-        ctx.set_state(host_in)
-        ctx.step_async(1)
-        ctx.get_state(out=host_out)
+        ctx.step_io(host_in, host_out, nsteps=1)
     barrier()
     step_s = []
     for _ in range(args.steps):
@@ -768,17 +766,18 @@ def main():
         flush.fill_(1)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        ctx.set_state(host_in)
-        ctx.step_async(1)
-        ctx.get_state(out=host_out)  # synchronises: the step's result is on the host
+        # one call: the state read from pinned host memory, one step, the result written to
+        # pinned host memory; returns when it is there
+        ctx.step_io(host_in, host_out, nsteps=1)
         step_s.append(time.perf_counter() - t0)
     barrier()
     e2e_s = max_over_ranks(float(np.mean(step_s)))
     nbytes = host_in.numel() * 4
     e2e = {"value": world * cells * 3 / e2e_s, "unit": UNIT, "h2d_bytes_per_step": nbytes,
            "d2h_bytes_per_step": nbytes,
-           "note": "host wall clock per step: pinned copy in, one step, copy out to the host; "
-                   "L2 flushed before each step outside the timed region"}
+           "note": "host wall clock per step of snap_step_io: the state read from pinned host "
+                   "memory (with its CFL rate), one step, the result written to pinned host "
+                   "memory; L2 flushed before each step outside the timed region"}
     ctx.close()
 
     # ---- FP64 fused step beside it ---------------------------------------------------------

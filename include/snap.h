@@ -169,6 +169,19 @@ int snap_step(snap_ctx *ctx, int nsteps, double dt_fixed, double *dt_used,
  * no status read-back (use snap_check). Same dt_fixed meaning as snap_step. */
 int snap_step_async(snap_ctx *ctx, int nsteps, double dt_fixed);
 
+/* One call from a caller's state to the state nsteps steps later (Sec. 4.3 steps, as
+ * snap_step_async), for one domain: snap_set_state, snap_step_async and snap_get_state with
+ * the buffer kinds found by the library.
+ *   Y_in   NULL (keep the context's state) or a state in the caller's layout of snap_set_state
+ *          (device memory, page-locked or pageable host memory), read before the first step;
+ *   Y_out  NULL or a buffer of the same layout for the state after the last step;
+ *   dtype  SNAP_F32 or SNAP_F64, the type of Y_in and Y_out.
+ * Returns when Y_out (if host memory) holds the result; with Y_out on the device or NULL the
+ * work is only enqueued. No status read-back (use snap_check). SNAP_EINVAL for a bad domain,
+ * nsteps < 1 or dtype; the errors of snap_set_state, snap_step_async and snap_get_state. */
+int snap_step_io(snap_ctx *ctx, int domain, const void *Y_in, void *Y_out, int dtype, int nsteps,
+                 double dt_fixed);
+
 /* Enqueue one Runge-Kutta stage (0, 1 or 2 of Sec. 4.3) for every domain. Stage 0 reads the
  * state and writes the first intermediate, stage 1 the second, stage 2 writes the new state in
  * place; a step is the three in order. For timing and tests of single stages. */

@@ -24,6 +24,7 @@ F64, F32 = 0, 1
 
 # every function declared in include/snap.h
 EXPORTS = ["snap_init_grid", "snap_set_state", "snap_get_state", "snap_step", "snap_step_async",
+           "snap_step_io",
            "snap_stage", "snap_check", "snap_reset_flags", "snap_budget_compute",
            "snap_compute_dt", "snap_saturation_adjust", "snap_record", "snap_step_adjoint",
            "snap_set_stream",
@@ -98,6 +99,7 @@ def load(path: Optional[str] = None) -> C.CDLL:
     lib.snap_get_state.argtypes = [P, C.c_int, P, C.c_int, C.c_int, P]
     lib.snap_step.argtypes = [P, C.c_int, C.c_double, C.POINTER(C.c_double), C.POINTER(Budget)]
     lib.snap_step_async.argtypes = [P, C.c_int, C.c_double]
+    lib.snap_step_io.argtypes = [P, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_double]
     lib.snap_stage.argtypes = [P, C.c_int, C.c_double]
     lib.snap_check.argtypes = [P, C.POINTER(C.c_uint)]
     lib.snap_reset_flags.argtypes = [P]
@@ -218,16 +220,24 @@ class Context:
             pass
 
     # -- state --------------------------------------------------------------------------
+    def _sized(self, Y, domain, what):
+        w = self.workloads[domain]
+        n = w.nv * w.nz * w.ny * w.nx
+        if (Y.size if isinstance(Y, np.ndarray) else Y.numel()) != n:
+            raise ValueError(f"{what}: expected {n} values (nv, nz, ny, nx) = "
+                             f"{(w.nv, w.nz, w.ny, w.nx)} for domain {domain}")
+        return Y
+
     def set_state(self, Y, domain=0, stream=None):
         """Y: numpy array (host) or torch tensor (CUDA or CPU), float32 or float64."""
-        ptr, dt, dev = _buffer(Y)
+        ptr, dt, dev = _buffer(self._sized(Y, domain, "set_state"))
         return self._check(self.lib.snap_set_state(self._ptr, domain, ptr, dt, dev, stream))
 
     def get_state(self, domain=0, out=None, dtype=np.float64, stream=None):
         w = self.workloads[domain]
         if out is None:
             out = np.empty((w.nv, w.nz, w.ny, w.nx), dtype=dtype)
-        ptr, dt, dev = _buffer(out)
+        ptr, dt, dev = _buffer(self._sized(out, domain, "get_state"))
         self._check(self.lib.snap_get_state(self._ptr, domain, ptr, dt, dev, stream))
         return out
 
@@ -239,6 +249,23 @@ class Context:
 
     def step_async(self, nsteps=1, dt_fixed=0.0):
         return self._check(self.lib.snap_step_async(self._ptr, nsteps, dt_fixed))
+
+    def step_io(self, Y=None, out=None, nsteps=1, dt_fixed=0.0, domain=0):
+        """snap_step_io: optionally load Y, advance nsteps, optionally write the result into
+        out (numpy array or torch tensor of the state's shape, float32 or float64; the same
+        type as Y when both are given). Returns out."""
+        ptr_in, dt_in, ptr_out, dt_out = None, None, None, None
+        if Y is not None:
+            ptr_in, dt_in, _ = _buffer(self._sized(Y, domain, "step_io"))
+        if out is not None:
+            ptr_out, dt_out, _ = _buffer(self._sized(out, domain, "step_io"))
+        if dt_in is not None and dt_out is not None and dt_in != dt_out:
+            raise ValueError("step_io: Y and out must have the same type")
+        dt = dt_in if dt_in is not None else (dt_out if dt_out is not None else
+                                                 (F32 if self.f32 else F64))
+        self._check(self.lib.snap_step_io(self._ptr, domain, ptr_in, ptr_out, dt, nsteps,
+                                          dt_fixed))
+        return out
 
     def stage(self, stage, dt_fixed=0.0):
         return self._check(self.lib.snap_stage(self._ptr, stage, dt_fixed))

@@ -1093,6 +1093,43 @@ extern "C" int snap_step_async(snap_ctx *ctx, int nsteps, double dt_fixed) {
   return SNAP_OK;
 }
 
+// Where a caller's buffer is for the device: 1 device (or managed) memory, 2 page-locked host
+// memory mapped into the device (*dev set to its device address), 0 pageable host memory.
+static int buffer_kind(const void *p, void **dev) {
+  cudaPointerAttributes a;
+  int kind = 0;
+  *dev = nullptr;
+  if (cudaPointerGetAttributes(&a, p) == cudaSuccess) {
+    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) {
+      kind = 1;
+      *dev = const_cast<void *>(p);
+    } else if (a.type == cudaMemoryTypeHost && a.devicePointer) {
+      kind = 2;
+      *dev = a.devicePointer;
+    }
+  }
+  cudaGetLastError();
+  return kind;
+}
+
+extern "C" int snap_step_io(snap_ctx *ctx, int domain, const void *Y_in, void *Y_out, int dtype,
+                            int nsteps, double dt_fixed) {
+  if (!ctx) return fail(nullptr, SNAP_EINVAL, "snap_step_io: NULL context");
+  if (domain < 0 || domain >= ctx->ndom || nsteps < 1 || (dtype != SNAP_F64 && dtype != SNAP_F32))
+    return fail(ctx, SNAP_EINVAL, "snap_step_io: bad domain, nsteps or dtype");
+  int rc;
+  if (Y_in) {
+    void *d = nullptr;
+    const int kind = buffer_kind(Y_in, &d);
+    if ((rc = snap_set_state(ctx, domain, Y_in, dtype, kind == 1, nullptr))) return rc;
+  }
+  if ((rc = snap_step_async(ctx, nsteps, dt_fixed))) return rc;
+  if (!Y_out) return SNAP_OK;
+  void *dst = nullptr;
+  const int kind = buffer_kind(Y_out, &dst);
+  return snap_get_state(ctx, domain, Y_out, dtype, kind == 1, nullptr);
+}
+
 static int read_status(snap_ctx *ctx, unsigned int *flags_out, int *sweeps_out) {
   unsigned int flags = 0;
   int sweeps = 0;

@@ -55,3 +55,79 @@ def test_pinned_and_pageable_host_buffers_agree(torch, ctx_dtype, io, shape):
         assert np.array_equal(out.numpy(), ref), steps
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("ctx_dtype", ["f32", "f64"])
+@pytest.mark.parametrize("buf", ["pinned", "device", "pageable", "other_type"])
+def test_step_io_equals_set_step_get(torch, ctx_dtype, buf):
+    """snap_step_io (state in, steps, state out in one call) gives bitwise the state of
+    set_state, the same steps and get_state, for page-locked, device and pageable buffers and
+    for buffers of the other type."""
+    from paper_1901_02955_gb300 import Context
+    w = W.add_random_motion(W.moist_bubble(nx=45, nz=35))
+    io = np.float64 if ctx_dtype == "f64" else np.float32
+    if buf == "other_type":
+        io = np.float32 if io == np.float64 else np.float64
+    tio = torch.float64 if io == np.float64 else torch.float32
+    Y = np.ascontiguousarray(w.Y.astype(io))
+    a = Context(w, dtype=ctx_dtype)
+    b = Context(w, dtype=ctx_dtype)
+    a.set_state(Y)
+    a.step(3, dt_fixed=0.02)
+    ref = a.get_state(dtype=io)
+    if buf == "pinned" or buf == "other_type":
+        y_in = torch.from_numpy(Y.copy()).pin_memory()
+        out = torch.empty(Y.shape, dtype=tio).pin_memory()
+    elif buf == "device":
+        y_in = torch.from_numpy(Y.copy()).cuda()
+        out = torch.empty(Y.shape, dtype=tio, device="cuda")
+    else:
+        y_in = Y.copy()
+        out = np.empty_like(Y)
+    b.step_io(y_in, out, nsteps=3, dt_fixed=0.02)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy() if not isinstance(out, np.ndarray) else out
+    assert np.array_equal(got, ref)
+    # the context holds the same state afterwards, and a later plain step leaves out alone
+    assert np.array_equal(b.get_state(dtype=io), ref)
+    if buf == "pinned":
+        keep = got.copy()
+        b.step(1, dt_fixed=0.02)
+        assert np.array_equal(out.numpy(), keep)
+    a.close()
+    b.close()
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_step_io_in_an_ensemble_and_the_persistent_step(torch, mode):
+    """In an ensemble the chosen domain's state comes out, in the three-launch step and in the
+    persistent one-launch step (dry domains: the two launch modes agree bitwise); every
+    domain advances."""
+    from paper_1901_02955_gb300 import Context
+    ws = [W.add_random_motion(W.warm_bubble(n=n)) for n in (40, 33, 48)]
+    a = Context(ws, dtype="f32")
+    b = Context(ws, dtype="f32")
+    b.use_persistent(mode)
+    for d, w in enumerate(ws):
+        a.set_state(w.Y.astype(np.float32), domain=d)
+        b.set_state(w.Y.astype(np.float32), domain=d)
+    a.step(2, dt_fixed=0.02)
+    out = torch.full(ws[1].Y.shape, -1.0, dtype=torch.float32).pin_memory()
+    b.step_io(None, out, nsteps=2, dt_fixed=0.02, domain=1)
+    assert np.array_equal(out.numpy(), a.get_state(domain=1, dtype=np.float32))
+    for d in range(3):
+        assert np.array_equal(b.get_state(domain=d, dtype=np.float32),
+                              a.get_state(domain=d, dtype=np.float32)), d
+    a.close()
+    b.close()
+
+
+def test_step_io_rejects_a_buffer_of_the_wrong_size(torch):
+    from paper_1901_02955_gb300 import Context
+    w = W.moist_bubble(nx=20, nz=16)
+    ctx = Context(w, dtype="f32")
+    with pytest.raises(ValueError):
+        ctx.step_io(None, np.empty((w.nv, w.nz, w.nx + 1), dtype=np.float32))
+    with pytest.raises(ValueError):
+        ctx.set_state(np.zeros(5, dtype=np.float32))
+    ctx.close()
