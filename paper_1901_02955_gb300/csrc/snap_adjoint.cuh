@@ -57,6 +57,20 @@ __device__ __forceinline__ const CstT<float> &acst<float>(const AdjArgs &a) { re
 template <>
 __device__ __forceinline__ const CstT<double> &acst<double>(const AdjArgs &a) { return a.cd; }
 
+// The shared reciprocal of the FP64 window transpose to ~1e-12 relative: the hardware's
+// approximate FP64 reciprocal (about 1e-6) and one Newton-Raphson step, which squares its
+// error (the adjoint is held to 1e-10 of the oracle's); FP32 as the forward kernels.
+template <class R>
+__device__ __forceinline__ R adj_rcp(R x) {
+  if constexpr (sizeof(R) == 8) {
+    double y;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+    return fma(y, fma(-x, y, 1.0), y);
+  } else {
+    return Ar<R>::rcp(x);
+  }
+}
+
 // WENO5 value of the left state from (a..e) and its gradient (Jiang-Shu weights):
 // dI/dq_j = sum_k w_k dv_k/dq_j + sum_k (v_k - I)/S (-2 alpha_k/(eps+beta_k)) dbeta_k/dq_j.
 template <class R>
@@ -201,9 +215,9 @@ __device__ __forceinline__ void weno5_pair_grad(const R q[5], R eps, R &QL, R &Q
   // indicator term below pairs a 13/12 larger factor 1 / e_k with a 12/13 smaller d beta
   constexpr R k3 = R(3.0 / 13.0);
   eps *= R(12.0 / 13.0);
-  const R e0 = eps + (tA * tA + (k3 * sA) * sA);
-  const R e1 = eps + (tB * tB + (k3 * sB) * sB);
-  const R e2 = eps + (tC * tC + (k3 * sC) * sC);
+  const R e0 = fma(tA, tA, fma(k3 * sA, sA, eps));
+  const R e1 = fma(tB, tB, fma(k3 * sB, sB, eps));
+  const R e2 = fma(tC, tC, fma(k3 * sC, sC, eps));
   // d beta / d q over each sub-stencil's own cells, but for the centre q2 (see below)
   const R dA0 = R(2) * tA + R(6.0 / 13.0) * sA, dA1 = R(-4) * tA - R(24.0 / 13.0) * sA;
   const R dB1 = R(2) * tB + R(6.0 / 13.0) * sB;
@@ -217,7 +231,7 @@ __device__ __forceinline__ void weno5_pair_grad(const R q[5], R eps, R &QL, R &Q
   const R nL1 = n1, nR1 = n1;
   const R AL = nL0 + n1 + nL2, AR = nR0 + n1 + nR2;
   R iAL, iAR, iP;
-  const R Z = Ar<R>::rcp(AL * AR * P);  // NaN outside the normal range: the test below fails
+  const R Z = adj_rcp<R>(AL * AR * P);  // NaN outside the normal range: the test below fails
   bool finite_pos;
   if constexpr (sizeof(R) == 8) {
     // 0 < Z < infinity (and not a NaN) from the high word, off the FP64 pipe: sign clear,
@@ -241,10 +255,11 @@ __device__ __forceinline__ void weno5_pair_grad(const R q[5], R eps, R &QL, R &Q
   // first-difference combinations s as the indicators: the left state's on A, B, C are
   // q2 + t/12 + s/4, q2 + t/12 - s/4, q2 + t/12 - s/4; the right state's q2 + t/12 - s/4,
   // q2 + t/12 + s/4, q2 + t/12 + s/4
-  const R TA = tA * R(1.0 / 12.0), TB = tB * R(1.0 / 12.0), TC = tC * R(1.0 / 12.0);
   const R SA = sA * R(0.25), SB = sB * R(0.25), SC = sC * R(0.25);
-  const R dL0 = TA + SA, dL1 = TB - SB, dL2 = TC - SC;
-  const R dR0 = TA - SA, dR1 = TB + SB, dR2 = TC + SC;
+  const R dL0 = fma(tA, R(1.0 / 12.0), SA), dL1 = fma(tB, R(1.0 / 12.0), -SB);
+  const R dL2 = fma(tC, R(1.0 / 12.0), -SC);
+  const R dR0 = fma(tA, R(1.0 / 12.0), -SA), dR1 = fma(tB, R(1.0 / 12.0), SB);
+  const R dR2 = fma(tC, R(1.0 / 12.0), SC);
   const R DL = wL0 * dL0 + wL1 * dL1 + wL2 * dL2, DR = wR0 * dR0 + wR1 * dR1 + wR2 * dR2;
   QL = q[2] + DL;
   QR = q[2] + DR;
