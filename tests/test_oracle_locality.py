@@ -47,9 +47,9 @@ def test_moist_xz_stage_depends_on_three_cells_each_way():
 
 
 def test_a_stencil_reaching_four_cells_would_be_seen():
-    """The window check is sensitive: the result at a cell four cells from the window's edge
-    differs between the full domain and a window that ends three cells from it, once the
-    flow there is not uniform."""
+    """The window check is sensitive: at the cell next to the window's centre, whose stencil
+    reaches one cell past the window's edge, the window's result differs from the full
+    domain's once the flow there is not uniform."""
     w = W.add_random_motion(W.jovian(nx=16, ny=16, nz=16, dtype="f64"))
     full, _ = Oracle(w).stage(0, w.Y, w.Y, 0.5)
     ww = window_of(w, 8, 8, 8)
