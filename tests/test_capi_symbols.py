@@ -115,3 +115,20 @@ def test_noslip_and_bottom_temperature_are_validated(lib):
     d.T_bottom = -1.0
     assert L.snap_init_grid(ctypes.byref(p), ctypes.byref(d), 1) == capi.EINVAL
     assert b"T_bottom" in L.snap_last_error(None)
+
+
+def test_empty_and_degenerate_grids_rejected_on_host(lib):
+    """No domain, a NULL descriptor, an empty axis or one shorter than the three cells a
+    WENO5 stencil reaches each way: SNAP_EINVAL before any CUDA call."""
+    import workloads as W
+    from paper_1901_02955_gb300 import capi
+    L = capi.load()
+    p = ctypes.c_void_p()
+    w = W.warm_bubble(n=8)
+    d, keep = capi.desc_from_workload(w)
+    assert L.snap_init_grid(ctypes.byref(p), ctypes.byref(d), 0) == capi.EINVAL
+    assert L.snap_init_grid(ctypes.byref(p), None, 1) == capi.EINVAL
+    for field, value in (("nx", 0), ("nz", 0), ("nz", 2), ("ny", 0)):
+        d, keep = capi.desc_from_workload(w)
+        setattr(d, field, value)
+        assert L.snap_init_grid(ctypes.byref(p), ctypes.byref(d), 1) == capi.EINVAL, (field, value)
