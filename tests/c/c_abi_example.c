@@ -83,6 +83,20 @@ int main(void) {
     }
   const double dm = fabs(b1.total[0] / b0.total[0] - 1.0);
   const double de = fabs(b1.energy_with_potential / b0.energy_with_potential - 1.0);
+  /* five more steps from Y in one call, against set_state, the same steps and get_state */
+  double *A = (double *)malloc(sizeof(double) * 4 * n), *B = (double *)malloc(sizeof(double) * 4 * n);
+  if (!A || !B) return 1;
+  if (check(snap_step_io(ctx, 0, Y, A, SNAP_F64, 5, 0.0), "snap_step_io", ctx)) return 1;
+  if (check(snap_set_state(ctx, 0, Y, SNAP_F64, 0, NULL), "snap_set_state", ctx)) return 1;
+  if (check(snap_step(ctx, 5, 0.0, NULL, NULL), "snap_step", ctx)) return 1;
+  if (check(snap_get_state(ctx, 0, B, SNAP_F64, 0, NULL), "snap_get_state", ctx)) return 1;
+  for (long c = 0; c < 4 * n; ++c)
+    if (A[c] != B[c]) {
+      fprintf(stderr, "snap_step_io differs at %ld\n", c);
+      return 1;
+    }
+  free(A);
+  free(B);
   snap_free(ctx);
   free(Y);
   if (!(dt > 0.0) || dm > 1e-12 || de > 1e-12) {
