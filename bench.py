@@ -127,26 +127,26 @@ def measured_peaks():
     return FALLBACK_HBM_GBS, "fallback"
 
 
-def kernel_sources_md5():
-    """Hash of the sources that define the stage kernel (its template, the structures it reads
-    and the tile it is instantiated with); a change in any invalidates the committed ncu
-    traffic figure."""
+def kernel_sources_md5(kern="kern_dry2d.cu"):
+    """Hash of the sources that define a stage kernel (its template, the structures it reads
+    and the file that instantiates it with its tiles); a change in any invalidates the
+    committed ncu traffic figure."""
     h = hashlib.md5()
     csrc = os.path.join(ROOT, "paper_1901_02955_gb300", "csrc")
-    for f in ("snap_stage.cuh", "snap_internal.h", "kern_dry2d.cu"):
+    for f in ("snap_stage.cuh", "snap_internal.h", kern):
         h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()
 
 
-def ncu_record():
-    """The committed ncu record of the stage kernel (DRAM bytes and warp instructions per
+def ncu_record(name="density_current", kern="kern_dry2d.cu"):
+    """The committed ncu record of a stage kernel (DRAM bytes and warp instructions per
     launch), if it was taken on the current kernel sources (else an empty dict)."""
-    path = os.path.join(ROOT, "profiles", "stage_kernel_density_current_traffic.json")
+    path = os.path.join(ROOT, "profiles", f"stage_kernel_{name}_traffic.json")
     if not os.path.exists(path):
         return {}
     try:
         d = json.load(open(path))
-        if d.get("sources_md5") == kernel_sources_md5():
+        if d.get("sources_md5") == kernel_sources_md5(kern):
             return d
     except Exception:
         pass
@@ -852,21 +852,32 @@ def timed_steps(ctx, stream, steps, warmup):
     return float(np.mean([s_.elapsed_time(e_) for s_, e_ in ev]))
 
 
-def stage_rooflines(ms_step, cells, nv, D, peak, peak_src):
-    """ALU and HBM fractions of the stage kernel from the in-step time (step / 3)."""
+def stage_rooflines(ms_step, cells, nv, D, peak, peak_src, record=None):
+    """ALU and HBM fractions of the stage kernel from the in-step time (step / 3); with a
+    current ncu record, its DRAM bytes per launch (traffic) and the warp-instruction issue
+    fraction."""
     stage_s = ms_step / 3.0 * 1e-3
     flops = alg_flops_per_cell_stage(D, D, nv)
     flops_sh = alg_flops_per_cell_stage(D, D, nv, shared_indicators=True)
     gbs = (8.0 / 3.0) * nv * 4 * cells / stage_s / 1e9
-    return {"stage_ms": ms_step / 3.0,
-            "alu": {"achieved": flops * cells / stage_s / 1e12, "peak": FP32_PEAK_TFLOPS,
-                    "unit": "TFLOP/s", "frac": flops * cells / stage_s / 1e12 / FP32_PEAK_TFLOPS,
-                    "algorithmic_flops_per_cell_stage": flops,
-                    "frac_shared_indicators": flops_sh * cells / stage_s / 1e12 /
-                    FP32_PEAK_TFLOPS},
-            "hbm": {"achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
-                    "peak_source": f"{peak_src} HBM copy bandwidth",
-                    "algorithmic_bytes_per_cell_stage": (8.0 / 3.0) * nv * 4}}
+    out = {"stage_ms": ms_step / 3.0,
+           "alu": {"achieved": flops * cells / stage_s / 1e12, "peak": FP32_PEAK_TFLOPS,
+                   "unit": "TFLOP/s", "frac": flops * cells / stage_s / 1e12 / FP32_PEAK_TFLOPS,
+                   "algorithmic_flops_per_cell_stage": flops,
+                   "frac_shared_indicators": flops_sh * cells / stage_s / 1e12 /
+                   FP32_PEAK_TFLOPS},
+           "hbm": {"achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                   "peak_source": f"{peak_src} HBM copy bandwidth",
+                   "algorithmic_bytes_per_cell_stage": (8.0 / 3.0) * nv * 4,
+                   "traffic": None}}
+    if record:
+        out["hbm"]["traffic"] = float(record["dram_bytes_per_launch"])
+        out["hbm"]["traffic_note"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one "
+                                      "stage-0 launch (its input is read once: Y_s is Y^n)")
+        rate = float(record["warp_instructions_per_launch"]) / stage_s
+        out["issue"] = {"achieved": rate, "peak": ISSUE_PEAK_WARP_INST,
+                        "unit": "warp instructions/s", "frac": rate / ISSUE_PEAK_WARP_INST}
+    return out
 
 
 def jovian_line(args, stream, peak, peak_src):
@@ -880,7 +891,8 @@ def jovian_line(args, stream, peak, peak_src):
     ctx.close()
     out = {"value": w.ncells * 3 / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
            "cells": w.ncells, "nfields": w.nv, "l2": "inputs larger than L2"}
-    out.update(stage_rooflines(ms, w.ncells, w.nv, 3, peak, peak_src))
+    out.update(stage_rooflines(ms, w.ncells, w.nv, 3, peak, peak_src,
+                               ncu_record("jovian_256x256x128", "kern_moist3d.cu")))
     return out
 
 
@@ -908,7 +920,8 @@ def ensemble_line(args, stream, peak, peak_src):
            "tile": list(info["tile"]), "tile_per_size": info.get("tile_per_size"),
            "ms_per_step_persistent": pers, "ms_per_step_three_launches": three,
            "l2": "inputs larger than L2"}
-    out.update(stage_rooflines(ms, cells, ws[0].nv, 2, peak, peak_src))
+    out.update(stage_rooflines(ms, cells, ws[0].nv, 2, peak, peak_src,
+                               ncu_record("ensemble_96", "kern_moist2d.cu")))
     return out
 
 
